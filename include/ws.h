@@ -1,0 +1,209 @@
+/*
+ * ws.h -- C ABI of libws, a GB300-native (sm_103a) watershed and waterfall
+ * partitioning library.
+ *
+ * The method is the one of "Parallel Watershed Partitioning: GPU-Based
+ * Hierarchical Image Segmentation" (Yeghiazaryan, Gabrielyan, Voiculescu,
+ * arXiv 2410.08946):
+ *   - watershed (Sec. 3, Alg. 1): step I states and steepest-descent arrows
+ *     (Eq. 1), step II fair resolution of non-minimal plateaux (Sec. 3.3,
+ *     Alg. 3), step III path reduction to the minima (Sec. 3.1, Fig. 4),
+ *     step IV Union-Find merge of minimal plateaux (Sec. 3.1);
+ *   - waterfall (Sec. 4, Alg. 4, Alg. 5): lowest pass of each basin, then the
+ *     basins joined across their lowest passes, NL levels in all.
+ *
+ * Conventions for every entry point
+ *   Images are dense, row-major, x fastest: a 2D pixel (x, y) is p = y*W + x,
+ *   a 3D voxel (x, y, z) is p = (z*H + y)*W + x (the row-major order of
+ *   Sec. 3.1).  N = W*H*D must be below 2^31.  Neighbourhoods contain in-image
+ *   pixels only (no padding, no wrap-around).
+ *
+ *   Labels are canonical: the K regions of a level are numbered 0..K-1 in the
+ *   order of each region's smallest pixel index.  (The paper's labels are the
+ *   index of a representative pixel, Sec. 3.1; any two equivalent labellings
+ *   map to the same canonical one.)
+ *
+ *   Buffers named *_d are device pointers owned by the caller; the library
+ *   never frees or keeps them after the call's work completes.  *_h are host
+ *   pointers (pinned memory gives the fastest copies).  Workspace (label and
+ *   parent arrays, edge tables) is owned by the context and stays resident
+ *   between calls; it grows on demand within the context's byte budget.
+ *
+ *   Device-side calls only enqueue work on `stream` (NULL = the legacy
+ *   default stream) and return without waiting for it.  Argument errors are
+ *   returned at once and enqueue nothing.  Errors found by the device (an
+ *   iteration cap reached, a full edge table) are recorded in the context's
+ *   device status word and returned by ws_context_check().  No call aborts,
+ *   throws or traps; every device loop is bounded.
+ *
+ *   A context may be used from one host thread at a time.  Calls on one
+ *   context must not overlap on the device (they share its workspace): use
+ *   one stream per context, or one context per stream.
+ */
+#ifndef WS_H
+#define WS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* same type as cudaStream_t / CUstream */
+typedef struct CUstream_st *ws_stream_t;
+
+typedef enum {
+    WS_OK = 0,
+    WS_ERR_INVALID = 1,      /* bad argument: pointer, shape, dtype, connectivity, NL */
+    WS_ERR_UNSUPPORTED = 2,  /* valid request that this build does not implement */
+    WS_ERR_OOM = 3,          /* workspace budget or device memory exhausted, or edge table full */
+    WS_ERR_CUDA = 4,         /* a CUDA runtime call failed (see ws_last_error) */
+    WS_ERR_NONCONVERGED = 5, /* a device loop hit its iteration cap */
+    WS_ERR_TIMEOUT = 6,      /* a device-wide barrier waited longer than its time limit */
+    WS_ERR_NOT_READY = 7,    /* ws_poll: the request has not finished yet */
+    WS_ERR_CANCELLED = 8     /* ws_poll: the request was cancelled */
+} ws_status;
+
+typedef enum { WS_U8 = 0, WS_U16 = 1 } ws_dtype;
+
+/* dims[0] = W (fastest), dims[1] = H, dims[2] = D (ignored when ndim == 2) */
+typedef struct {
+    int32_t ndim;
+    int32_t pad_;
+    int64_t dims[3];
+} ws_shape;
+
+typedef struct ws_context ws_context;
+
+/* Tuning knobs (all optional; zero = library default). */
+typedef struct {
+    int32_t plateau_round_cap;   /* max global rounds of the step II distance relaxation */
+    int32_t jump_round_cap;      /* max global rounds of step III pointer jumping */
+    int32_t jumps_per_round;     /* pointer hops per pixel per round (the paper's RR, Sec. 3.1) */
+    int32_t barrier_timeout_ms;  /* device-wide barrier wait limit */
+    int64_t edge_capacity;       /* slots of the region-adjacency hash table */
+} ws_tuning;
+
+/* ------------------------------------------------------------------------ */
+/* context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device`.  workspace_budget_bytes bounds
+ * the device memory the context may hold (0 = no bound).  Nothing is
+ * allocated until the first call that needs workspace. */
+ws_status ws_context_create(ws_context **out, int device, size_t workspace_budget_bytes);
+
+/* Frees the context and its workspace.  The caller must make sure no work of
+ * this context is still running (synchronise its streams first). */
+void ws_context_destroy(ws_context *ctx);
+
+/* Waits for `stream`, then reads and clears the device status word: WS_OK if
+ * every call enqueued on this context since the last check completed, else
+ * the first error recorded (WS_ERR_NONCONVERGED, WS_ERR_TIMEOUT, WS_ERR_OOM). */
+ws_status ws_context_check(ws_context *ctx, ws_stream_t stream);
+
+/* Human-readable message for the last error of this context ("" if none).
+ * The pointer stays valid until the next call on the context. */
+const char *ws_last_error(const ws_context *ctx);
+
+/* Replaces the tuning knobs (zero fields keep their defaults). */
+ws_status ws_context_set_tuning(ws_context *ctx, const ws_tuning *t);
+
+/* Device bytes currently held by the context's workspace. */
+size_t ws_context_workspace_bytes(const ws_context *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* hot path                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Pipeline steps 1-2 of Sec. 1 (minimal smoothing, gradient magnitude; Fig. 2
+ * marks both optional).  The paper names no operator; this library uses a
+ * 5x5 binomial blur [1 4 6 4 1]^2 with (sum + 128) >> 8, a 3x3 integer
+ * Sobel, the exact floor square root of gx^2 + gy^2 clipped to 255, then
+ * >> quant_shift (0..7).  Borders replicate the edge pixel.
+ *   img_d   uint8 [H*W] (2D only; shape->ndim must be 2)
+ *   grad_d  uint8 [H*W] output; must not overlap img_d
+ */
+ws_status ws_gradient(ws_context *ctx, const uint8_t *img_d, const ws_shape *shape, int quant_shift,
+                      uint8_t *grad_d, ws_stream_t stream);
+
+/*
+ * Watershed, steps I-IV of Alg. 1 with the step II result of Sec. 3.3 / Alg. 3
+ * (each non-minimal plateau pixel drains towards the nearest lower border of
+ * its plateau; ties between equally near neighbours go to the larger pixel
+ * index, as Eq. 1 does for steepest descent).
+ *   grad_d        gradient samples, dtype WS_U8 or WS_U16, [N]
+ *   connectivity  4 or 8 (ndim 2), 6 (ndim 3; 26 returns WS_ERR_UNSUPPORTED)
+ *   labels_d      int32 [N] output, canonical basin ids 0..K-1
+ *   count_d       int32 [1] output, K (may be NULL)
+ */
+ws_status ws_watershed(ws_context *ctx, const void *grad_d, ws_dtype dtype, const ws_shape *shape,
+                       int connectivity, int32_t *labels_d, int32_t *count_d, ws_stream_t stream);
+
+/*
+ * Waterfall levels 1..NL-1 above given level-0 basins (Sec. 4, Alg. 4 with the
+ * lowest passes of Alg. 5 step V).  pass(A, B) is the smallest
+ * max(G(p), G(q)) over adjacent pixels p in A, q in B; newmin(A) is A's
+ * lowest pass.  Level k+1 joins A and B whenever pass(A, B) equals newmin(A)
+ * or newmin(B) (chains of such joins merge), so every level is a union of
+ * regions of the level below.
+ *   labels0_d  int32 [N] canonical level-0 labels (as ws_watershed writes them)
+ *   NL         number of levels counting level 0 (Sec. 4), NL >= 1
+ *   levels_d   int32 [(NL-1)*N] output, level k at offset (k-1)*N
+ *   counts_d   int32 [NL] output, region count of levels 0..NL-1 (may be NULL)
+ */
+ws_status ws_waterfall(ws_context *ctx, const int32_t *labels0_d, const void *grad_d, ws_dtype dtype,
+                       const ws_shape *shape, int connectivity, int NL, int32_t *levels_d,
+                       int32_t *counts_d, ws_stream_t stream);
+
+/*
+ * The whole hierarchy of Alg. 4: ws_watershed followed by ws_waterfall.
+ *   levels_d  int32 [NL*N] output, level 0 first
+ *   counts_d  int32 [NL] output (may be NULL)
+ */
+ws_status ws_segment(ws_context *ctx, const void *grad_d, ws_dtype dtype, const ws_shape *shape,
+                     int connectivity, int NL, int32_t *levels_d, int32_t *counts_d,
+                     ws_stream_t stream);
+
+/*
+ * ws_segment on HOST buffers: copies grad_h to the device, runs the
+ * hierarchy, copies levels and counts back, and waits for completion before
+ * returning (this call does synchronise `stream`).  Returns the device status
+ * as ws_context_check would.
+ *   grad_h    host gradient [N];  levels_h  host int32 [NL*N];  counts_h  host int32 [NL]
+ */
+ws_status ws_segment_host(ws_context *ctx, const void *grad_h, ws_dtype dtype, const ws_shape *shape,
+                          int connectivity, int NL, int32_t *levels_h, int32_t *counts_h,
+                          ws_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* step-level entry points (for parity checks of individual steps)           */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Step I alone (Alg. 1 step I, Eq. 1).
+ *   states_d  uint8 [N] output: 0 lower neighbour, 1 strict minimum (or no
+ *             neighbour), 2 plateau pixel whose chosen equal neighbour has a
+ *             larger index, 3 one whose equal neighbours all have smaller ones
+ *   arrows_d  int32 [N] output: q for states 0 and 2, p itself for 1 and 3
+ */
+ws_status ws_step1(ws_context *ctx, const void *grad_d, ws_dtype dtype, const ws_shape *shape,
+                   int connectivity, uint8_t *states_d, int32_t *arrows_d, ws_stream_t stream);
+
+/*
+ * Step II distances (the fixpoint of Alg. 3, where -S is the distance):
+ *   dist_d  int32 [N] output: 0 for state-0 pixels, the equal-valued path
+ *           length to the nearest state-0 pixel of the plateau for plateau
+ *           pixels that have one, -1 otherwise (state 1, minimal plateaux)
+ */
+ws_status ws_plateau_distance(ws_context *ctx, const void *grad_d, ws_dtype dtype,
+                              const ws_shape *shape, int connectivity, int32_t *dist_d,
+                              ws_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WS_H */

@@ -1,0 +1,242 @@
+"""Thin ctypes binding of libws (the C ABI in include/ws.h).
+
+Argument marshalling only: every step of the watershed / waterfall runs in the
+library's CUDA kernels.  Device buffers are torch CUDA tensors (passed by
+``data_ptr()``), the stream is torch's current stream unless given.  There is
+no CPU fallback: if libws.so is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libws.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "ws.h")
+
+WS_OK, WS_ERR_INVALID, WS_ERR_UNSUPPORTED, WS_ERR_OOM, WS_ERR_CUDA = 0, 1, 2, 3, 4
+WS_ERR_NONCONVERGED, WS_ERR_TIMEOUT, WS_ERR_NOT_READY, WS_ERR_CANCELLED = 5, 6, 7, 8
+WS_U8, WS_U16 = 0, 1
+STATUS_NAMES = {0: "WS_OK", 1: "WS_ERR_INVALID", 2: "WS_ERR_UNSUPPORTED", 3: "WS_ERR_OOM", 4: "WS_ERR_CUDA",
+                5: "WS_ERR_NONCONVERGED", 6: "WS_ERR_TIMEOUT", 7: "WS_ERR_NOT_READY", 8: "WS_ERR_CANCELLED"}
+
+
+class WsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ws_shape(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("pad_", ctypes.c_int32), ("dims", ctypes.c_int64 * 3)]
+
+
+class ws_tuning(ctypes.Structure):
+    _fields_ = [("plateau_round_cap", ctypes.c_int32), ("jump_round_cap", ctypes.c_int32),
+                ("jumps_per_round", ctypes.c_int32), ("barrier_timeout_ms", ctypes.c_int32),
+                ("edge_capacity", ctypes.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def declared_symbols(header: str = HEADER):
+    """Names of the functions include/ws.h declares."""
+    txt = open(header).read()
+    return sorted(set(re.findall(r"^\s*(?:ws_status|void|const char \*|size_t)\s*\*?\s*(ws_\w+)\s*\(",
+                                 txt, flags=re.M)))
+
+
+def load(path: str = LIB_PATH):
+    """Loads libws.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libws.so not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        SH = ctypes.POINTER(ws_shape)
+        sig = {
+            "ws_context_create": ([ctypes.POINTER(P), I, S], I),
+            "ws_context_destroy": ([P], None),
+            "ws_context_check": ([P, P], I),
+            "ws_last_error": ([P], ctypes.c_char_p),
+            "ws_context_set_tuning": ([P, ctypes.POINTER(ws_tuning)], I),
+            "ws_context_workspace_bytes": ([P], S),
+            "ws_gradient": ([P, P, SH, I, P, P], I),
+            "ws_watershed": ([P, P, I, SH, I, P, P, P], I),
+            "ws_waterfall": ([P, P, P, I, SH, I, I, P, P, P], I),
+            "ws_segment": ([P, P, I, SH, I, I, P, P, P], I),
+            "ws_segment_host": ([P, P, I, SH, I, I, P, P, P], I),
+            "ws_step1": ([P, P, I, SH, I, P, P, P], I),
+            "ws_plateau_distance": ([P, P, I, SH, I, P, P], I),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def _shape_of(shape) -> ws_shape:
+    shape = tuple(int(s) for s in shape)
+    s = ws_shape()
+    if len(shape) == 1:
+        shape = (1,) + shape
+    if len(shape) == 2:
+        s.ndim = 2
+        s.dims[0], s.dims[1], s.dims[2] = shape[1], shape[0], 1
+    elif len(shape) == 3:
+        s.ndim = 3
+        s.dims[0], s.dims[1], s.dims[2] = shape[2], shape[1], shape[0]
+    else:
+        raise ValueError("images are 2D (H, W) or 3D (D, H, W)")
+    return s
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.uint8:
+        return WS_U8
+    if t.dtype == torch.uint16:
+        return WS_U16
+    raise TypeError("gradient must be uint8 or uint16")
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A libws context (workspace + device status word) on one GPU."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        self.lib = load()
+        self.handle = ctypes.c_void_p()
+        st = self.lib.ws_context_create(ctypes.byref(self.handle), int(device), int(budget_bytes))
+        if st != WS_OK:
+            raise WsError(st, "ws_context_create failed")
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            self.lib.ws_context_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- plumbing ---------------------------------------------------------
+    def last_error(self) -> str:
+        return (self.lib.ws_last_error(self.handle) or b"").decode()
+
+    def _ok(self, st: int):
+        if st != WS_OK:
+            raise WsError(st, self.last_error())
+
+    def check(self, stream=None):
+        """Synchronise the stream and raise if the device recorded an error."""
+        self._ok(self.lib.ws_context_check(self.handle, _stream(stream)))
+
+    def set_tuning(self, **kw):
+        t = ws_tuning(**kw)
+        self._ok(self.lib.ws_context_set_tuning(self.handle, ctypes.byref(t)))
+
+    def workspace_bytes(self) -> int:
+        return int(self.lib.ws_context_workspace_bytes(self.handle))
+
+    # -- entry points -------------------------------------------------------
+    def gradient(self, img, quant_shift: int = 0, out=None, stream=None):
+        import torch
+        if img.dtype != torch.uint8 or img.dim() != 2:
+            raise TypeError("gradient takes a 2D uint8 image")
+        out = torch.empty_like(img) if out is None else out
+        sh = _shape_of(img.shape)
+        self._ok(self.lib.ws_gradient(self.handle, _dev(img), ctypes.byref(sh), int(quant_shift), _dev(out),
+                                      _stream(stream)))
+        return out
+
+    def step1(self, grad, conn: int, stream=None):
+        import torch
+        states = torch.empty(grad.shape, dtype=torch.uint8, device=grad.device)
+        arrows = torch.empty(grad.shape, dtype=torch.int32, device=grad.device)
+        sh = _shape_of(grad.shape)
+        self._ok(self.lib.ws_step1(self.handle, _dev(grad), _dtype_code(grad), ctypes.byref(sh), int(conn),
+                                   _dev(states), _dev(arrows), _stream(stream)))
+        return states, arrows
+
+    def plateau_distance(self, grad, conn: int, stream=None):
+        import torch
+        dist = torch.empty(grad.shape, dtype=torch.int32, device=grad.device)
+        sh = _shape_of(grad.shape)
+        self._ok(self.lib.ws_plateau_distance(self.handle, _dev(grad), _dtype_code(grad), ctypes.byref(sh),
+                                              int(conn), _dev(dist), _stream(stream)))
+        return dist
+
+    def watershed(self, grad, conn: int, labels=None, count=None, stream=None):
+        import torch
+        labels = torch.empty(grad.shape, dtype=torch.int32, device=grad.device) if labels is None else labels
+        count = torch.empty(1, dtype=torch.int32, device=grad.device) if count is None else count
+        sh = _shape_of(grad.shape)
+        self._ok(self.lib.ws_watershed(self.handle, _dev(grad), _dtype_code(grad), ctypes.byref(sh), int(conn),
+                                       _dev(labels), _dev(count), _stream(stream)))
+        return labels, count
+
+    def waterfall(self, labels0, grad, conn: int, NL: int, levels=None, counts=None, stream=None):
+        import torch
+        if levels is None:
+            levels = torch.empty((max(NL - 1, 1),) + tuple(grad.shape), dtype=torch.int32, device=grad.device)
+        counts = torch.empty(NL, dtype=torch.int32, device=grad.device) if counts is None else counts
+        sh = _shape_of(grad.shape)
+        self._ok(self.lib.ws_waterfall(self.handle, _dev(labels0), _dev(grad), _dtype_code(grad), ctypes.byref(sh),
+                                       int(conn), int(NL), _dev(levels), _dev(counts), _stream(stream)))
+        return levels[: NL - 1], counts
+
+    def segment(self, grad, conn: int, NL: int, levels=None, counts=None, stream=None):
+        import torch
+        if levels is None:
+            levels = torch.empty((NL,) + tuple(grad.shape), dtype=torch.int32, device=grad.device)
+        counts = torch.empty(NL, dtype=torch.int32, device=grad.device) if counts is None else counts
+        sh = _shape_of(grad.shape)
+        self._ok(self.lib.ws_segment(self.handle, _dev(grad), _dtype_code(grad), ctypes.byref(sh), int(conn),
+                                     int(NL), _dev(levels), _dev(counts), _stream(stream)))
+        return levels, counts
+
+    def segment_host(self, grad_h, conn: int, NL: int, levels_h=None, counts_h=None, stream=None):
+        """grad_h, levels_h, counts_h: CPU tensors (pinned for speed).  Blocks until done."""
+        import torch
+        if grad_h.is_cuda or not grad_h.is_contiguous():
+            raise ValueError("segment_host takes a contiguous CPU tensor")
+        if levels_h is None:
+            levels_h = torch.empty((NL,) + tuple(grad_h.shape), dtype=torch.int32, pin_memory=True)
+        if counts_h is None:
+            counts_h = torch.empty(NL, dtype=torch.int32)
+        sh = _shape_of(grad_h.shape)
+        self._ok(self.lib.ws_segment_host(self.handle, ctypes.c_void_p(grad_h.data_ptr()), _dtype_code(grad_h),
+                                          ctypes.byref(sh), int(conn), int(NL), ctypes.c_void_p(levels_h.data_ptr()),
+                                          ctypes.c_void_p(counts_h.data_ptr()), _stream(stream)))
+        return levels_h, counts_h

@@ -1,0 +1,409 @@
+// ws_api.cu -- the C ABI of libws (declared in include/ws.h): contexts,
+// workspace management under a byte budget, argument validation, dispatch to
+// the per-(dtype, connectivity) pipelines, the device status word.
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "ws_internal.h"
+
+using namespace ws;
+
+namespace ws {
+
+int tune_plateau_cap(const ws_context *c) { return c->tun.plateau_round_cap > 0 ? c->tun.plateau_round_cap : (1 << 24); }
+int tune_jump_cap(const ws_context *c) { return c->tun.jump_round_cap > 0 ? c->tun.jump_round_cap : 4096; }
+int tune_rr(const ws_context *c) { return c->tun.jumps_per_round > 0 ? c->tun.jumps_per_round : 6; }
+unsigned long long tune_timeout_ns(const ws_context *c)
+{
+    long long ms = c->tun.barrier_timeout_ms > 0 ? c->tun.barrier_timeout_ms : 4000;
+    return (unsigned long long)ms * 1000000ull;
+}
+
+ws_status set_cuda_error(ws_context *c, cudaError_t e, const char *what)
+{
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    c->err = buf;
+    return e == cudaErrorMemoryAllocation ? WS_ERR_OOM : WS_ERR_CUDA;
+}
+
+static ws_status set_error(ws_context *c, ws_status st, const char *msg)
+{
+    c->err = msg;
+    return st;
+}
+
+template <typename P> static ws_status dalloc(ws_context *c, P **p, size_t bytes)
+{
+    if (c->budget && c->held + bytes > c->budget) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "workspace budget exceeded: need %zu more bytes, %zu of %zu held", bytes,
+                 c->held, c->budget);
+        c->err = buf;
+        return WS_ERR_OOM;
+    }
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_cuda_error(c, e, "cudaMalloc");
+    }
+    c->held += bytes;
+    *p = (P *)q;
+    return WS_OK;
+}
+
+template <typename P> static void dfree(ws_context *c, P **p, size_t bytes)
+{
+    if (*p) {
+        cudaFree((void *)*p);
+        c->held -= bytes;
+        *p = nullptr;
+    }
+}
+
+ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles, size_t nblk)
+{
+    Workspace &w = c->w;
+    ws_status st = WS_OK;
+    if (N > w.N) {
+        dfree(c, &w.par, w.N * 4);
+        dfree(c, &w.aux, w.N * 4);
+        dfree(c, &w.st, w.N);
+        w.N = 0;
+        if ((st = dalloc(c, &w.par, N * 4)) || (st = dalloc(c, &w.aux, N * 4)) || (st = dalloc(c, &w.st, N)))
+            return st;
+        w.N = N;
+    }
+    if (ntiles > w.ntiles) {
+        dfree(c, &w.act, w.ntiles * 2);
+        w.ntiles = 0;
+        if ((st = dalloc(c, &w.act, ntiles * 2))) return st;
+        w.ntiles = ntiles;
+    }
+    if (nblk > w.nblk) {
+        dfree(c, &w.blk, (w.nblk + 1) * 4);
+        w.nblk = 0;
+        if ((st = dalloc(c, &w.blk, (nblk + 1) * 4))) return st;
+        w.nblk = nblk;
+    }
+    return WS_OK;
+}
+
+ws_status ensure_edges(ws_context *c, size_t cap)
+{
+    Workspace &w = c->w;
+    if (cap <= w.edge_cap) return WS_OK;
+    cudaDeviceSynchronize();
+    dfree(c, &w.keys, w.edge_cap * 8);
+    dfree(c, &w.vals, w.edge_cap * 4);
+    dfree(c, &w.slots, w.edge_cap * 4);
+    w.edge_cap = 0;
+    ws_status st;
+    if ((st = dalloc(c, &w.keys, cap * 8)) || (st = dalloc(c, &w.vals, cap * 4)) ||
+        (st = dalloc(c, &w.slots, cap * 4)))
+        return st;
+    cudaError_t e = cudaMemset(w.keys, 0xff, cap * 8);
+    if (e == cudaSuccess) e = cudaMemset(w.vals, 0xff, cap * 4);
+    if (e == cudaSuccess) e = cudaMemset(w.ecount, 0, 4);
+    if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
+    w.edge_cap = cap;
+    return WS_OK;
+}
+
+ws_status ensure_regions(ws_context *c, size_t kmax, int levels)
+{
+    Workspace &w = c->w;
+    if (kmax <= w.kmax && levels <= w.levels_cap) return WS_OK;
+    size_t nk = kmax > w.kmax ? kmax : w.kmax;
+    int nl = levels > w.levels_cap ? levels : w.levels_cap;
+    dfree(c, &w.gmap, w.kmax * 4 * (size_t)w.levels_cap);
+    dfree(c, &w.newmin, w.kmax * 4);
+    dfree(c, &w.uf, w.kmax * 4);
+    dfree(c, &w.rank, w.kmax * 4);
+    w.kmax = 0;
+    w.levels_cap = 0;
+    ws_status st;
+    if ((st = dalloc(c, &w.gmap, nk * 4 * (size_t)nl)) || (st = dalloc(c, &w.newmin, nk * 4)) ||
+        (st = dalloc(c, &w.uf, nk * 4)) || (st = dalloc(c, &w.rank, nk * 4)))
+        return st;
+    w.kmax = nk;
+    w.levels_cap = nl;
+    return WS_OK;
+}
+
+const Launchers *launchers(int dtype, int conn)
+{
+    if (dtype == WS_U8) return launchers_u8(conn);
+    if (dtype == WS_U16) return launchers_u16(conn);
+    return nullptr;
+}
+
+}  // namespace ws
+
+// ---------------------------------------------------------------------------
+// argument validation
+// ---------------------------------------------------------------------------
+
+static ws_status make_geo(ws_context *c, const ws_shape *shape, Geo *g)
+{
+    if (!shape) return set_error(c, WS_ERR_INVALID, "shape is NULL");
+    if (shape->ndim != 2 && shape->ndim != 3) return set_error(c, WS_ERR_INVALID, "ndim must be 2 or 3");
+    int64_t W = shape->dims[0], H = shape->dims[1], D = shape->ndim == 3 ? shape->dims[2] : 1;
+    if (W < 1 || H < 1 || D < 1) return set_error(c, WS_ERR_INVALID, "every dimension must be >= 1");
+    if (W > 0x7fffffff || H > 0x7fffffff || D > 0x7fffffff || W * H > 0x7fffffffLL ||
+        W * H * D > 0x7fffffffLL)
+        return set_error(c, WS_ERR_INVALID, "image too large: N must be below 2^31");
+    g->W = (int)W;
+    g->H = (int)H;
+    g->D = (int)D;
+    g->HW = (int)(W * H);
+    g->N = (int)(W * H * D);
+    return WS_OK;
+}
+
+static ws_status check_conn(ws_context *c, const ws_shape *shape, int conn)
+{
+    if (shape->ndim == 2 && (conn == 4 || conn == 8)) return WS_OK;
+    if (shape->ndim == 3 && conn == 6) return WS_OK;
+    if (shape->ndim == 3 && conn == 26) return set_error(c, WS_ERR_UNSUPPORTED, "26-connectivity is not implemented");
+    return set_error(c, WS_ERR_INVALID, "connectivity must be 4 or 8 (2D) or 6 (3D)");
+}
+
+static ws_status prep(ws_context *c, const void *grad, int dtype, const ws_shape *shape, int conn, Geo *g,
+                      const Launchers **L)
+{
+    if (!c) return WS_ERR_INVALID;
+    c->err.clear();
+    ws_status st = make_geo(c, shape, g);
+    if (st) return st;
+    if ((st = check_conn(c, shape, conn))) return st;
+    if (dtype != WS_U8 && dtype != WS_U16) return set_error(c, WS_ERR_INVALID, "dtype must be WS_U8 or WS_U16");
+    if (!grad) return set_error(c, WS_ERR_INVALID, "gradient pointer is NULL");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != c->device) {
+        cudaError_t e = cudaSetDevice(c->device);
+        if (e != cudaSuccess) return set_cuda_error(c, e, "cudaSetDevice");
+    }
+    *L = launchers(dtype, conn);
+    if (!*L) return set_error(c, WS_ERR_UNSUPPORTED, "no pipeline for this dtype / connectivity");
+    return WS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+ws_status ws_context_create(ws_context **out, int device, size_t budget)
+{
+    if (!out) return WS_ERR_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return device < 0 ? WS_ERR_INVALID : WS_ERR_CUDA;
+    }
+    ws_context *c = new (std::nothrow) ws_context();
+    if (!c) return WS_ERR_OOM;
+    c->device = device;
+    c->budget = budget;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete c;
+        return WS_ERR_CUDA;
+    }
+    ws_status st = dalloc(c, &c->status, sizeof(DevStatus));
+    if (st == WS_OK) st = dalloc(c, &c->w.ecount, 4);
+    if (st == WS_OK) st = dalloc(c, &c->w.bsum, 4096 * 4);
+    if (st == WS_OK) st = dalloc(c, &c->w.kcount, 4);
+    if (st == WS_OK) {
+        e = cudaMemset(c->status, 0, sizeof(DevStatus));
+        if (e == cudaSuccess) e = cudaMemset(c->w.ecount, 0, 4);
+        if (e == cudaSuccess) e = cudaMemset(c->w.kcount, 0, 4);
+        if (e != cudaSuccess) st = WS_ERR_CUDA;
+    }
+    if (st != WS_OK) {
+        ws_context_destroy(c);
+        return st;
+    }
+    *out = c;
+    return WS_OK;
+}
+
+void ws_context_destroy(ws_context *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    Workspace &w = c->w;
+    cudaFree(c->status);
+    void *ptrs[] = {w.par, w.aux, w.st, w.act, w.blk, w.keys, w.vals, w.slots, w.ecount, w.gmap, w.newmin,
+                    w.uf, w.rank, w.bsum, w.kcount, w.grad_stage, w.levels_stage, w.counts_stage};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+ws_status ws_context_check(ws_context *c, ws_stream_t stream)
+{
+    if (!c) return WS_ERR_INVALID;
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return set_cuda_error(c, e, "stream synchronize");
+    DevStatus h;
+    e = cudaMemcpy(&h, c->status, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_cuda_error(c, e, "status read");
+    if (h.code == 0) return WS_OK;
+    cudaMemset(c->status, 0, sizeof(DevStatus));
+    char buf[200];
+    const char *what = "device error";
+    switch (h.where) {
+    case 2: what = "step II plateau relaxation reached its round cap"; break;
+    case 3: what = "Union retry cap reached"; break;
+    case 4: what = "Union retry cap reached"; break;
+    case 5: what = "step III pointer jumping reached its round cap"; break;
+    case 6: what = "region adjacency table full (raise ws_tuning.edge_capacity)"; break;
+    case 100: what = "device-wide barrier timed out"; break;
+    }
+    snprintf(buf, sizeof buf, "%s (code %d, site %d)", what, h.code, h.where);
+    c->err = buf;
+    return (ws_status)h.code;
+}
+
+const char *ws_last_error(const ws_context *c) { return c ? c->err.c_str() : "no context"; }
+
+ws_status ws_context_set_tuning(ws_context *c, const ws_tuning *t)
+{
+    if (!c || !t) return WS_ERR_INVALID;
+    if (t->plateau_round_cap < 0 || t->jump_round_cap < 0 || t->jumps_per_round < 0 || t->barrier_timeout_ms < 0 ||
+        t->edge_capacity < 0)
+        return set_error(c, WS_ERR_INVALID, "tuning values must be >= 0");
+    c->tun = *t;
+    return WS_OK;
+}
+
+size_t ws_context_workspace_bytes(const ws_context *c) { return c ? c->held : 0; }
+
+ws_status ws_gradient(ws_context *c, const uint8_t *img_d, const ws_shape *shape, int quant_shift, uint8_t *grad_d,
+                      ws_stream_t stream)
+{
+    if (!c) return WS_ERR_INVALID;
+    c->err.clear();
+    Geo g;
+    ws_status st = make_geo(c, shape, &g);
+    if (st) return st;
+    if (shape->ndim != 2) return set_error(c, WS_ERR_UNSUPPORTED, "ws_gradient takes 2D images");
+    if (!img_d || !grad_d) return set_error(c, WS_ERR_INVALID, "NULL buffer");
+    if (quant_shift < 0 || quant_shift > 7) return set_error(c, WS_ERR_INVALID, "quant_shift must be 0..7");
+    if ((const void *)img_d == (const void *)grad_d) return set_error(c, WS_ERR_INVALID, "img and grad overlap");
+    cudaSetDevice(c->device);
+    return launch_gradient(c, img_d, g.W, g.H, quant_shift, grad_d, (cudaStream_t)stream);
+}
+
+ws_status ws_step1(ws_context *c, const void *grad_d, ws_dtype dtype, const ws_shape *shape, int conn,
+                   uint8_t *states_d, int32_t *arrows_d, ws_stream_t stream)
+{
+    Geo g;
+    const Launchers *L = nullptr;
+    ws_status st = prep(c, grad_d, dtype, shape, conn, &g, &L);
+    if (st) return st;
+    if (!states_d || !arrows_d) return set_error(c, WS_ERR_INVALID, "NULL output");
+    return L->step1(c, grad_d, g, states_d, arrows_d, (cudaStream_t)stream);
+}
+
+ws_status ws_plateau_distance(ws_context *c, const void *grad_d, ws_dtype dtype, const ws_shape *shape, int conn,
+                              int32_t *dist_d, ws_stream_t stream)
+{
+    Geo g;
+    const Launchers *L = nullptr;
+    ws_status st = prep(c, grad_d, dtype, shape, conn, &g, &L);
+    if (st) return st;
+    if (!dist_d) return set_error(c, WS_ERR_INVALID, "NULL output");
+    return L->plateau_distance(c, grad_d, g, dist_d, (cudaStream_t)stream);
+}
+
+ws_status ws_watershed(ws_context *c, const void *grad_d, ws_dtype dtype, const ws_shape *shape, int conn,
+                       int32_t *labels_d, int32_t *count_d, ws_stream_t stream)
+{
+    Geo g;
+    const Launchers *L = nullptr;
+    ws_status st = prep(c, grad_d, dtype, shape, conn, &g, &L);
+    if (st) return st;
+    if (!labels_d) return set_error(c, WS_ERR_INVALID, "NULL labels");
+    return L->watershed(c, grad_d, g, labels_d, count_d, (cudaStream_t)stream);
+}
+
+ws_status ws_waterfall(ws_context *c, const int32_t *labels0_d, const void *grad_d, ws_dtype dtype,
+                       const ws_shape *shape, int conn, int NL, int32_t *levels_d, int32_t *counts_d,
+                       ws_stream_t stream)
+{
+    Geo g;
+    const Launchers *L = nullptr;
+    ws_status st = prep(c, grad_d, dtype, shape, conn, &g, &L);
+    if (st) return st;
+    if (!labels0_d) return set_error(c, WS_ERR_INVALID, "NULL labels0");
+    if (NL < 1) return set_error(c, WS_ERR_INVALID, "NL must be >= 1");
+    if (NL > 1 && !levels_d) return set_error(c, WS_ERR_INVALID, "NULL levels");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = launch_count_labels(c, labels0_d, g.N, s))) return st;
+    return L->waterfall(c, labels0_d, grad_d, g, NL, levels_d, counts_d, (size_t)g.N, s);
+}
+
+ws_status ws_segment(ws_context *c, const void *grad_d, ws_dtype dtype, const ws_shape *shape, int conn, int NL,
+                     int32_t *levels_d, int32_t *counts_d, ws_stream_t stream)
+{
+    Geo g;
+    const Launchers *L = nullptr;
+    ws_status st = prep(c, grad_d, dtype, shape, conn, &g, &L);
+    if (st) return st;
+    if (!levels_d) return set_error(c, WS_ERR_INVALID, "NULL levels");
+    if (NL < 1) return set_error(c, WS_ERR_INVALID, "NL must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = L->watershed(c, grad_d, g, levels_d, nullptr, s))) return st;
+    // distinct minimal plateaux are never adjacent, so K0 <= ceil(N / 2)
+    return L->waterfall(c, levels_d, grad_d, g, NL, levels_d + g.N, counts_d, (size_t)g.N / 2 + 1, s);
+}
+
+ws_status ws_segment_host(ws_context *c, const void *grad_h, ws_dtype dtype, const ws_shape *shape, int conn,
+                          int NL, int32_t *levels_h, int32_t *counts_h, ws_stream_t stream)
+{
+    Geo g;
+    const Launchers *L = nullptr;
+    ws_status st = prep(c, grad_h, dtype, shape, conn, &g, &L);
+    if (st) return st;
+    if (!levels_h || NL < 1) return set_error(c, WS_ERR_INVALID, "NULL levels or NL < 1");
+    Workspace &w = c->w;
+    // staging buffers, grown on demand: host_n = bytes of the levels buffer;
+    // the gradient buffer gets half of that (>= 2 bytes per pixel)
+    size_t b = dtype == WS_U8 ? 1 : 2;
+    size_t levels_bytes = (size_t)NL * g.N * 4;
+    if (levels_bytes > w.host_n) {
+        dfree(c, &w.levels_stage, w.host_n);
+        dfree(c, &w.grad_stage, w.host_n / 2);
+        w.host_n = 0;
+        if ((st = dalloc(c, &w.levels_stage, levels_bytes)) || (st = dalloc(c, &w.grad_stage, levels_bytes / 2)))
+            return st;
+        w.host_n = levels_bytes;
+    }
+    if (g.N * b > w.host_n / 2) return set_error(c, WS_ERR_INVALID, "staging too small");
+    if (!w.counts_stage && (st = dalloc(c, &w.counts_stage, 64 * 4))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(w.grad_stage, grad_h, (size_t)g.N * b, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return set_cuda_error(c, e, "H2D copy");
+    if ((st = L->watershed(c, w.grad_stage, g, w.levels_stage, nullptr, s))) return st;
+    int32_t *cnt = NL <= 64 ? w.counts_stage : nullptr;
+    if ((st = L->waterfall(c, w.levels_stage, w.grad_stage, g, NL, w.levels_stage + g.N, cnt, (size_t)g.N / 2 + 1, s)))
+        return st;
+    e = cudaMemcpyAsync(levels_h, w.levels_stage, levels_bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && counts_h && cnt)
+        e = cudaMemcpyAsync(counts_h, cnt, (size_t)NL * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return set_cuda_error(c, e, "D2H copy");
+    return ws_context_check(c, stream);
+}
+
+}  // extern "C"

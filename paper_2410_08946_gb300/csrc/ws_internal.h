@@ -1,0 +1,110 @@
+// ws_internal.h -- host-side internals of libws shared by its translation
+// units: the context (workspace, tuning, device status word) and the
+// per-(dtype, connectivity) launcher table.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ws.h"
+#include "ws_device.cuh"
+
+namespace ws {
+
+// Tile shapes of the step II relaxation (one CTA relaxes one tile in shared
+// memory with a one-pixel frozen halo).
+struct TileGeo {
+    int TX, TY, TZ;
+    int ntx, nty, ntz;
+    int ntiles;
+};
+
+// Workspace held by a context; every array is sized for the largest image
+// seen so far and stays resident between calls.
+struct Workspace {
+    size_t N = 0;           // pixels the per-pixel arrays can hold
+    int32_t *par = nullptr; // arrows / union-find parents / roots   [N]
+    int32_t *aux = nullptr; // plateau distance, then per-root min index / id [N]
+    uint8_t *st = nullptr;  // states, then "first pixel of its region" flags [N]
+    size_t ntiles = 0;
+    uint8_t *act = nullptr; // active-tile flags, two rounds            [2*ntiles]
+    size_t nblk = 0;
+    int32_t *blk = nullptr; // per-chunk counts for the compaction scan [nblk+1]
+    // region adjacency hash table
+    size_t edge_cap = 0;            // power of two
+    unsigned long long *keys = nullptr;  // (a << 32 | b), empty = ~0
+    uint32_t *vals = nullptr;       // pass value (min height), empty = ~0
+    int32_t *slots = nullptr;       // used slots, in insertion order [edge_cap]
+    int32_t *ecount = nullptr;      // number of used slots             [1]
+    // region graph arrays (level-0 region count K0 <= kmax)
+    size_t kmax = 0;
+    int levels_cap = 0;             // NL-1 the gmap array can hold
+    int32_t *gmap = nullptr;        // level-0 id -> level-k id, [levels_cap][kmax]
+    uint32_t *newmin = nullptr;     // [kmax]
+    int32_t *uf = nullptr;          // [kmax]
+    int32_t *rank = nullptr;        // [kmax]
+    int32_t *bsum = nullptr;        // per-block sums for device-wide scans [4096]
+    int32_t *kcount = nullptr;      // K0 of the last watershed [1]
+    // host-copy staging for ws_segment_host
+    size_t host_n = 0;
+    uint8_t *grad_stage = nullptr;  // device copy of a host gradient
+    int32_t *levels_stage = nullptr;
+    int32_t *counts_stage = nullptr;
+};
+
+}  // namespace ws
+
+struct ws_context {
+    int device = 0;
+    size_t budget = 0;       // 0 = unbounded
+    size_t held = 0;         // bytes held by the workspace
+    std::string err;
+    ws_tuning tun{};
+    ws::DevStatus *status = nullptr;
+    ws::Workspace w;
+    int num_sms = 0;
+};
+
+namespace ws {
+
+// Effective tuning values.
+int tune_plateau_cap(const ws_context *c);
+int tune_jump_cap(const ws_context *c);
+int tune_rr(const ws_context *c);
+unsigned long long tune_timeout_ns(const ws_context *c);
+
+// Workspace management (ws_api.cu).
+ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles, size_t nblk);
+ws_status ensure_edges(ws_context *c, size_t cap);
+ws_status ensure_regions(ws_context *c, size_t kmax, int levels);
+ws_status set_cuda_error(ws_context *c, cudaError_t e, const char *what);
+
+// Launchers instantiated per (sample type, connectivity).
+struct Launchers {
+    ws_status (*watershed)(ws_context *, const void *grad, const Geo &, int32_t *labels,
+                           int32_t *count, cudaStream_t);
+    ws_status (*step1)(ws_context *, const void *grad, const Geo &, uint8_t *states, int32_t *arrows,
+                       cudaStream_t);
+    ws_status (*plateau_distance)(ws_context *, const void *grad, const Geo &, int32_t *dist,
+                                  cudaStream_t);
+    ws_status (*waterfall)(ws_context *, const int32_t *labels0, const void *grad, const Geo &, int NL,
+                           int32_t *levels, int32_t *counts, size_t kmax, cudaStream_t);
+};
+
+// dtype: 0 = u8, 1 = u16; conn: 4, 8, 6.  Returns nullptr when unsupported.
+const Launchers *launchers(int dtype, int conn);
+
+// Instantiation entry points (one per translation unit).
+const Launchers *launchers_u8(int conn);
+const Launchers *launchers_u16(int conn);
+
+// K0 = max(labels) + 1 into c->w.kcount (ws_gradient.cu).
+ws_status launch_count_labels(ws_context *c, const int32_t *labels, int N, cudaStream_t s);
+
+// Gradient (ws_gradient.cu).
+ws_status launch_gradient(ws_context *c, const uint8_t *img, int W, int H, int shift, uint8_t *grad,
+                          cudaStream_t s);
+
+}  // namespace ws

@@ -1,0 +1,721 @@
+// ws_kernels.cuh -- the watershed (steps I-IV) and waterfall kernels of
+// libws, templated on the gradient sample type T (uint8_t / uint16_t) and the
+// connectivity CONN (4, 8 in 2D; 6 in 3D).  Included by one translation
+// unit per sample type, which instantiates the launchers.
+//
+// Pipeline of ws_watershed (all on one stream, no host synchronisation):
+//   k_step1          Eq. 1 arrows and states (Alg. 1 step I); initial step II
+//                    distances (0 on state-0 pixels); flags tiles holding
+//                    plateau pixels
+//   k_plateau        step II: exact geodesic distance of every non-minimal
+//                    plateau pixel to its plateau's lower border, by
+//                    in-tile relaxation in shared memory with frozen halos
+//                    and device-wide rounds over active tiles (the
+//                    block-asynchronous balanced scheme of Sec. 3.4, Alg. 3,
+//                    run to its fixpoint); cooperative launch
+//   k_resolve_union  step II pointer choice on non-minimal plateaux, and
+//                    step IV Union of adjacent minimal-plateau pixels
+//                    (atomicCAS links towards the smaller root)
+//   k_jump           step III pointer jumping, RR hops per pixel per round,
+//                    rounds until nothing changes (Sec. 3.1, Fig. 4), then the
+//                    smallest pixel index of every basin; cooperative launch
+//   k_flags / k_scan / k_assign / k_label
+//                    canonical compaction: ids 0..K-1 by smallest pixel index
+// ws_waterfall:
+//   k_rag            Alg. 5 step V on pixel pairs: pass(A,B) = min over
+//                    adjacent pixels of max(G(p), G(q)), warp-deduplicated
+//                    into a hash table of region pairs
+//   k_levels         NL-1 rounds of lowest-pass merging on the region graph
+//                    (newmin, Union over kept edges, canonical ids);
+//                    cooperative launch
+//   k_level_write    levels[k][p] = map_k[L0[p]] for all k in one pass
+//   k_hash_clear     returns the used table slots to empty
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "ws_device.cuh"
+#include "ws_internal.h"
+
+namespace ws {
+
+constexpr int INF_D = 0x3fffffff;   // "no distance" (INF_D + 1 does not overflow)
+constexpr int NTHR = 256;           // threads per CTA of the per-pixel kernels
+constexpr unsigned long long EMPTY_KEY = ~0ull;
+
+template <int CONN> struct PTile {
+    static constexpr int ND = Dim<CONN>::nd;
+    static constexpr int TX = ND == 2 ? 32 : 16;
+    static constexpr int TY = ND == 2 ? 32 : 8;
+    static constexpr int TZ = ND == 2 ? 1 : 8;
+    static constexpr int HX = TX + 2, HY = TY + 2, HZ = ND == 2 ? 1 : TZ + 2;
+    static constexpr int HS = HX * HY * HZ;
+    static constexpr int NPIX = TX * TY * TZ;
+    static constexpr int PER_THR = NPIX / NTHR;
+};
+
+template <int CONN> inline TileGeo make_tilegeo(const Geo &g)
+{
+    using PT = PTile<CONN>;
+    TileGeo t;
+    t.TX = PT::TX;
+    t.TY = PT::TY;
+    t.TZ = PT::TZ;
+    t.ntx = (g.W + PT::TX - 1) / PT::TX;
+    t.nty = (g.H + PT::TY - 1) / PT::TY;
+    t.ntz = (g.D + PT::TZ - 1) / PT::TZ;
+    t.ntiles = t.ntx * t.nty * t.ntz;
+    return t;
+}
+
+static __device__ __forceinline__ void coords(const Geo &g, int p, int &x, int &y, int &z)
+{
+    z = p / g.HW;
+    int r = p - z * g.HW;
+    y = r / g.W;
+    x = r - y * g.W;
+}
+
+template <int CONN>
+static __device__ __forceinline__ bool nb_at(const Geo &g, int x, int y, int z, int i, int &q)
+{
+    int xx = x + Nb<CONN>::dx(i), yy = y + Nb<CONN>::dy(i), zz = z + Nb<CONN>::dz(i);
+    if (xx < 0 || xx >= g.W || yy < 0 || yy >= g.H || zz < 0 || zz >= g.D) return false;
+    q = (zz * g.H + yy) * g.W + xx;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// step I (Eq. 1)
+// ---------------------------------------------------------------------------
+
+template <typename T, int CONN>
+static __global__ void __launch_bounds__(NTHR) k_step1(const T *__restrict__ g, Geo geo, int32_t *__restrict__ par,
+                                                uint8_t *__restrict__ st, int32_t *__restrict__ dist,
+                                                uint8_t *__restrict__ act, TileGeo tg)
+{
+    for (int p = blockIdx.x * NTHR + threadIdx.x; p < geo.N; p += gridDim.x * NTHR) {
+        int x, y, z;
+        coords(geo, p, x, y, z);
+        const unsigned gp = g[p];
+        unsigned m = 0xffffffffu;
+        int q = -1;
+#pragma unroll
+        for (int i = 0; i < Nb<CONN>::n; i++) {
+            int r;
+            if (!nb_at<CONN>(geo, x, y, z, i, r)) continue;
+            unsigned v = g[r];
+            if (v < m || (v == m && r > q)) {
+                m = v;
+                q = r;
+            }
+        }
+        uint8_t s;
+        int32_t l;
+        if (q < 0 || m > gp) {
+            s = 1;
+            l = p;
+        } else if (m < gp) {
+            s = 0;
+            l = q;
+        } else if (q > p) {
+            s = 2;
+            l = q;
+        } else {
+            s = 3;
+            l = p;
+        }
+        par[p] = l;
+        st[p] = s;
+        if (dist) dist[p] = s == 0 ? 0 : INF_D;
+        if (act && s >= 2) {
+            int t = ((z / tg.TZ) * tg.nty + y / tg.TY) * tg.ntx + x / tg.TX;
+            act[t] = 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// step II: plateau distances (cooperative, device-wide rounds)
+// ---------------------------------------------------------------------------
+
+template <typename T, int CONN>
+static __global__ void __launch_bounds__(NTHR) k_plateau(const T *__restrict__ g, Geo geo, TileGeo tg,
+                                                  int32_t *dist, uint8_t *act, DevStatus *status,
+                                                  int round_cap, unsigned long long timeout_ns)
+{
+    using PT = PTile<CONN>;
+    __shared__ int gs[PT::HS];
+    __shared__ int ds[PT::HS];
+    __shared__ int flag_s;
+    const int tid = threadIdx.x;
+    uint8_t *act0 = act, *act1 = act + tg.ntiles;
+
+    for (int r = 0;; r++) {
+        uint8_t *cur = (r & 1) ? act1 : act0;
+        uint8_t *nxt = (r & 1) ? act0 : act1;
+        if (blockIdx.x == 0 && tid == 0) status->changed[(r + 1) % 3] = 0;
+        for (int t = blockIdx.x; t < tg.ntiles; t += gridDim.x) {
+            __syncthreads();
+            if (tid == 0) {
+                flag_s = *(volatile uint8_t *)(cur + t);
+                if (flag_s) cur[t] = 0;
+            }
+            __syncthreads();
+            if (!flag_s) continue;
+            const int tx = t % tg.ntx, ty = (t / tg.ntx) % tg.nty, tz = t / (tg.ntx * tg.nty);
+            const int x0 = tx * PT::TX - 1, y0 = ty * PT::TY - 1, z0 = PT::ND == 2 ? 0 : tz * PT::TZ - 1;
+            for (int i = tid; i < PT::HS; i += NTHR) {
+                int hx = i % PT::HX, hy = (i / PT::HX) % PT::HY, hz = i / (PT::HX * PT::HY);
+                int x = x0 + hx, y = y0 + hy, z = z0 + hz;
+                if (x >= 0 && x < geo.W && y >= 0 && y < geo.H && z >= 0 && z < geo.D) {
+                    int q = (z * geo.H + y) * geo.W + x;
+                    gs[i] = (int)g[q];
+                    ds[i] = __ldcg(dist + q);
+                } else {
+                    gs[i] = -1;
+                    ds[i] = INF_D;
+                }
+            }
+            __syncthreads();
+            int orig[PT::PER_THR];
+#pragma unroll
+            for (int k = 0; k < PT::PER_THR; k++) {
+                int i = tid + k * NTHR;
+                int lx = i % PT::TX, ly = (i / PT::TX) % PT::TY, lz = i / (PT::TX * PT::TY);
+                int h = ((lz + (PT::ND == 3)) * PT::HY + ly + 1) * PT::HX + lx + 1;
+                orig[k] = ds[h];
+            }
+            // in-tile relaxation to the fixpoint (halo frozen)
+            for (int it = 0; it < 4 * PT::NPIX + 8; it++) {
+                int ch = 0;
+#pragma unroll
+                for (int k = 0; k < PT::PER_THR; k++) {
+                    int i = tid + k * NTHR;
+                    int lx = i % PT::TX, ly = (i / PT::TX) % PT::TY, lz = i / (PT::TX * PT::TY);
+                    int h = ((lz + (PT::ND == 3)) * PT::HY + ly + 1) * PT::HX + lx + 1;
+                    int gv = gs[h];
+                    int d = ds[h];
+                    if (gv < 0 || d == 0) continue;
+                    int best = d;
+#pragma unroll
+                    for (int n = 0; n < Nb<CONN>::n; n++) {
+                        int hn = h + (Nb<CONN>::dz(n) * PT::HY + Nb<CONN>::dy(n)) * PT::HX + Nb<CONN>::dx(n);
+                        if (gs[hn] == gv) best = imin(best, ds[hn] + 1);
+                    }
+                    if (best < d) {
+                        ds[h] = best;
+                        ch = 1;
+                    }
+                }
+                if (!__syncthreads_or(ch)) break;
+            }
+            int border = 0;
+#pragma unroll
+            for (int k = 0; k < PT::PER_THR; k++) {
+                int i = tid + k * NTHR;
+                int lx = i % PT::TX, ly = (i / PT::TX) % PT::TY, lz = i / (PT::TX * PT::TY);
+                int h = ((lz + (PT::ND == 3)) * PT::HY + ly + 1) * PT::HX + lx + 1;
+                if (ds[h] != orig[k]) {
+                    int x = x0 + 1 + lx, y = y0 + 1 + ly, z = z0 + (PT::ND == 3) + lz;
+                    __stcg(dist + (z * geo.H + y) * geo.W + x, ds[h]);
+                    if (lx == 0 || lx == PT::TX - 1 || ly == 0 || ly == PT::TY - 1 ||
+                        (PT::ND == 3 && (lz == 0 || lz == PT::TZ - 1)))
+                        border = 1;
+                }
+            }
+            if (__syncthreads_or(border) && tid == 0) {
+                for (int dz = (PT::ND == 3 ? -1 : 0); dz <= (PT::ND == 3 ? 1 : 0); dz++)
+                    for (int dy = -1; dy <= 1; dy++)
+                        for (int dx = -1; dx <= 1; dx++) {
+                            int ax = tx + dx, ay = ty + dy, az = tz + dz;
+                            if (ax < 0 || ax >= tg.ntx || ay < 0 || ay >= tg.nty || az < 0 || az >= tg.ntz)
+                                continue;
+                            if (dx == 0 && dy == 0 && dz == 0) continue;
+                            nxt[(az * tg.nty + ay) * tg.ntx + ax] = 1;
+                        }
+                atomicAdd(&status->changed[r % 3], 1);
+            }
+        }
+        __threadfence();
+        if (!grid_barrier(status, timeout_ns)) return;
+        int any = *(volatile int *)&status->changed[r % 3];
+        if (any == 0) {
+            if (blockIdx.x == 0 && tid == 0) status->rounds_plateau = r + 1;
+            return;
+        }
+        if (r + 1 >= round_cap) {
+            if (blockIdx.x == 0 && tid == 0) record_error(status, DEV_NONCONVERGED, 2);
+            return;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// step II pointer choice + step IV Union
+// ---------------------------------------------------------------------------
+
+static __device__ __forceinline__ int uf_find(int32_t *par, int a)
+{
+    volatile int32_t *vp = par;
+    for (;;) {
+        int b = vp[a];
+        if (b == a) return a;
+        int c = vp[b];
+        if (c == b) return b;
+        vp[a] = c;  // path halving: c is an ancestor of a
+        a = c;
+    }
+}
+
+static __device__ __forceinline__ void uf_union(int32_t *par, int a, int b, DevStatus *s)
+{
+    for (int it = 0; it < (1 << 20); it++) {
+        a = uf_find(par, a);
+        b = uf_find(par, b);
+        if (a == b) return;
+        if (a < b) {
+            int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(par + a, a, b) == a) return;
+    }
+    record_error(s, DEV_NONCONVERGED, 4);
+}
+
+template <typename T, int CONN>
+static __global__ void __launch_bounds__(NTHR) k_resolve_union(const T *__restrict__ g, Geo geo, int32_t *par,
+                                                        const uint8_t *__restrict__ st,
+                                                        const int32_t *__restrict__ dist, DevStatus *status)
+{
+    for (int p = blockIdx.x * NTHR + threadIdx.x; p < geo.N; p += gridDim.x * NTHR) {
+        if (st[p] < 2) continue;
+        int x, y, z;
+        coords(geo, p, x, y, z);
+        const unsigned gp = g[p];
+        const int d = dist[p];
+        if (d < INF_D) {
+            // non-minimal plateau: drain to the largest-index equal neighbour one step closer
+            int best = -1;
+#pragma unroll
+            for (int i = 0; i < Nb<CONN>::n; i++) {
+                int q;
+                if (!nb_at<CONN>(geo, x, y, z, i, q)) continue;
+                if (g[q] == gp && dist[q] == d - 1 && q > best) best = q;
+            }
+            par[p] = best;
+        } else {
+            // minimal plateau: Union with equal-valued minimal-plateau neighbours q > p
+#pragma unroll
+            for (int i = Half<CONN>::first; i < Nb<CONN>::n; i++) {
+                int q;
+                if (!nb_at<CONN>(geo, x, y, z, i, q)) continue;
+                if (st[q] >= 2 && dist[q] >= INF_D && g[q] == gp) uf_union(par, p, q, status);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// step III pointer jumping (cooperative) + smallest pixel index per basin
+// ---------------------------------------------------------------------------
+
+static __global__ void __launch_bounds__(NTHR) k_jump(int N, int32_t *par, int32_t *mi, int RR, DevStatus *status,
+                                               int round_cap, unsigned long long timeout_ns)
+{
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    for (int r = 0;; r++) {
+        if (blockIdx.x == 0 && tid == 0) status->changed[(r + 1) % 3] = 0;
+        int ch = 0;
+        for (int p = blockIdx.x * NTHR + tid; p < N; p += gridDim.x * NTHR) {
+            if (r == 0) mi[p] = 0x7fffffff;
+            int l0 = __ldcg(par + p);
+            int l = l0;
+            for (int i = 0; i < RR; i++) {
+                int l2 = __ldcg(par + l);
+                if (l2 == l) break;
+                l = l2;
+            }
+            if (l != l0) {
+                __stcg(par + p, l);
+                ch = 1;
+            }
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, ch);
+        if (lane == 0 && bal) atomicAdd(&status->changed[r % 3], 1);
+        __threadfence();
+        if (!grid_barrier(status, timeout_ns)) return;
+        if (*(volatile int *)&status->changed[r % 3] == 0) {
+            if (blockIdx.x == 0 && tid == 0) status->rounds_jump = r + 1;
+            break;
+        }
+        if (r + 1 >= round_cap) {
+            if (blockIdx.x == 0 && tid == 0) record_error(status, DEV_NONCONVERGED, 5);
+            return;
+        }
+    }
+    // every pixel now points at its basin's root; record the smallest index
+    for (int p = blockIdx.x * NTHR + tid; p < N; p += gridDim.x * NTHR) {
+        int r = __ldcg(par + p);
+        unsigned grp = __match_any_sync(__activemask(), r);
+        int leader = __ffs(grp) - 1;
+        if (lane == leader) atomicMin(mi + r, p);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// canonical compaction
+// ---------------------------------------------------------------------------
+
+constexpr int CHUNK = NTHR * 8;   // pixels per CTA in the compaction kernels
+
+// F[p] = 1 iff p is the smallest pixel of its basin; per-chunk counts.
+static __global__ void __launch_bounds__(NTHR) k_flags(int N, const int32_t *__restrict__ par,
+                                                const int32_t *__restrict__ mi, uint8_t *__restrict__ F,
+                                                int32_t *__restrict__ blk)
+{
+    const int base = blockIdx.x * CHUNK;
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        int p = base + j * NTHR + threadIdx.x;
+        if (p < N) {
+            int f = mi[par[p]] == p;
+            F[p] = (uint8_t)f;
+            cnt += f;
+        }
+    }
+    __shared__ int red[NTHR / 32];
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < NTHR / 32; w++) s += red[w];
+        blk[blockIdx.x] = s;
+    }
+}
+
+// Exclusive scan of blk[0..n) in place, total to blk[n] (one CTA of 1024).
+static __global__ void __launch_bounds__(1024) k_scan(int32_t *blk, int n, int32_t *total_out)
+{
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < n; base += 1024) {
+        int i = base + threadIdx.x;
+        int v = i < n ? blk[i] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int s = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;
+        }
+        __syncthreads();
+        int excl = carry + (wid ? wsum[wid - 1] : 0) + x - v;
+        if (i < n) blk[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += wsum[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        blk[n] = carry;
+        if (total_out) *total_out = carry;
+    }
+}
+
+// id[root] = rank of the basin's smallest pixel among all basins' smallest pixels.
+static __global__ void __launch_bounds__(NTHR) k_assign(int N, const int32_t *__restrict__ par, int32_t *mi,
+                                                 const uint8_t *__restrict__ F, const int32_t *__restrict__ blk)
+{
+    __shared__ int wsum[NTHR / 32];
+    __shared__ int carry;
+    const int base = blockIdx.x * CHUNK;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = blk[blockIdx.x];
+    __syncthreads();
+    for (int j = 0; j < 8; j++) {
+        int p = base + j * NTHR + threadIdx.x;
+        int f = (p < N) ? F[p] : 0;
+        unsigned b = __ballot_sync(0xffffffffu, f);
+        int before = __popc(b & ((1u << lane) - 1u));
+        if (lane == 0) wsum[wid] = __popc(b);
+        __syncthreads();
+        int off = carry;
+        for (int w = 0; w < wid; w++) off += wsum[w];
+        if (f) mi[par[p]] = off + before;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int s = 0;
+            for (int w = 0; w < NTHR / 32; w++) s += wsum[w];
+            carry += s;
+        }
+        __syncthreads();
+    }
+}
+
+static __global__ void __launch_bounds__(NTHR) k_label(int N, const int32_t *__restrict__ par,
+                                                const int32_t *__restrict__ mi, int32_t *__restrict__ labels)
+{
+    for (int p = blockIdx.x * NTHR + threadIdx.x; p < N; p += gridDim.x * NTHR) labels[p] = mi[par[p]];
+}
+
+// Step II distances as reported by ws_plateau_distance (-1 = no distance).
+static __global__ void __launch_bounds__(NTHR) k_dist_out(int N, const int32_t *__restrict__ d, int32_t *__restrict__ out)
+{
+    for (int p = blockIdx.x * NTHR + threadIdx.x; p < N; p += gridDim.x * NTHR) {
+        int v = d[p];
+        out[p] = v >= INF_D ? -1 : v;
+    }
+}
+
+static __global__ void k_copy_int(const int32_t *src, int32_t *dst)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = *src;
+}
+
+// ---------------------------------------------------------------------------
+// waterfall: region adjacency (Alg. 5 step V on pixel pairs)
+// ---------------------------------------------------------------------------
+
+static __device__ __forceinline__ unsigned long long mix64(unsigned long long k)
+{
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+static __device__ __forceinline__ void edge_insert(unsigned long long key, unsigned h, unsigned long long *keys,
+                                            uint32_t *vals, int32_t *slots, int32_t *ecount,
+                                            unsigned long long mask, DevStatus *status)
+{
+    unsigned long long s = mix64(key) & mask;
+    for (int probe = 0; probe < 4096; probe++) {
+        unsigned long long k = *(volatile unsigned long long *)(keys + s);
+        if (k == key) {
+            atomicMin(vals + s, h);
+            return;
+        }
+        if (k == EMPTY_KEY) {
+            unsigned long long old = atomicCAS(keys + s, EMPTY_KEY, key);
+            if (old == EMPTY_KEY) {
+                int idx = atomicAdd(ecount, 1);
+                slots[idx] = (int32_t)s;
+                atomicMin(vals + s, h);
+                return;
+            }
+            if (old == key) {
+                atomicMin(vals + s, h);
+                return;
+            }
+        }
+        s = (s + 1) & mask;
+    }
+    record_error(status, DEV_EDGE_TABLE_FULL, 6);
+}
+
+template <typename T, int CONN>
+static __global__ void __launch_bounds__(NTHR) k_rag(const T *__restrict__ g, Geo geo, const int32_t *__restrict__ L,
+                                              unsigned long long *keys, uint32_t *vals, int32_t *slots,
+                                              int32_t *ecount, unsigned long long mask, DevStatus *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * NTHR;
+    const int nIter = (geo.N + stride - 1) / stride;
+    for (int it = 0; it < nIter; it++) {
+        int p = it * stride + blockIdx.x * NTHR + threadIdx.x;
+        bool in = p < geo.N;
+        int x = 0, y = 0, z = 0, A = 0;
+        unsigned gp = 0;
+        if (in) {
+            coords(geo, p, x, y, z);
+            A = L[p];
+            gp = g[p];
+        }
+#pragma unroll
+        for (int i = Half<CONN>::first; i < Nb<CONN>::n; i++) {
+            int q;
+            bool has = false;
+            unsigned long long key = 0;
+            unsigned h = 0;
+            if (in && nb_at<CONN>(geo, x, y, z, i, q)) {
+                int B = L[q];
+                if (B != A) {
+                    has = true;
+                    int a = imin(A, B), b = imax(A, B);
+                    key = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
+                    unsigned gq = g[q];
+                    h = gp > gq ? gp : gq;
+                }
+            }
+            unsigned m = __ballot_sync(0xffffffffu, has);
+            if (!has) continue;
+            unsigned grp = __match_any_sync(m, key);
+            unsigned hmin = __reduce_min_sync(grp, h);
+            if (lane == __ffs(grp) - 1) edge_insert(key, hmin, keys, vals, slots, ecount, mask, status);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// waterfall: lowest-pass merging on the region graph (cooperative)
+// ---------------------------------------------------------------------------
+
+static __device__ __forceinline__ int block_sum(int v, int *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+    return s;
+}
+
+static __global__ void __launch_bounds__(NTHR) k_levels(const unsigned long long *__restrict__ keys,
+                                                 const uint32_t *__restrict__ vals,
+                                                 const int32_t *__restrict__ slots, const int32_t *ecount,
+                                                 const int32_t *k0_ptr, int NL, int32_t *gmap, size_t kstride,
+                                                 uint32_t *newmin, int32_t *uf, int32_t *rank, int32_t *bsum,
+                                                 int32_t *counts, DevStatus *status,
+                                                 unsigned long long timeout_ns)
+{
+    __shared__ int red[NTHR / 32];
+    __shared__ int carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int gsz = gridDim.x * NTHR;
+    const int E = *ecount;
+    const int K0 = *k0_ptr;
+    if (blockIdx.x == 0 && tid == 0 && counts) counts[0] = K0;
+    int Kk = K0;
+    for (int k = 0; k + 1 < NL; k++) {
+        const int32_t *gm = k == 0 ? nullptr : gmap + (size_t)(k - 1) * kstride;
+        int32_t *gout = gmap + (size_t)k * kstride;
+        // A: reset
+        for (int a = blockIdx.x * NTHR + tid; a < Kk; a += gsz) {
+            newmin[a] = 0xffffffffu;
+            uf[a] = a;
+        }
+        if (!grid_barrier(status, timeout_ns)) return;
+        // B: newmin(A) = lowest pass of A
+        for (int e = blockIdx.x * NTHR + tid; e < E; e += gsz) {
+            int s = slots[e];
+            unsigned long long key = keys[s];
+            int a0 = (int)(key >> 32), b0 = (int)(key & 0xffffffffu);
+            unsigned h = vals[s];
+            int A = gm ? __ldcg(gm + a0) : a0, B = gm ? __ldcg(gm + b0) : b0;
+            if (A != B) {
+                atomicMin(newmin + A, h);
+                atomicMin(newmin + B, h);
+            }
+        }
+        if (!grid_barrier(status, timeout_ns)) return;
+        // C: Union across every edge that is the lowest pass of one endpoint
+        for (int e = blockIdx.x * NTHR + tid; e < E; e += gsz) {
+            int s = slots[e];
+            unsigned long long key = keys[s];
+            int a0 = (int)(key >> 32), b0 = (int)(key & 0xffffffffu);
+            unsigned h = vals[s];
+            int A = gm ? __ldcg(gm + a0) : a0, B = gm ? __ldcg(gm + b0) : b0;
+            if (A != B && (h == __ldcg(newmin + A) || h == __ldcg(newmin + B))) uf_union(uf, A, B, status);
+        }
+        if (!grid_barrier(status, timeout_ns)) return;
+        // D: flatten; count roots per contiguous chunk (order-preserving scan)
+        const int chunk = (Kk + gridDim.x - 1) / gridDim.x;
+        const int c0 = blockIdx.x * chunk, c1 = min(Kk, c0 + chunk);
+        int cnt = 0;
+        for (int a = c0 + tid; a < c1; a += NTHR) {
+            int r = uf_find(uf, a);
+            cnt += (r == a);
+        }
+        int tot = block_sum(cnt, red);
+        if (tid == 0) bsum[blockIdx.x] = tot;
+        if (!grid_barrier(status, timeout_ns)) return;
+        // E: ranks of the roots (roots = smallest level-k id of each new region)
+        int off = 0, all = 0;
+        for (int b = tid; b < (int)gridDim.x; b += NTHR) {
+            int v = *(volatile int *)(bsum + b);
+            all += v;
+            if (b < (int)blockIdx.x) off += v;
+        }
+        off = block_sum(off, red);
+        all = block_sum(all, red);
+        if (tid == 0) carry = off;
+        __syncthreads();
+        for (int a0 = c0; a0 < c1; a0 += NTHR) {
+            int a = a0 + tid;
+            int isr = 0;
+            if (a < c1) isr = uf_find(uf, a) == a;
+            unsigned b = __ballot_sync(0xffffffffu, isr);
+            __syncthreads();
+            if (lane == 0) red[wid] = __popc(b);
+            __syncthreads();
+            int o = carry;
+            for (int w = 0; w < wid; w++) o += red[w];
+            if (isr) rank[a] = o + __popc(b & ((1u << lane) - 1u));
+            __syncthreads();
+            if (tid == 0) {
+                int s = 0;
+                for (int w = 0; w < NTHR / 32; w++) s += red[w];
+                carry += s;
+            }
+            __syncthreads();
+        }
+        if (blockIdx.x == 0 && tid == 0 && counts) counts[k + 1] = all;
+        if (!grid_barrier(status, timeout_ns)) return;
+        // F: compose the level-0 -> level-(k+1) map
+        for (int c = blockIdx.x * NTHR + tid; c < K0; c += gsz) {
+            int A = gm ? __ldcg(gm + c) : c;
+            gout[c] = __ldcg(rank + uf_find(uf, A));
+        }
+        Kk = all;
+        if (!grid_barrier(status, timeout_ns)) return;
+    }
+}
+
+static __global__ void __launch_bounds__(NTHR) k_level_write(int N, const int32_t *__restrict__ L0,
+                                                      const int32_t *__restrict__ gmap, size_t kstride,
+                                                      int nlev, int32_t *__restrict__ out)
+{
+    for (int p = blockIdx.x * NTHR + threadIdx.x; p < N; p += gridDim.x * NTHR) {
+        int c = L0[p];
+        for (int k = 0; k < nlev; k++) __stcs(out + (size_t)k * N + p, gmap[(size_t)k * kstride + c]);
+    }
+}
+
+static __global__ void __launch_bounds__(NTHR) k_hash_clear(unsigned long long *keys, uint32_t *vals,
+                                                     const int32_t *slots, int32_t *ecount)
+{
+    const int E = *ecount;
+    for (int e = blockIdx.x * NTHR + threadIdx.x; e < E; e += gridDim.x * NTHR) {
+        int s = slots[e];
+        keys[s] = EMPTY_KEY;
+        vals[s] = 0xffffffffu;
+    }
+}
+
+static __global__ void k_reset_count(int32_t *ecount, DevStatus *status)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        status->edges = *ecount;
+        *ecount = 0;
+    }
+}
+
+}  // namespace ws
