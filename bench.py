@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark of the watershed + waterfall hot path (arXiv 2410.08946) on GB300.
+
+Workload (one "step"): the whole hierarchy -- watershed steps I-IV plus the
+waterfall up to NL = 6 levels -- of a 928 x 928 x 928 (799,178,752 voxel)
+uint16 gradient volume, 6-connectivity.  The volume is the seeded synthetic
+stand-in for the paper's 800-megavoxel MicroCT image: distance to the nearest
+of 50,000 random seed points scaled to [0, 65535], plus uniform noise
+U{0..64}.  Inputs (1.6 GB) and outputs (19.2 GB) are far larger than L2, so
+no cache flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  Keys:
+  value / unit        Gvoxels processed per second, device-resident input
+  e2e                 the same through ws_segment_host (pinned host buffers,
+                      host<->device copies inside the timed region)
+  roofline            the dominant kernel phase: algorithmic bytes per launch
+                      / its CUDA-event time, against the measured HBM peak
+  path_roofline       the whole step: (2 + 4 NL) bytes per voxel / step time
+  cpu_baseline        the CPU oracle (1 thread) on a bounded sample volume
+  phases_ms           per-phase device time per step (CUDA events)
+  gpu_launches        kernels libws enqueued per timed step
+  clocks              nvidia-smi samples taken during the timed region
+--impl reference times the CPU oracle itself (the reference arm).
+Multi-GPU (torchrun): replicas, one volume per rank, no collective on the
+data path ("weak" scaling); value = voxels of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "watershed+waterfall Gvox/s & %HBM roofline; served p50/p99 ms vs per-image"
+SIDE, SEEDS, NL, CONN = 928, 50000, 6, 6
+SEED = 2410089460 + 2
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic bytes per voxel of each phase (minimal input + output of the
+# function the phase computes; b = 2 bytes per uint16 sample).
+PHASE_BYTES = {
+    "step1": 2 + 4,            # read G, write the arrow
+    "jump": 4 + 4,             # read arrows, write roots
+    "compact": 4 + 4,          # read roots, write canonical labels
+    "rag": 4 + 2,              # read labels and G
+    "level_write": 4 + 4 * (NL - 1),   # read L0, write NL-1 planes
+    "resolve_union": 2 + 4,    # read G (plateau pixels), write arrows
+    "plateau": 2 + 4,
+}
+KERNEL_OF_PHASE = {"step1": "k_step1", "plateau": "k_plateau", "resolve_union": "k_resolve_union",
+                   "jump": "k_jump", "compact": "k_flags/k_scan/k_assign/k_label", "rag": "k_rag",
+                   "levels": "k_levels", "level_write": "k_level_write", "cleanup": "k_hash_clear"}
+
+
+def workload_name(side):
+    return (f"3D {side}x{side}x{side} uint16 distance-to-{SEEDS if side == SIDE else 'scaled'}-seeds + "
+            f"U{{0..64}} noise, 6-connectivity, watershed + waterfall NL={NL}")
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def sample_seeds(side):
+    return max(16, round(SEEDS * side ** 3 / SIDE ** 3))
+
+
+class ClockSampler:
+    """nvidia-smi clocks + throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel source has not changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2410_08946_gb300", "csrc", "ws_kernels.cuh")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = rec.get(kernel)
+    if not ent or ent.get("source_sha") != h:
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def cpu_baseline(side=320):
+    """The oracle as it stands (one thread) on a bounded sample volume."""
+    import oracle
+    from paper_2410_08946_gb300 import synth
+    n = sample_seeds(side)
+    vol = synth.distance_volume(side, side, side, n, seed=SEED)
+    t0 = time.perf_counter()
+    oracle.segment(vol, CONN, NL)
+    dt = time.perf_counter() - t0
+    return {"value": side ** 3 / dt / 1e9, "unit": "Gvox/s", "cores": 1, "kind": "oracle",
+            "sample": f"{side}^3 uint16 distance volume, {n} seeds (same density as 928^3 / 50,000), "
+                      f"watershed + waterfall NL={NL}, one oracle run of {dt:.1f} s on 1 of "
+                      f"{os.cpu_count()} host cores ({os.uname().machine})"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the host cores, bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2410_08946_gb300 import synth
+    side = args.ref_side
+    n = sample_seeds(side)
+    vol = synth.distance_volume(side, side, side, n, seed=SEED)
+    for _ in range(args.warmup):
+        oracle.segment(vol, CONN, NL)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.segment(vol, CONN, NL)
+        times.append(time.perf_counter() - t0)
+    dt = sum(times) / len(times)
+    value = side ** 3 / dt / 1e9
+    sample = (f"{side}^3 uint16 distance volume, {n} seeds (same density as 928^3 / 50,000); "
+              f"one oracle run per step on 1 of {os.cpu_count()} host cores ({os.uname().machine})")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gvox/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": workload_name(SIDE), "sample_side": side, "l2": "not applicable (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "Gvox/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Gvox/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=SIDE, help="cube side (default 928)")
+    ap.add_argument("--ref-side", type=int, default=192, help="sample side of the reference arm")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    from paper_2410_08946_gb300 import binding, synth
+    if not os.path.exists(binding.LIB_PATH):
+        __graft_entry__.build()
+
+    side = args.side
+    n_seeds = sample_seeds(side) if side != SIDE else SEEDS
+    vol = synth.distance_volume(side, side, side, n_seeds, seed=SEED)
+    N = vol.size
+    grad_d = torch.from_numpy(vol).cuda()
+    levels_d = torch.empty((NL,) + vol.shape, dtype=torch.int32, device="cuda")
+    counts_d = torch.empty(NL, dtype=torch.int32, device="cuda")
+    ctx = binding.Context(local)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.segment(grad_d, CONN, NL, levels_d, counts_d)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.check()
+    ctx.phase_times()                      # discard
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    sampler.start()
+    time.sleep(0.3)
+    ctx.set_profiling(True)
+    l0 = ctx.launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    launches = (ctx.launches() - l0) / args.steps
+    ctx.check()
+    phases = ctx.phase_times()
+    ctx.set_profiling(False)
+    clocks = sampler.stop()
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms = ms_total / args.steps
+    value = N * world / (ms / 1e3) / 1e9
+    counts = counts_d.cpu().tolist()
+
+    peak, peak_src = hbm_peak()
+    per_step = {k: v[0] / args.steps for k, v in phases.items() if v[1]}
+    dom = max((k for k in per_step if k in PHASE_BYTES), key=lambda k: per_step[k])
+    dom_launches = phases[dom][1] / args.steps
+    dom_ms = per_step[dom] / max(dom_launches, 1)
+    alg = PHASE_BYTES[dom] * N
+    achieved = alg / (dom_ms / 1e3) / 1e9
+    kern = KERNEL_OF_PHASE.get(dom, dom)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_for(kern), "kernel": kern, "phase": dom,
+                "alg_bytes_per_launch": alg, "peak_source": f"{peak_src} (copy, MEASURED_PEAKS.json hbm_gbs)"
+                if peak_src == "measured" else "fallback 6.8 TB/s"}
+    path_bytes = (2 + 4 * NL) * N
+    path_achieved = path_bytes / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "Gvox/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": workload_name(side), "voxels": N, "NL": NL, "connectivity": CONN,
+                       "levels_counts": counts, "l2": "inputs (1.6 GB) and outputs (19.2 GB) larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "path_roofline": {"bytes_per_voxel": 2 + 4 * NL, "achieved": path_achieved, "peak": peak,
+                              "unit": "GB/s", "frac": path_achieved / peak},
+            "phases_ms": {k: round(v, 4) for k, v in per_step.items()},
+            "gpu_launches": launches, "clocks": clocks}
+
+    if not args.no_e2e:
+        grad_h = torch.from_numpy(vol).pin_memory()
+        levels_h = torch.empty((NL,) + vol.shape, dtype=torch.int32).pin_memory()
+        counts_h = torch.empty(NL, dtype=torch.int32)
+        ctx.segment_host(grad_h, CONN, NL, levels_h, counts_h)       # warm the staging buffers
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.segment_host(grad_h, CONN, NL, levels_h, counts_h)
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        line["e2e"] = {"value": N * world / e2e_s / 1e9, "unit": "Gvox/s", "ms_per_step": e2e_s * 1e3,
+                       "h2d_bytes_per_step": int(N * 2), "d2h_bytes_per_step": int(NL * N * 4 + NL * 4)}
+        del grad_h, levels_h
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

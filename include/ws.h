@@ -114,6 +114,26 @@ ws_status ws_context_set_tuning(ws_context *ctx, const ws_tuning *t);
 size_t ws_context_workspace_bytes(const ws_context *ctx);
 
 /* ------------------------------------------------------------------------ */
+/* tracing                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Turns per-phase CUDA-event timing on (enable != 0) or off.  When on, every
+ * phase a call enqueues is bracketed by two events on the call's stream. */
+ws_status ws_context_set_profiling(ws_context *ctx, int enable);
+
+/* Number of timed phases, and the name of phase i ("step1", "plateau", ...). */
+int ws_phase_count(void);
+const char *ws_phase_name(int phase);
+
+/* Waits for the events recorded since the last call, then writes the summed
+ * device time (ms) and the number of timed instances of each phase into
+ * total_ms[0..n) and calls[0..n) (either may be NULL) and resets the sums. */
+ws_status ws_context_phase_times(ws_context *ctx, double *total_ms, long long *calls, int n);
+
+/* Number of CUDA kernels this context has enqueued since it was created. */
+unsigned long long ws_context_launches(const ws_context *ctx);
+
+/* ------------------------------------------------------------------------ */
 /* hot path                                                                  */
 /* ------------------------------------------------------------------------ */
 

@@ -46,7 +46,7 @@ _lock = threading.Lock()
 def declared_symbols(header: str = HEADER):
     """Names of the functions include/ws.h declares."""
     txt = open(header).read()
-    return sorted(set(re.findall(r"^\s*(?:ws_status|void|const char \*|size_t)\s*\*?\s*(ws_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:ws_status|void|const char \*|size_t|int|unsigned long long)\s*\*?\s*(ws_\w+)\s*\(",
                                  txt, flags=re.M)))
 
 
@@ -75,6 +75,11 @@ def load(path: str = LIB_PATH):
             "ws_segment_host": ([P, P, I, SH, I, I, P, P, P], I),
             "ws_step1": ([P, P, I, SH, I, P, P, P], I),
             "ws_plateau_distance": ([P, P, I, SH, I, P, P], I),
+            "ws_context_set_profiling": ([P, I], I),
+            "ws_phase_count": ([], I),
+            "ws_phase_name": ([I], ctypes.c_char_p),
+            "ws_context_phase_times": ([P, P, P, I], I),
+            "ws_context_launches": ([P], ctypes.c_ulonglong),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -168,6 +173,21 @@ class Context:
 
     def workspace_bytes(self) -> int:
         return int(self.lib.ws_context_workspace_bytes(self.handle))
+
+    def set_profiling(self, on: bool = True):
+        self._ok(self.lib.ws_context_set_profiling(self.handle, 1 if on else 0))
+
+    def phase_times(self):
+        """{phase name: (total ms, instances)} since the last call (waits for the events)."""
+        n = int(self.lib.ws_phase_count())
+        ms = (ctypes.c_double * n)()
+        calls = (ctypes.c_longlong * n)()
+        self._ok(self.lib.ws_context_phase_times(self.handle, ms, calls, n))
+        return {self.lib.ws_phase_name(i).decode(): (ms[i], calls[i]) for i in range(n)}
+
+    def launches(self) -> int:
+        """Kernels this context has enqueued so far."""
+        return int(self.lib.ws_context_launches(self.handle))
 
     # -- entry points -------------------------------------------------------
     def gradient(self, img, quant_shift: int = 0, out=None, stream=None):

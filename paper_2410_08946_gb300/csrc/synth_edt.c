@@ -163,6 +163,38 @@ int synth_edt3d(int64_t W, int64_t H, int64_t D, const int64_t *seeds, int64_t n
     return 0;
 }
 
+typedef struct {
+    const uint32_t *d2;
+    uint16_t *out;
+    int64_t i0, i1;
+    uint64_t d2max, key;
+    int noise_levels;
+    uint64_t local_max;
+} conv_t;
+
+static void *run_max(void *arg)
+{
+    conv_t *c = (conv_t *)arg;
+    uint64_t m = 0;
+    for (int64_t i = c->i0; i < c->i1; i++)
+        if (c->d2[i] > m) m = c->d2[i];
+    c->local_max = m;
+    return NULL;
+}
+
+static void *run_convert(void *arg)
+{
+    conv_t *c = (conv_t *)arg;
+    const uint64_t full = 65535ull * 65535ull;
+    for (int64_t i = c->i0; i < c->i1; i++) {
+        uint64_t base = isqrt64((uint64_t)c->d2[i] * full / c->d2max);
+        uint64_t nz = c->noise_levels > 0 ? splitmix64(c->key + (uint64_t)i) % (uint64_t)c->noise_levels : 0;
+        uint64_t v = base + nz;
+        c->out[i] = (uint16_t)(v > 65535 ? 65535 : v);
+    }
+    return NULL;
+}
+
 /* Full volume generator (definition at the top of this file). */
 int synth_distance_volume(int64_t W, int64_t H, int64_t D, const int64_t *seeds, int64_t nseeds,
                           uint64_t noise_key, int noise_levels, uint16_t *out, int nthreads)
@@ -175,17 +207,30 @@ int synth_distance_volume(int64_t W, int64_t H, int64_t D, const int64_t *seeds,
         free(d2);
         return rc;
     }
-    uint64_t d2max = 0;
-    for (int64_t i = 0; i < N; i++)
-        if (d2[i] > d2max) d2max = d2[i];
-    if (d2max == 0) d2max = 1;
-    const uint64_t full = 65535ull * 65535ull;
-    for (int64_t i = 0; i < N; i++) {
-        uint64_t base = isqrt64((uint64_t)d2[i] * full / d2max);
-        uint64_t nz = noise_levels > 0 ? splitmix64(noise_key + (uint64_t)i) % (uint64_t)noise_levels : 0;
-        uint64_t v = base + nz;
-        out[i] = (uint16_t)(v > 65535 ? 65535 : v);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    conv_t jobs[256];
+    for (int t = 0; t < nthreads; t++) {
+        jobs[t].d2 = d2;
+        jobs[t].out = out;
+        jobs[t].i0 = N * t / nthreads;
+        jobs[t].i1 = N * (t + 1) / nthreads;
+        jobs[t].key = noise_key;
+        jobs[t].noise_levels = noise_levels;
+        pthread_create(&th[t], NULL, run_max, &jobs[t]);
     }
+    uint64_t d2max = 0;
+    for (int t = 0; t < nthreads; t++) {
+        pthread_join(th[t], NULL);
+        if (jobs[t].local_max > d2max) d2max = jobs[t].local_max;
+    }
+    if (d2max == 0) d2max = 1;
+    for (int t = 0; t < nthreads; t++) {
+        jobs[t].d2max = d2max;
+        pthread_create(&th[t], NULL, run_convert, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
     free(d2);
     return 0;
 }

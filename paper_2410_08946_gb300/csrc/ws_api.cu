@@ -134,6 +134,44 @@ ws_status ensure_regions(ws_context *c, size_t kmax, int levels)
     return WS_OK;
 }
 
+static cudaEvent_t prof_event(ws_context *c)
+{
+    if (!c->prof.pool.empty()) {
+        cudaEvent_t e = c->prof.pool.back();
+        c->prof.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+PhaseScope::PhaseScope(ws_context *c_, int ph_, cudaStream_t s_) : c(c_), ph(ph_), s(s_)
+{
+    if (!c->prof.on) return;
+    a = prof_event(c);
+    if (a) cudaEventRecord(a, s);
+}
+
+PhaseScope::~PhaseScope()
+{
+    if (!a) return;
+    cudaEvent_t b = prof_event(c);
+    if (!b) {
+        c->prof.pool.push_back(a);
+        return;
+    }
+    cudaEventRecord(b, s);
+    c->prof.pending.push_back({ph, a, b});
+}
+
+static const char *const PHASE_NAMES[NPHASE] = {"step1",       "plateau", "resolve_union", "jump",
+                                                "compact",     "rag",     "levels",        "level_write",
+                                                "cleanup",     "gradient", "copy"};
+
 const Launchers *launchers(int dtype, int conn)
 {
     if (dtype == WS_U8) return launchers_u8(conn);
@@ -246,6 +284,11 @@ void ws_context_destroy(ws_context *c)
                     w.uf, w.rank, w.bsum, w.kcount, w.grad_stage, w.levels_stage, w.counts_stage};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (auto &r : c->prof.pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->prof.pool) cudaEventDestroy(e);
     delete c;
 }
 
@@ -268,6 +311,8 @@ ws_status ws_context_check(ws_context *c, ws_stream_t stream)
     case 4: what = "Union retry cap reached"; break;
     case 5: what = "step III pointer jumping reached its round cap"; break;
     case 6: what = "region adjacency table full (raise ws_tuning.edge_capacity)"; break;
+    case 7: what = "step II found a plateau pixel with no neighbour one step closer"; break;
+    case 8: what = "level-0 labels out of range (expected canonical ids 0..K-1)"; break;
     case 100: what = "device-wide barrier timed out"; break;
     }
     snprintf(buf, sizeof buf, "%s (code %d, site %d)", what, h.code, h.where);
@@ -276,6 +321,49 @@ ws_status ws_context_check(ws_context *c, ws_stream_t stream)
 }
 
 const char *ws_last_error(const ws_context *c) { return c ? c->err.c_str() : "no context"; }
+
+ws_status ws_context_set_profiling(ws_context *c, int enable)
+{
+    if (!c) return WS_ERR_INVALID;
+    c->prof.on = enable != 0;
+    return WS_OK;
+}
+
+int ws_phase_count(void) { return NPHASE; }
+
+const char *ws_phase_name(int phase) { return (phase >= 0 && phase < NPHASE) ? PHASE_NAMES[phase] : ""; }
+
+ws_status ws_context_phase_times(ws_context *c, double *total_ms, long long *calls, int n)
+{
+    if (!c || n < 0) return WS_ERR_INVALID;
+    cudaSetDevice(c->device);
+    Prof &P = c->prof;
+    for (auto &r : P.pending) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.f;
+        }
+        P.total_ms[r.phase] += ms;
+        P.calls[r.phase] += 1;
+        P.pool.push_back(r.a);
+        P.pool.push_back(r.b);
+    }
+    P.pending.clear();
+    for (int i = 0; i < n && i < NPHASE; i++) {
+        if (total_ms) total_ms[i] = P.total_ms[i];
+        if (calls) calls[i] = P.calls[i];
+    }
+    for (int i = 0; i < NPHASE; i++) {
+        P.total_ms[i] = 0;
+        P.calls[i] = 0;
+    }
+    return WS_OK;
+}
+
+unsigned long long ws_context_launches(const ws_context *c) { return c ? c->launches : 0; }
 
 ws_status ws_context_set_tuning(ws_context *c, const ws_tuning *t)
 {
@@ -378,30 +466,40 @@ ws_status ws_segment_host(ws_context *c, const void *grad_h, ws_dtype dtype, con
     if (st) return st;
     if (!levels_h || NL < 1) return set_error(c, WS_ERR_INVALID, "NULL levels or NL < 1");
     Workspace &w = c->w;
-    // staging buffers, grown on demand: host_n = bytes of the levels buffer;
-    // the gradient buffer gets half of that (>= 2 bytes per pixel)
+    // staging buffers, grown on demand (host_n = bytes of the levels buffer,
+    // grad_n = bytes of the gradient buffer)
     size_t b = dtype == WS_U8 ? 1 : 2;
-    size_t levels_bytes = (size_t)NL * g.N * 4;
+    size_t levels_bytes = (size_t)NL * g.N * 4, grad_bytes = (size_t)g.N * b;
     if (levels_bytes > w.host_n) {
         dfree(c, &w.levels_stage, w.host_n);
-        dfree(c, &w.grad_stage, w.host_n / 2);
         w.host_n = 0;
-        if ((st = dalloc(c, &w.levels_stage, levels_bytes)) || (st = dalloc(c, &w.grad_stage, levels_bytes / 2)))
-            return st;
+        if ((st = dalloc(c, &w.levels_stage, levels_bytes))) return st;
         w.host_n = levels_bytes;
     }
-    if (g.N * b > w.host_n / 2) return set_error(c, WS_ERR_INVALID, "staging too small");
+    if (grad_bytes > w.grad_n) {
+        dfree(c, &w.grad_stage, w.grad_n);
+        w.grad_n = 0;
+        if ((st = dalloc(c, &w.grad_stage, grad_bytes))) return st;
+        w.grad_n = grad_bytes;
+    }
     if (!w.counts_stage && (st = dalloc(c, &w.counts_stage, 64 * 4))) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(w.grad_stage, grad_h, (size_t)g.N * b, cudaMemcpyHostToDevice, s);
+    cudaError_t e;
+    {
+        PhaseScope ps(c, PH_COPY, s);
+        e = cudaMemcpyAsync(w.grad_stage, grad_h, (size_t)g.N * b, cudaMemcpyHostToDevice, s);
+    }
     if (e != cudaSuccess) return set_cuda_error(c, e, "H2D copy");
     if ((st = L->watershed(c, w.grad_stage, g, w.levels_stage, nullptr, s))) return st;
     int32_t *cnt = NL <= 64 ? w.counts_stage : nullptr;
     if ((st = L->waterfall(c, w.levels_stage, w.grad_stage, g, NL, w.levels_stage + g.N, cnt, (size_t)g.N / 2 + 1, s)))
         return st;
-    e = cudaMemcpyAsync(levels_h, w.levels_stage, levels_bytes, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && counts_h && cnt)
-        e = cudaMemcpyAsync(counts_h, cnt, (size_t)NL * 4, cudaMemcpyDeviceToHost, s);
+    {
+        PhaseScope ps(c, PH_COPY, s);
+        e = cudaMemcpyAsync(levels_h, w.levels_stage, levels_bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && counts_h && cnt)
+            e = cudaMemcpyAsync(counts_h, cnt, (size_t)NL * 4, cudaMemcpyDeviceToHost, s);
+    }
     if (e != cudaSuccess) return set_cuda_error(c, e, "D2H copy");
     return ws_context_check(c, stream);
 }

@@ -17,6 +17,7 @@ enum : int {
     DEV_NONCONVERGED = 5,
     DEV_TIMEOUT = 6,
     DEV_EDGE_TABLE_FULL = 3,
+    DEV_BAD_LABELS = 1,
 };
 
 struct DevStatus {

@@ -88,7 +88,9 @@ ws_status launch_gradient(ws_context *c, const uint8_t *img, int W, int H, int s
                           cudaStream_t s)
 {
     dim3 grid((W + GTW - 1) / GTW, (H + GTH - 1) / GTH);
+    PhaseScope ps(c, PH_GRADIENT, s);
     k_gradient<<<grid, 256, 0, s>>>(img, W, H, shift, grad);
+    c->launches += 1;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "gradient launch");
 }
@@ -99,6 +101,7 @@ ws_status launch_count_labels(ws_context *c, const int32_t *labels, int N, cudaS
     if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
     int grid = c->num_sms * 8;
     k_max_label<<<grid, 256, 0, s>>>(labels, N, c->w.kcount);
+    c->launches += 1;
     e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "count launch");
 }

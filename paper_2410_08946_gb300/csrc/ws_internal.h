@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/ws.h"
 #include "ws_device.cuh"
@@ -48,10 +49,38 @@ struct Workspace {
     int32_t *bsum = nullptr;        // per-block sums for device-wide scans [4096]
     int32_t *kcount = nullptr;      // K0 of the last watershed [1]
     // host-copy staging for ws_segment_host
-    size_t host_n = 0;
+    size_t host_n = 0, grad_n = 0;
     uint8_t *grad_stage = nullptr;  // device copy of a host gradient
     int32_t *levels_stage = nullptr;
     int32_t *counts_stage = nullptr;
+};
+
+// Phases timed by the optional event profiler (ws_context_set_profiling).
+enum Phase {
+    PH_STEP1 = 0,     // Eq. 1 states and arrows
+    PH_PLATEAU,       // step II distances
+    PH_RESOLVE,       // step II pointer choice + step IV Union
+    PH_JUMP,          // step III pointer jumping + smallest index per basin
+    PH_COMPACT,       // canonical ids
+    PH_RAG,           // region adjacency (pass values)
+    PH_LEVELS,        // lowest-pass merging on the region graph
+    PH_LEVEL_WRITE,   // per-pixel level planes
+    PH_CLEANUP,       // edge table reset
+    PH_GRADIENT,      // blur + Sobel
+    PH_COPY,          // host <-> device copies of ws_segment_host
+    NPHASE
+};
+
+struct Prof {
+    int on = 0;
+    struct Rec {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    double total_ms[NPHASE] = {};
+    long long calls[NPHASE] = {};
 };
 
 }  // namespace ws
@@ -65,9 +94,21 @@ struct ws_context {
     ws::DevStatus *status = nullptr;
     ws::Workspace w;
     int num_sms = 0;
+    unsigned long long launches = 0;  // kernels enqueued by this context
+    ws::Prof prof;
 };
 
 namespace ws {
+
+// Brackets one phase with timing events when profiling is on.
+struct PhaseScope {
+    ws_context *c;
+    int ph;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    PhaseScope(ws_context *c_, int ph_, cudaStream_t s_);
+    ~PhaseScope();
+};
 
 // Effective tuning values.
 int tune_plateau_cap(const ws_context *c);

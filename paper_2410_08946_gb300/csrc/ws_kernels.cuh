@@ -304,6 +304,10 @@ static __global__ void __launch_bounds__(NTHR) k_resolve_union(const T *__restri
                 if (!nb_at<CONN>(geo, x, y, z, i, q)) continue;
                 if (g[q] == gp && dist[q] == d - 1 && q > best) best = q;
             }
+            if (best < 0) {  // cannot happen for a converged distance field
+                record_error(status, DEV_NONCONVERGED, 7);
+                best = p;
+            }
             par[p] = best;
         } else {
             // minimal plateau: Union with equal-valued minimal-plateau neighbours q > p
@@ -556,7 +560,7 @@ static __global__ void __launch_bounds__(NTHR) k_rag(const T *__restrict__ g, Ge
             unsigned h = 0;
             if (in && nb_at<CONN>(geo, x, y, z, i, q)) {
                 int B = L[q];
-                if (B != A) {
+                if (B != A && A >= 0 && B >= 0) {
                     has = true;
                     int a = imin(A, B), b = imax(A, B);
                     key = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
@@ -602,6 +606,10 @@ static __global__ void __launch_bounds__(NTHR) k_levels(const unsigned long long
     const int gsz = gridDim.x * NTHR;
     const int E = *ecount;
     const int K0 = *k0_ptr;
+    if (K0 < 1 || (size_t)K0 > kstride) {
+        if (blockIdx.x == 0 && tid == 0) record_error(status, DEV_BAD_LABELS, 8);
+        return;  // uniform: every CTA leaves before the first barrier
+    }
     if (blockIdx.x == 0 && tid == 0 && counts) counts[0] = K0;
     int Kk = K0;
     for (int k = 0; k + 1 < NL; k++) {
@@ -695,7 +703,8 @@ static __global__ void __launch_bounds__(NTHR) k_level_write(int N, const int32_
 {
     for (int p = blockIdx.x * NTHR + threadIdx.x; p < N; p += gridDim.x * NTHR) {
         int c = L0[p];
-        for (int k = 0; k < nlev; k++) __stcs(out + (size_t)k * N + p, gmap[(size_t)k * kstride + c]);
+        bool ok = c >= 0 && (size_t)c < kstride;
+        for (int k = 0; k < nlev; k++) __stcs(out + (size_t)k * N + p, ok ? gmap[(size_t)k * kstride + c] : -1);
     }
 }
 

@@ -46,8 +46,10 @@ template <typename T, int CONN> static ws_status run_step1(ws_context *c, const 
                                                            uint8_t *states, int32_t *arrows, cudaStream_t s)
 {
     TileGeo tg = make_tilegeo<CONN>(geo);
+    PhaseScope ps(c, PH_STEP1, s);
     k_step1<T, CONN><<<pixel_grid(c, geo.N), NTHR, 0, s>>>((const T *)grad, geo, arrows, states, nullptr,
                                                            nullptr, tg);
+    c->launches += 1;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "step1 launch");
 }
@@ -64,10 +66,18 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
     cudaError_t e = cudaMemsetAsync(w.act, 0, 2 * (size_t)tg.ntiles, s);
     if (e == cudaSuccess) e = reset_barrier(c, s);
     if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
-    k_step1<T, CONN><<<pixel_grid(c, geo.N), NTHR, 0, s>>>(g, geo, w.par, w.st, w.aux, w.act, tg);
-    int grid = coop_grid(c, k_plateau<T, CONN>, tg.ntiles);
-    e = launch_coop(k_plateau<T, CONN>, grid, s, g, geo, tg, w.aux, w.act, c->status, tune_plateau_cap(c),
-                    tune_timeout_ns(c));
+    {
+        PhaseScope ps(c, PH_STEP1, s);
+        k_step1<T, CONN><<<pixel_grid(c, geo.N), NTHR, 0, s>>>(g, geo, w.par, w.st, w.aux, w.act, tg);
+        c->launches += 1;
+    }
+    {
+        PhaseScope ps(c, PH_PLATEAU, s);
+        int grid = coop_grid(c, k_plateau<T, CONN>, tg.ntiles);
+        e = launch_coop(k_plateau<T, CONN>, grid, s, g, geo, tg, w.aux, w.act, c->status, tune_plateau_cap(c),
+                        tune_timeout_ns(c));
+        c->launches += 1;
+    }
     if (e != cudaSuccess) return set_cuda_error(c, e, "plateau launch");
     return WS_OK;
 }
@@ -79,6 +89,7 @@ template <typename T, int CONN> static ws_status run_plateau_distance(ws_context
     ws_status st = run_front<T, CONN>(c, (const T *)grad, geo, s);
     if (st != WS_OK) return st;
     k_dist_out<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo.N, c->w.aux, dist);
+    c->launches += 1;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "plateau distance");
 }
@@ -90,19 +101,34 @@ template <typename T, int CONN> static ws_status run_watershed(ws_context *c, co
     ws_status st = run_front<T, CONN>(c, g, geo, s);
     if (st != WS_OK) return st;
     Workspace &w = c->w;
-    k_resolve_union<T, CONN><<<pixel_grid(c, geo.N), NTHR, 0, s>>>(g, geo, w.par, w.st, w.aux, c->status);
+    {
+        PhaseScope ps(c, PH_RESOLVE, s);
+        k_resolve_union<T, CONN><<<pixel_grid(c, geo.N), NTHR, 0, s>>>(g, geo, w.par, w.st, w.aux, c->status);
+        c->launches += 1;
+    }
     cudaError_t e = reset_barrier(c, s);
     if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
-    int grid = coop_grid(c, k_jump, (geo.N + NTHR - 1) / NTHR);
-    e = launch_coop(k_jump, grid, s, geo.N, w.par, w.aux, tune_rr(c), c->status, tune_jump_cap(c),
-                    tune_timeout_ns(c));
+    {
+        PhaseScope ps(c, PH_JUMP, s);
+        int grid = coop_grid(c, k_jump, (geo.N + NTHR - 1) / NTHR);
+        e = launch_coop(k_jump, grid, s, geo.N, w.par, w.aux, tune_rr(c), c->status, tune_jump_cap(c),
+                        tune_timeout_ns(c));
+        c->launches += 1;
+    }
     if (e != cudaSuccess) return set_cuda_error(c, e, "jump launch");
-    const int nblk = (geo.N + CHUNK - 1) / CHUNK;
-    k_flags<<<nblk, NTHR, 0, s>>>(geo.N, w.par, w.aux, w.st, w.blk);
-    k_scan<<<1, 1024, 0, s>>>(w.blk, nblk, w.kcount);
-    k_assign<<<nblk, NTHR, 0, s>>>(geo.N, w.par, w.aux, w.st, w.blk);
-    k_label<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo.N, w.par, w.aux, labels);
-    if (count) k_copy_int<<<1, 32, 0, s>>>(w.kcount, count);
+    {
+        PhaseScope ps(c, PH_COMPACT, s);
+        const int nblk = (geo.N + CHUNK - 1) / CHUNK;
+        k_flags<<<nblk, NTHR, 0, s>>>(geo.N, w.par, w.aux, w.st, w.blk);
+        k_scan<<<1, 1024, 0, s>>>(w.blk, nblk, w.kcount);
+        k_assign<<<nblk, NTHR, 0, s>>>(geo.N, w.par, w.aux, w.st, w.blk);
+        k_label<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo.N, w.par, w.aux, labels);
+        c->launches += 4;
+        if (count) {
+            k_copy_int<<<1, 32, 0, s>>>(w.kcount, count);
+            c->launches += 1;
+        }
+    }
     e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "watershed launch");
 }
@@ -116,7 +142,10 @@ template <typename T, int CONN> static ws_status run_waterfall(ws_context *c, co
     // the caller of this function from the labels); K0 <= kmax.
     Workspace &w = c->w;
     if (NL <= 1) {
-        if (counts) k_copy_int<<<1, 32, 0, s>>>(w.kcount, counts);
+        if (counts) {
+            k_copy_int<<<1, 32, 0, s>>>(w.kcount, counts);
+            c->launches += 1;
+        }
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "waterfall launch");
     }
@@ -130,19 +159,35 @@ template <typename T, int CONN> static ws_status run_waterfall(ws_context *c, co
     st = ensure_regions(c, kmax, NL - 1);
     if (st != WS_OK) return st;
     const T *g = (const T *)grad;
-    k_rag<T, CONN><<<pixel_grid(c, geo.N), NTHR, 0, s>>>(g, geo, labels0, w.keys, w.vals, w.slots, w.ecount,
-                                                         (unsigned long long)(w.edge_cap - 1), c->status);
+    {
+        PhaseScope ps(c, PH_RAG, s);
+        k_rag<T, CONN><<<pixel_grid(c, geo.N), NTHR, 0, s>>>(g, geo, labels0, w.keys, w.vals, w.slots, w.ecount,
+                                                             (unsigned long long)(w.edge_cap - 1), c->status);
+        c->launches += 1;
+    }
     cudaError_t e = reset_barrier(c, s);
     if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
-    int grid = coop_grid(c, k_levels, c->num_sms * 4);
-    if (grid > 4096) grid = 4096;
-    e = launch_coop(k_levels, grid, s, (const unsigned long long *)w.keys, (const uint32_t *)w.vals,
-                    (const int32_t *)w.slots, (const int32_t *)w.ecount, (const int32_t *)w.kcount, NL, w.gmap,
-                    w.kmax, w.newmin, w.uf, w.rank, w.bsum, counts, c->status, tune_timeout_ns(c));
+    {
+        PhaseScope ps(c, PH_LEVELS, s);
+        int grid = coop_grid(c, k_levels, c->num_sms * 4);
+        if (grid > 4096) grid = 4096;
+        e = launch_coop(k_levels, grid, s, (const unsigned long long *)w.keys, (const uint32_t *)w.vals,
+                        (const int32_t *)w.slots, (const int32_t *)w.ecount, (const int32_t *)w.kcount, NL, w.gmap,
+                        w.kmax, w.newmin, w.uf, w.rank, w.bsum, counts, c->status, tune_timeout_ns(c));
+        c->launches += 1;
+    }
     if (e != cudaSuccess) return set_cuda_error(c, e, "levels launch");
-    k_level_write<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo.N, labels0, w.gmap, w.kmax, NL - 1, levels);
-    k_hash_clear<<<pixel_grid(c, (long long)geo.N / 4 + 1), NTHR, 0, s>>>(w.keys, w.vals, w.slots, w.ecount);
-    k_reset_count<<<1, 32, 0, s>>>(w.ecount, c->status);
+    {
+        PhaseScope ps(c, PH_LEVEL_WRITE, s);
+        k_level_write<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo.N, labels0, w.gmap, w.kmax, NL - 1, levels);
+        c->launches += 1;
+    }
+    {
+        PhaseScope ps(c, PH_CLEANUP, s);
+        k_hash_clear<<<pixel_grid(c, (long long)geo.N / 4 + 1), NTHR, 0, s>>>(w.keys, w.vals, w.slots, w.ecount);
+        k_reset_count<<<1, 32, 0, s>>>(w.ecount, c->status);
+        c->launches += 2;
+    }
     e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "waterfall launch");
 }
