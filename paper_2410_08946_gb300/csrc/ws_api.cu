@@ -64,30 +64,44 @@ template <typename P> static void dfree(ws_context *c, P **p, size_t bytes)
     }
 }
 
-ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles, size_t nblk)
+ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles)
 {
     Workspace &w = c->w;
     ws_status st = WS_OK;
     if (N > w.N) {
         dfree(c, &w.par, w.N * 4);
         dfree(c, &w.aux, w.N * 4);
-        dfree(c, &w.st, w.N);
+        dfree(c, &w.dist, w.N * 4);
+        dfree(c, &w.roots, w.rmax * 4);
+        dfree(c, &w.rootm, w.rmax * 4);
+        dfree(c, &w.bitmap, w.nwords * 4);
+        dfree(c, &w.gcnt, (w.ngroups + 1) * 4);
+        dfree(c, &w.csum, (w.nchunks + 1) * 4);
         w.N = 0;
-        if ((st = dalloc(c, &w.par, N * 4)) || (st = dalloc(c, &w.aux, N * 4)) || (st = dalloc(c, &w.st, N)))
+        const size_t rmax = N / 2 + 2, nwords = (N + 31) / 32, ngroups = (nwords + 31) / 32;
+        const size_t nchunks = (ngroups + 2047) / 2048;
+        if ((st = dalloc(c, &w.par, N * 4)) || (st = dalloc(c, &w.aux, N * 4)) || (st = dalloc(c, &w.dist, N * 4)) ||
+            (st = dalloc(c, &w.roots, rmax * 4)) || (st = dalloc(c, &w.rootm, rmax * 4)) ||
+            (st = dalloc(c, &w.bitmap, nwords * 4)) || (st = dalloc(c, &w.gcnt, (ngroups + 1) * 4)) ||
+            (st = dalloc(c, &w.csum, (nchunks + 1) * 4)))
             return st;
+        cudaError_t e = cudaMemset(w.bitmap, 0, nwords * 4);
+        if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
+        w.rmax = rmax;
+        w.nwords = nwords;
+        w.ngroups = ngroups;
+        w.nchunks = nchunks;
         w.N = N;
     }
     if (ntiles > w.ntiles) {
+        dfree(c, &w.plat, w.ntiles);
         dfree(c, &w.act, w.ntiles * 2);
+        dfree(c, &w.tlist, w.ntiles * 4);
         w.ntiles = 0;
-        if ((st = dalloc(c, &w.act, ntiles * 2))) return st;
+        if ((st = dalloc(c, &w.plat, ntiles)) || (st = dalloc(c, &w.act, ntiles * 2)) ||
+            (st = dalloc(c, &w.tlist, ntiles * 4)))
+            return st;
         w.ntiles = ntiles;
-    }
-    if (nblk > w.nblk) {
-        dfree(c, &w.blk, (w.nblk + 1) * 4);
-        w.nblk = 0;
-        if ((st = dalloc(c, &w.blk, (nblk + 1) * 4))) return st;
-        w.nblk = nblk;
     }
     return WS_OK;
 }
@@ -260,6 +274,7 @@ ws_status ws_context_create(ws_context **out, int device, size_t budget)
     if (st == WS_OK) st = dalloc(c, &c->w.ecount, 4);
     if (st == WS_OK) st = dalloc(c, &c->w.bsum, 4096 * 4);
     if (st == WS_OK) st = dalloc(c, &c->w.kcount, 4);
+    if (st == WS_OK) st = dalloc(c, &c->w.counters, 16);
     if (st == WS_OK) {
         e = cudaMemset(c->status, 0, sizeof(DevStatus));
         if (e == cudaSuccess) e = cudaMemset(c->w.ecount, 0, 4);
@@ -280,8 +295,10 @@ void ws_context_destroy(ws_context *c)
     cudaSetDevice(c->device);
     Workspace &w = c->w;
     cudaFree(c->status);
-    void *ptrs[] = {w.par, w.aux, w.st, w.act, w.blk, w.keys, w.vals, w.slots, w.ecount, w.gmap, w.newmin,
-                    w.uf, w.rank, w.bsum, w.kcount, w.grad_stage, w.levels_stage, w.counts_stage};
+    void *ptrs[] = {w.par,   w.aux,    w.dist,   w.plat,   w.act,    w.tlist,  w.roots,  w.rootm,
+                    w.counters, w.bitmap, w.gcnt, w.csum,   w.keys,   w.vals,   w.slots,  w.ecount,
+                    w.gmap,  w.newmin, w.uf,     w.rank,   w.bsum,   w.kcount, w.grad_stage, w.levels_stage,
+                    w.counts_stage};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &r : c->prof.pending) {
@@ -313,6 +330,7 @@ ws_status ws_context_check(ws_context *c, ws_stream_t stream)
     case 6: what = "region adjacency table full (raise ws_tuning.edge_capacity)"; break;
     case 7: what = "step II found a plateau pixel with no neighbour one step closer"; break;
     case 8: what = "level-0 labels out of range (expected canonical ids 0..K-1)"; break;
+    case 9: what = "root chase exceeded its hop cap"; break;
     case 100: what = "device-wide barrier timed out"; break;
     }
     snprintf(buf, sizeof buf, "%s (code %d, site %d)", what, h.code, h.where);
@@ -451,10 +469,7 @@ ws_status ws_segment(ws_context *c, const void *grad_d, ws_dtype dtype, const ws
     if (st) return st;
     if (!levels_d) return set_error(c, WS_ERR_INVALID, "NULL levels");
     if (NL < 1) return set_error(c, WS_ERR_INVALID, "NL must be >= 1");
-    cudaStream_t s = (cudaStream_t)stream;
-    if ((st = L->watershed(c, grad_d, g, levels_d, nullptr, s))) return st;
-    // distinct minimal plateaux are never adjacent, so K0 <= ceil(N / 2)
-    return L->waterfall(c, levels_d, grad_d, g, NL, levels_d + g.N, counts_d, (size_t)g.N / 2 + 1, s);
+    return L->segment(c, grad_d, g, NL, levels_d, counts_d, (cudaStream_t)stream);
 }
 
 ws_status ws_segment_host(ws_context *c, const void *grad_h, ws_dtype dtype, const ws_shape *shape, int conn,
@@ -490,10 +505,8 @@ ws_status ws_segment_host(ws_context *c, const void *grad_h, ws_dtype dtype, con
         e = cudaMemcpyAsync(w.grad_stage, grad_h, (size_t)g.N * b, cudaMemcpyHostToDevice, s);
     }
     if (e != cudaSuccess) return set_cuda_error(c, e, "H2D copy");
-    if ((st = L->watershed(c, w.grad_stage, g, w.levels_stage, nullptr, s))) return st;
     int32_t *cnt = NL <= 64 ? w.counts_stage : nullptr;
-    if ((st = L->waterfall(c, w.levels_stage, w.grad_stage, g, NL, w.levels_stage + g.N, cnt, (size_t)g.N / 2 + 1, s)))
-        return st;
+    if ((st = L->segment(c, w.grad_stage, g, NL, w.levels_stage, cnt, s))) return st;
     {
         PhaseScope ps(c, PH_COPY, s);
         e = cudaMemcpyAsync(levels_h, w.levels_stage, levels_bytes, cudaMemcpyDeviceToHost, s);

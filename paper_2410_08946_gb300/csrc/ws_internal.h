@@ -26,13 +26,21 @@ struct TileGeo {
 // seen so far and stays resident between calls.
 struct Workspace {
     size_t N = 0;           // pixels the per-pixel arrays can hold
-    int32_t *par = nullptr; // arrows / union-find parents / roots   [N]
-    int32_t *aux = nullptr; // plateau distance, then per-root min index / id [N]
-    uint8_t *st = nullptr;  // states, then "first pixel of its region" flags [N]
+    int32_t *par = nullptr; // in-tile path ends, then roots                 [N]
+    int32_t *aux = nullptr; // smallest index per root, then canonical id    [N]
+    int32_t *dist = nullptr;// step II distances (plateau tiles only)        [N]
     size_t ntiles = 0;
-    uint8_t *act = nullptr; // active-tile flags, two rounds            [2*ntiles]
-    size_t nblk = 0;
-    int32_t *blk = nullptr; // per-chunk counts for the compaction scan [nblk+1]
+    uint8_t *plat = nullptr;  // tile holds plateau pixels                   [ntiles]
+    uint8_t *act = nullptr;   // active-tile flags, two rounds               [2*ntiles]
+    int32_t *tlist = nullptr; // list of plateau tiles                       [ntiles]
+    size_t rmax = 0;
+    int32_t *roots = nullptr; // list of basin roots                         [rmax]
+    int32_t *rootm = nullptr; // smallest pixel index of each listed root    [rmax]
+    int32_t *counters = nullptr;  // plateau tiles, roots, ...               [4]
+    size_t nwords = 0, ngroups = 0, nchunks = 0;
+    uint32_t *bitmap = nullptr;   // one bit per pixel index (kept zero)     [nwords]
+    int32_t *gcnt = nullptr;      // popcount per 32-word group, then prefix [ngroups]
+    int32_t *csum = nullptr;      // scan chunk sums                         [nchunks + 1]
     // region adjacency hash table
     size_t edge_cap = 0;            // power of two
     unsigned long long *keys = nullptr;  // (a << 32 | b), empty = ~0
@@ -117,7 +125,7 @@ int tune_rr(const ws_context *c);
 unsigned long long tune_timeout_ns(const ws_context *c);
 
 // Workspace management (ws_api.cu).
-ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles, size_t nblk);
+ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles);
 ws_status ensure_edges(ws_context *c, size_t cap);
 ws_status ensure_regions(ws_context *c, size_t kmax, int levels);
 ws_status set_cuda_error(ws_context *c, cudaError_t e, const char *what);
@@ -132,6 +140,8 @@ struct Launchers {
                                   cudaStream_t);
     ws_status (*waterfall)(ws_context *, const int32_t *labels0, const void *grad, const Geo &, int NL,
                            int32_t *levels, int32_t *counts, size_t kmax, cudaStream_t);
+    ws_status (*segment)(ws_context *, const void *grad, const Geo &, int NL, int32_t *levels, int32_t *counts,
+                         cudaStream_t);
 };
 
 // dtype: 0 = u8, 1 = u16; conn: 4, 8, 6.  Returns nullptr when unsupported.

@@ -136,123 +136,7 @@ static __global__ void __launch_bounds__(NTHR) k_step1(const T *__restrict__ g, 
 }
 
 // ---------------------------------------------------------------------------
-// step II: plateau distances (cooperative, device-wide rounds)
-// ---------------------------------------------------------------------------
-
-template <typename T, int CONN>
-static __global__ void __launch_bounds__(NTHR) k_plateau(const T *__restrict__ g, Geo geo, TileGeo tg,
-                                                  int32_t *dist, uint8_t *act, DevStatus *status,
-                                                  int round_cap, unsigned long long timeout_ns)
-{
-    using PT = PTile<CONN>;
-    __shared__ int gs[PT::HS];
-    __shared__ int ds[PT::HS];
-    __shared__ int flag_s;
-    const int tid = threadIdx.x;
-    uint8_t *act0 = act, *act1 = act + tg.ntiles;
-
-    for (int r = 0;; r++) {
-        uint8_t *cur = (r & 1) ? act1 : act0;
-        uint8_t *nxt = (r & 1) ? act0 : act1;
-        if (blockIdx.x == 0 && tid == 0) status->changed[(r + 1) % 3] = 0;
-        for (int t = blockIdx.x; t < tg.ntiles; t += gridDim.x) {
-            __syncthreads();
-            if (tid == 0) {
-                flag_s = *(volatile uint8_t *)(cur + t);
-                if (flag_s) cur[t] = 0;
-            }
-            __syncthreads();
-            if (!flag_s) continue;
-            const int tx = t % tg.ntx, ty = (t / tg.ntx) % tg.nty, tz = t / (tg.ntx * tg.nty);
-            const int x0 = tx * PT::TX - 1, y0 = ty * PT::TY - 1, z0 = PT::ND == 2 ? 0 : tz * PT::TZ - 1;
-            for (int i = tid; i < PT::HS; i += NTHR) {
-                int hx = i % PT::HX, hy = (i / PT::HX) % PT::HY, hz = i / (PT::HX * PT::HY);
-                int x = x0 + hx, y = y0 + hy, z = z0 + hz;
-                if (x >= 0 && x < geo.W && y >= 0 && y < geo.H && z >= 0 && z < geo.D) {
-                    int q = (z * geo.H + y) * geo.W + x;
-                    gs[i] = (int)g[q];
-                    ds[i] = __ldcg(dist + q);
-                } else {
-                    gs[i] = -1;
-                    ds[i] = INF_D;
-                }
-            }
-            __syncthreads();
-            int orig[PT::PER_THR];
-#pragma unroll
-            for (int k = 0; k < PT::PER_THR; k++) {
-                int i = tid + k * NTHR;
-                int lx = i % PT::TX, ly = (i / PT::TX) % PT::TY, lz = i / (PT::TX * PT::TY);
-                int h = ((lz + (PT::ND == 3)) * PT::HY + ly + 1) * PT::HX + lx + 1;
-                orig[k] = ds[h];
-            }
-            // in-tile relaxation to the fixpoint (halo frozen)
-            for (int it = 0; it < 4 * PT::NPIX + 8; it++) {
-                int ch = 0;
-#pragma unroll
-                for (int k = 0; k < PT::PER_THR; k++) {
-                    int i = tid + k * NTHR;
-                    int lx = i % PT::TX, ly = (i / PT::TX) % PT::TY, lz = i / (PT::TX * PT::TY);
-                    int h = ((lz + (PT::ND == 3)) * PT::HY + ly + 1) * PT::HX + lx + 1;
-                    int gv = gs[h];
-                    int d = ds[h];
-                    if (gv < 0 || d == 0) continue;
-                    int best = d;
-#pragma unroll
-                    for (int n = 0; n < Nb<CONN>::n; n++) {
-                        int hn = h + (Nb<CONN>::dz(n) * PT::HY + Nb<CONN>::dy(n)) * PT::HX + Nb<CONN>::dx(n);
-                        if (gs[hn] == gv) best = imin(best, ds[hn] + 1);
-                    }
-                    if (best < d) {
-                        ds[h] = best;
-                        ch = 1;
-                    }
-                }
-                if (!__syncthreads_or(ch)) break;
-            }
-            int border = 0;
-#pragma unroll
-            for (int k = 0; k < PT::PER_THR; k++) {
-                int i = tid + k * NTHR;
-                int lx = i % PT::TX, ly = (i / PT::TX) % PT::TY, lz = i / (PT::TX * PT::TY);
-                int h = ((lz + (PT::ND == 3)) * PT::HY + ly + 1) * PT::HX + lx + 1;
-                if (ds[h] != orig[k]) {
-                    int x = x0 + 1 + lx, y = y0 + 1 + ly, z = z0 + (PT::ND == 3) + lz;
-                    __stcg(dist + (z * geo.H + y) * geo.W + x, ds[h]);
-                    if (lx == 0 || lx == PT::TX - 1 || ly == 0 || ly == PT::TY - 1 ||
-                        (PT::ND == 3 && (lz == 0 || lz == PT::TZ - 1)))
-                        border = 1;
-                }
-            }
-            if (__syncthreads_or(border) && tid == 0) {
-                for (int dz = (PT::ND == 3 ? -1 : 0); dz <= (PT::ND == 3 ? 1 : 0); dz++)
-                    for (int dy = -1; dy <= 1; dy++)
-                        for (int dx = -1; dx <= 1; dx++) {
-                            int ax = tx + dx, ay = ty + dy, az = tz + dz;
-                            if (ax < 0 || ax >= tg.ntx || ay < 0 || ay >= tg.nty || az < 0 || az >= tg.ntz)
-                                continue;
-                            if (dx == 0 && dy == 0 && dz == 0) continue;
-                            nxt[(az * tg.nty + ay) * tg.ntx + ax] = 1;
-                        }
-                atomicAdd(&status->changed[r % 3], 1);
-            }
-        }
-        __threadfence();
-        if (!grid_barrier(status, timeout_ns)) return;
-        int any = *(volatile int *)&status->changed[r % 3];
-        if (any == 0) {
-            if (blockIdx.x == 0 && tid == 0) status->rounds_plateau = r + 1;
-            return;
-        }
-        if (r + 1 >= round_cap) {
-            if (blockIdx.x == 0 && tid == 0) record_error(status, DEV_NONCONVERGED, 2);
-            return;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// step II pointer choice + step IV Union
+// Union-Find (step IV of Alg. 1 and the region graph merge)
 // ---------------------------------------------------------------------------
 
 static __device__ __forceinline__ int uf_find(int32_t *par, int a)
@@ -284,123 +168,9 @@ static __device__ __forceinline__ void uf_union(int32_t *par, int a, int b, DevS
     record_error(s, DEV_NONCONVERGED, 4);
 }
 
-template <typename T, int CONN>
-static __global__ void __launch_bounds__(NTHR) k_resolve_union(const T *__restrict__ g, Geo geo, int32_t *par,
-                                                        const uint8_t *__restrict__ st,
-                                                        const int32_t *__restrict__ dist, DevStatus *status)
-{
-    for (int p = blockIdx.x * NTHR + threadIdx.x; p < geo.N; p += gridDim.x * NTHR) {
-        if (st[p] < 2) continue;
-        int x, y, z;
-        coords(geo, p, x, y, z);
-        const unsigned gp = g[p];
-        const int d = dist[p];
-        if (d < INF_D) {
-            // non-minimal plateau: drain to the largest-index equal neighbour one step closer
-            int best = -1;
-#pragma unroll
-            for (int i = 0; i < Nb<CONN>::n; i++) {
-                int q;
-                if (!nb_at<CONN>(geo, x, y, z, i, q)) continue;
-                if (g[q] == gp && dist[q] == d - 1 && q > best) best = q;
-            }
-            if (best < 0) {  // cannot happen for a converged distance field
-                record_error(status, DEV_NONCONVERGED, 7);
-                best = p;
-            }
-            par[p] = best;
-        } else {
-            // minimal plateau: Union with equal-valued minimal-plateau neighbours q > p
-#pragma unroll
-            for (int i = Half<CONN>::first; i < Nb<CONN>::n; i++) {
-                int q;
-                if (!nb_at<CONN>(geo, x, y, z, i, q)) continue;
-                if (st[q] >= 2 && dist[q] >= INF_D && g[q] == gp) uf_union(par, p, q, status);
-            }
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
-// step III pointer jumping (cooperative) + smallest pixel index per basin
+// scans
 // ---------------------------------------------------------------------------
-
-static __global__ void __launch_bounds__(NTHR) k_jump(int N, int32_t *par, int32_t *mi, int RR, DevStatus *status,
-                                               int round_cap, unsigned long long timeout_ns)
-{
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    for (int r = 0;; r++) {
-        if (blockIdx.x == 0 && tid == 0) status->changed[(r + 1) % 3] = 0;
-        int ch = 0;
-        for (int p = blockIdx.x * NTHR + tid; p < N; p += gridDim.x * NTHR) {
-            if (r == 0) mi[p] = 0x7fffffff;
-            int l0 = __ldcg(par + p);
-            int l = l0;
-            for (int i = 0; i < RR; i++) {
-                int l2 = __ldcg(par + l);
-                if (l2 == l) break;
-                l = l2;
-            }
-            if (l != l0) {
-                __stcg(par + p, l);
-                ch = 1;
-            }
-        }
-        unsigned bal = __ballot_sync(0xffffffffu, ch);
-        if (lane == 0 && bal) atomicAdd(&status->changed[r % 3], 1);
-        __threadfence();
-        if (!grid_barrier(status, timeout_ns)) return;
-        if (*(volatile int *)&status->changed[r % 3] == 0) {
-            if (blockIdx.x == 0 && tid == 0) status->rounds_jump = r + 1;
-            break;
-        }
-        if (r + 1 >= round_cap) {
-            if (blockIdx.x == 0 && tid == 0) record_error(status, DEV_NONCONVERGED, 5);
-            return;
-        }
-    }
-    // every pixel now points at its basin's root; record the smallest index
-    for (int p = blockIdx.x * NTHR + tid; p < N; p += gridDim.x * NTHR) {
-        int r = __ldcg(par + p);
-        unsigned grp = __match_any_sync(__activemask(), r);
-        int leader = __ffs(grp) - 1;
-        if (lane == leader) atomicMin(mi + r, p);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// canonical compaction
-// ---------------------------------------------------------------------------
-
-constexpr int CHUNK = NTHR * 8;   // pixels per CTA in the compaction kernels
-
-// F[p] = 1 iff p is the smallest pixel of its basin; per-chunk counts.
-static __global__ void __launch_bounds__(NTHR) k_flags(int N, const int32_t *__restrict__ par,
-                                                const int32_t *__restrict__ mi, uint8_t *__restrict__ F,
-                                                int32_t *__restrict__ blk)
-{
-    const int base = blockIdx.x * CHUNK;
-    int cnt = 0;
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-        int p = base + j * NTHR + threadIdx.x;
-        if (p < N) {
-            int f = mi[par[p]] == p;
-            F[p] = (uint8_t)f;
-            cnt += f;
-        }
-    }
-    __shared__ int red[NTHR / 32];
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int s = 0;
-        for (int w = 0; w < NTHR / 32; w++) s += red[w];
-        blk[blockIdx.x] = s;
-    }
-}
 
 // Exclusive scan of blk[0..n) in place, total to blk[n] (one CTA of 1024).
 static __global__ void __launch_bounds__(1024) k_scan(int32_t *blk, int n, int32_t *total_out)
@@ -441,26 +211,30 @@ static __global__ void __launch_bounds__(1024) k_scan(int32_t *blk, int n, int32
     }
 }
 
-// id[root] = rank of the basin's smallest pixel among all basins' smallest pixels.
-static __global__ void __launch_bounds__(NTHR) k_assign(int N, const int32_t *__restrict__ par, int32_t *mi,
-                                                 const uint8_t *__restrict__ F, const int32_t *__restrict__ blk)
+// Device-wide exclusive scan, step 1: each CTA scans SCAN_CHUNK elements of
+// a in place and writes the chunk total to sums[blockIdx.x].
+constexpr int SCAN_CHUNK = 2048;
+static __global__ void __launch_bounds__(NTHR) k_scan_chunks(int32_t *a, int n, int32_t *sums)
 {
     __shared__ int wsum[NTHR / 32];
     __shared__ int carry;
-    const int base = blockIdx.x * CHUNK;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = blk[blockIdx.x];
+    const int base = blockIdx.x * SCAN_CHUNK;
+    if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int j = 0; j < 8; j++) {
-        int p = base + j * NTHR + threadIdx.x;
-        int f = (p < N) ? F[p] : 0;
-        unsigned b = __ballot_sync(0xffffffffu, f);
-        int before = __popc(b & ((1u << lane) - 1u));
-        if (lane == 0) wsum[wid] = __popc(b);
+    for (int j = 0; j < SCAN_CHUNK; j += NTHR) {
+        const int i = base + j + threadIdx.x;
+        const int v = i < n ? a[i] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
         __syncthreads();
         int off = carry;
         for (int w = 0; w < wid; w++) off += wsum[w];
-        if (f) mi[par[p]] = off + before;
+        if (i < n) a[i] = off + x - v;
         __syncthreads();
         if (threadIdx.x == 0) {
             int s = 0;
@@ -469,20 +243,16 @@ static __global__ void __launch_bounds__(NTHR) k_assign(int N, const int32_t *__
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0) sums[blockIdx.x] = carry;
 }
 
-static __global__ void __launch_bounds__(NTHR) k_label(int N, const int32_t *__restrict__ par,
-                                                const int32_t *__restrict__ mi, int32_t *__restrict__ labels)
+// step 3: add the scanned chunk offsets
+static __global__ void __launch_bounds__(NTHR) k_scan_add(int32_t *a, int n, const int32_t *__restrict__ sums)
 {
-    for (int p = blockIdx.x * NTHR + threadIdx.x; p < N; p += gridDim.x * NTHR) labels[p] = mi[par[p]];
-}
-
-// Step II distances as reported by ws_plateau_distance (-1 = no distance).
-static __global__ void __launch_bounds__(NTHR) k_dist_out(int N, const int32_t *__restrict__ d, int32_t *__restrict__ out)
-{
-    for (int p = blockIdx.x * NTHR + threadIdx.x; p < N; p += gridDim.x * NTHR) {
-        int v = d[p];
-        out[p] = v >= INF_D ? -1 : v;
+    const int off = sums[blockIdx.x];
+    for (int j = threadIdx.x; j < SCAN_CHUNK; j += NTHR) {
+        const int i = blockIdx.x * SCAN_CHUNK + j;
+        if (i < n) a[i] += off;
     }
 }
 
@@ -595,6 +365,7 @@ static __device__ __forceinline__ int block_sum(int v, int *red)
 static __global__ void __launch_bounds__(NTHR) k_levels(const unsigned long long *__restrict__ keys,
                                                  const uint32_t *__restrict__ vals,
                                                  const int32_t *__restrict__ slots, const int32_t *ecount,
+                                                 const int32_t *__restrict__ idmap,
                                                  const int32_t *k0_ptr, int NL, int32_t *gmap, size_t kstride,
                                                  uint32_t *newmin, int32_t *uf, int32_t *rank, int32_t *bsum,
                                                  int32_t *counts, DevStatus *status,
@@ -626,6 +397,10 @@ static __global__ void __launch_bounds__(NTHR) k_levels(const unsigned long long
             int s = slots[e];
             unsigned long long key = keys[s];
             int a0 = (int)(key >> 32), b0 = (int)(key & 0xffffffffu);
+            if (idmap) {
+                a0 = idmap[a0];
+                b0 = idmap[b0];
+            }
             unsigned h = vals[s];
             int A = gm ? __ldcg(gm + a0) : a0, B = gm ? __ldcg(gm + b0) : b0;
             if (A != B) {
@@ -639,6 +414,10 @@ static __global__ void __launch_bounds__(NTHR) k_levels(const unsigned long long
             int s = slots[e];
             unsigned long long key = keys[s];
             int a0 = (int)(key >> 32), b0 = (int)(key & 0xffffffffu);
+            if (idmap) {
+                a0 = idmap[a0];
+                b0 = idmap[b0];
+            }
             unsigned h = vals[s];
             int A = gm ? __ldcg(gm + a0) : a0, B = gm ? __ldcg(gm + b0) : b0;
             if (A != B && (h == __ldcg(newmin + A) || h == __ldcg(newmin + B))) uf_union(uf, A, B, status);

@@ -5,17 +5,17 @@
 
 #include <stddef.h>
 
-#include "ws_kernels.cuh"
+#include "ws_tiles.cuh"
 
 namespace ws {
 
 // Grid size of a cooperative launch: every CTA must be co-resident.
-template <typename K> static int coop_grid(ws_context *c, K kernel, int want)
+template <typename K> static int coop_grid(ws_context *c, K kernel, int threads, size_t smem, int want)
 {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NTHR, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
     if (per_sm < 1) per_sm = 1;
-    int maxg = per_sm * c->num_sms;
+    const int maxg = per_sm * c->num_sms;
     if (want < 1) want = 1;
     return want < maxg ? want : maxg;
 }
@@ -36,11 +36,23 @@ static inline cudaError_t reset_barrier(ws_context *c, cudaStream_t s)
 }
 
 template <typename K, typename... Args>
-static cudaError_t launch_coop(K kernel, int grid, cudaStream_t s, Args... args)
+static cudaError_t launch_coop(K kernel, int grid, int threads, size_t smem, cudaStream_t s, Args... args)
 {
     void *argv[] = {(void *)&args...};
-    return cudaLaunchCooperativeKernel((const void *)kernel, dim3(grid), dim3(NTHR), argv, 0, s);
+    return cudaLaunchCooperativeKernel((const void *)kernel, dim3(grid), dim3(threads), argv, smem, s);
 }
+
+template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+static inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// ---------------------------------------------------------------------------
+// step I alone (debug entry point)
+// ---------------------------------------------------------------------------
 
 template <typename T, int CONN> static ws_status run_step1(ws_context *c, const void *grad, const Geo &geo,
                                                            uint8_t *states, int32_t *arrows, cudaStream_t s)
@@ -54,27 +66,38 @@ template <typename T, int CONN> static ws_status run_step1(ws_context *c, const 
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "step1 launch");
 }
 
-// Steps I and II; leaves arrows in w.par, states in w.st, distances in w.aux.
+// ---------------------------------------------------------------------------
+// the tiled watershed core
+// ---------------------------------------------------------------------------
+
+// Steps I and II: leaves in-tile path ends in w.par, step II distances of
+// the plateau tiles in w.dist, the plateau tiles in w.tlist.
 template <typename T, int CONN> static ws_status run_front(ws_context *c, const T *g, const Geo &geo,
-                                                           cudaStream_t s)
+                                                           const TileGeo &tg, cudaStream_t s)
 {
-    TileGeo tg = make_tilegeo<CONN>(geo);
-    size_t nblk = ((size_t)geo.N + CHUNK - 1) / CHUNK;
-    ws_status st = ensure_pixels(c, geo.N, tg.ntiles, nblk);
-    if (st != WS_OK) return st;
+    using C = TC<CONN>;
     Workspace &w = c->w;
+    ws_status st = ensure_pixels(c, geo.N, tg.ntiles);
+    if (st != WS_OK) return st;
     cudaError_t e = cudaMemsetAsync(w.act, 0, 2 * (size_t)tg.ntiles, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 16, s);
     if (e == cudaSuccess) e = reset_barrier(c, s);
     if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
     {
         PhaseScope ps(c, PH_STEP1, s);
-        k_step1<T, CONN><<<pixel_grid(c, geo.N), NTHR, 0, s>>>(g, geo, w.par, w.st, w.aux, w.act, tg);
+        const size_t smem = align16((size_t)C::HS * sizeof(T)) + (size_t)C::NPIX * 4;
+        if ((e = allow_smem(k_init<T, CONN>, smem)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
+        k_init<T, CONN><<<tg.ntiles, C::NT, smem, s>>>(g, geo, tg, w.par, w.aux, w.dist, w.plat, w.act, w.tlist,
+                                                       w.roots, w.counters);
         c->launches += 1;
     }
     {
         PhaseScope ps(c, PH_PLATEAU, s);
-        int grid = coop_grid(c, k_plateau<T, CONN>, tg.ntiles);
-        e = launch_coop(k_plateau<T, CONN>, grid, s, g, geo, tg, w.aux, w.act, c->status, tune_plateau_cap(c),
+        const size_t smem = (size_t)C::HS * 8;
+        if ((e = allow_smem(k_plateau2<T, CONN>, smem)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
+        const int grid = coop_grid(c, k_plateau2<T, CONN>, C::NT, smem, tg.ntiles);
+        e = launch_coop(k_plateau2<T, CONN>, grid, C::NT, smem, s, g, geo, tg, w.dist, (const uint8_t *)w.plat, w.act,
+                        (const int32_t *)w.tlist, (const int32_t *)w.counters, c->status, tune_plateau_cap(c),
                         tune_timeout_ns(c));
         c->launches += 1;
     }
@@ -82,64 +105,172 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
     return WS_OK;
 }
 
-template <typename T, int CONN> static ws_status run_plateau_distance(ws_context *c, const void *grad,
-                                                                      const Geo &geo, int32_t *dist,
-                                                                      cudaStream_t s)
+// Whole watershed: roots in w.par, canonical id of every root in w.aux,
+// K0 in w.counters[CNT_ROOTS]; with do_rag, the region table holds every
+// adjacent pair of basins (keyed by root pixel) with its pass value.
+template <typename T, int CONN> static ws_status run_core(ws_context *c, const T *g, const Geo &geo, bool do_rag,
+                                                          cudaStream_t s)
 {
-    ws_status st = run_front<T, CONN>(c, (const T *)grad, geo, s);
+    using C = TC<CONN>;
+    const TileGeo tg = tiles_for<CONN>(geo);
+    ws_status st = run_front<T, CONN>(c, g, geo, tg, s);
     if (st != WS_OK) return st;
-    k_dist_out<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo.N, c->w.aux, dist);
+    Workspace &w = c->w;
+    cudaError_t e = cudaSuccess;
+    {
+        PhaseScope ps(c, PH_RESOLVE, s);
+        const int grid = tg.ntiles < c->num_sms * 8 ? tg.ntiles : c->num_sms * 8;
+        k_resolve2<T, CONN><<<grid, C::NT, 0, s>>>(g, geo, tg, w.par, w.dist, w.plat, w.tlist, w.counters,
+                                                   c->status);
+        c->launches += 1;
+    }
+    if ((e = reset_barrier(c, s)) != cudaSuccess) return set_cuda_error(c, e, "memset");
+    {
+        PhaseScope ps(c, PH_JUMP, s);
+        const int grid = coop_grid(c, k_jump2<CONN>, NTHR, 0, c->num_sms * 8);
+        e = launch_coop(k_jump2<CONN>, grid, NTHR, 0, s, geo, tg, w.par, (const int32_t *)w.dist,
+                        (const int32_t *)w.tlist, w.counters, w.roots, tune_rr(c), c->status, tune_jump_cap(c),
+                        tune_timeout_ns(c));
+        c->launches += 1;
+        if (e != cudaSuccess) return set_cuda_error(c, e, "jump launch");
+    }
+    if (do_rag) {
+        const int halfn = Nb<CONN>::n / 2;
+        size_t want = (size_t)geo.N * halfn / 8;
+        if (c->tun.edge_capacity > 0) want = (size_t)c->tun.edge_capacity;
+        size_t cap = 1 << 16;
+        while (cap < want && cap < ((size_t)1 << 28)) cap <<= 1;
+        if ((st = ensure_edges(c, cap)) != WS_OK) return st;
+    }
+    {
+        PhaseScope ps(c, PH_RAG, s);
+        const size_t smem = (size_t)C::HASH * 12 + (size_t)C::BS * 4 + align16((size_t)C::BS * sizeof(T));
+        if ((e = allow_smem(k_label<T, CONN>, smem)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
+        k_label<T, CONN><<<tg.ntiles, C::NT, smem, s>>>(g, geo, tg, w.par, w.aux, do_rag ? 1 : 0, w.keys, w.vals,
+                                                        w.slots, w.ecount,
+                                                        (unsigned long long)(w.edge_cap ? w.edge_cap - 1 : 0),
+                                                        c->status);
+        c->launches += 1;
+    }
+    {
+        PhaseScope ps(c, PH_COMPACT, s);
+        const int ng = (int)((geo.N + 1023) / 1024), nw = (int)((geo.N + 31) / 32);
+        const int nch = (ng + SCAN_CHUNK - 1) / SCAN_CHUNK;
+        const int rg = c->num_sms * 4;
+        k_rank_mark<<<rg, NTHR, 0, s>>>(w.roots, w.counters, w.aux, w.rootm, w.bitmap);
+        k_rank_groups<<<(ng + NTHR / 32 - 1) / (NTHR / 32), NTHR, 0, s>>>(w.bitmap, nw, w.gcnt, ng);
+        k_scan_chunks<<<nch, NTHR, 0, s>>>(w.gcnt, ng, w.csum);
+        k_scan<<<1, 1024, 0, s>>>(w.csum, nch, nullptr);
+        k_scan_add<<<nch, NTHR, 0, s>>>(w.gcnt, ng, w.csum);
+        k_rank_assign<<<rg, NTHR, 0, s>>>(w.roots, w.counters, w.rootm, w.bitmap, w.gcnt, w.aux);
+        k_rank_clear<<<rg, NTHR, 0, s>>>(w.counters, w.rootm, w.bitmap);
+        c->launches += 7;
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "watershed launch");
+}
+
+// One pass writing level 0 (canonical ids) and levels 1..NL-1.
+static inline ws_status run_write(ws_context *c, const Geo &geo, int NL, int32_t *out, cudaStream_t s)
+{
+    Workspace &w = c->w;
+    PhaseScope ps(c, PH_LEVEL_WRITE, s);
+    const bool vec = (geo.N % 4 == 0) && (((uintptr_t)out & 15) == 0);
+    const int grid = pixel_grid(c, vec ? geo.N / 4 : geo.N);
+    if (vec)
+        k_write_vec<<<grid, NTHR, 0, s>>>(geo.N, w.par, w.aux, w.gmap, w.kmax, NL, out);
+    else
+        k_write_scalar<<<grid, NTHR, 0, s>>>(geo.N, w.par, w.aux, w.gmap, w.kmax, NL, out);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "plateau distance");
+    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "write launch");
+}
+
+// Region-graph merging for levels 1..NL-1 over the filled region table;
+// idmap maps table keys to canonical level-0 ids (nullptr: keys are ids).
+static inline ws_status run_levels(ws_context *c, int NL, const int32_t *idmap, const int32_t *k0_ptr,
+                                   int32_t *counts, cudaStream_t s)
+{
+    Workspace &w = c->w;
+    cudaError_t e = reset_barrier(c, s);
+    if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
+    PhaseScope ps(c, PH_LEVELS, s);
+    int grid = coop_grid(c, k_levels, NTHR, 0, c->num_sms * 4);
+    if (grid > 4096) grid = 4096;
+    e = launch_coop(k_levels, grid, NTHR, 0, s, (const unsigned long long *)w.keys, (const uint32_t *)w.vals,
+                    (const int32_t *)w.slots, (const int32_t *)w.ecount, idmap, k0_ptr, NL, w.gmap, w.kmax,
+                    w.newmin, w.uf, w.rank, w.bsum, counts, c->status, tune_timeout_ns(c));
+    c->launches += 1;
+    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "levels launch");
+}
+
+static inline ws_status run_cleanup(ws_context *c, cudaStream_t s)
+{
+    Workspace &w = c->w;
+    PhaseScope ps(c, PH_CLEANUP, s);
+    k_hash_clear<<<c->num_sms * 4, NTHR, 0, s>>>(w.keys, w.vals, w.slots, w.ecount);
+    k_reset_count<<<1, 32, 0, s>>>(w.ecount, c->status);
+    c->launches += 2;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "cleanup launch");
 }
 
 template <typename T, int CONN> static ws_status run_watershed(ws_context *c, const void *grad, const Geo &geo,
                                                                int32_t *labels, int32_t *count, cudaStream_t s)
 {
-    const T *g = (const T *)grad;
-    ws_status st = run_front<T, CONN>(c, g, geo, s);
+    ws_status st = run_core<T, CONN>(c, (const T *)grad, geo, false, s);
     if (st != WS_OK) return st;
-    Workspace &w = c->w;
-    {
-        PhaseScope ps(c, PH_RESOLVE, s);
-        k_resolve_union<T, CONN><<<pixel_grid(c, geo.N), NTHR, 0, s>>>(g, geo, w.par, w.st, w.aux, c->status);
+    if ((st = run_write(c, geo, 1, labels, s)) != WS_OK) return st;
+    if (count) {
+        k_copy_int<<<1, 32, 0, s>>>(c->w.counters + CNT_ROOTS, count);
         c->launches += 1;
     }
-    cudaError_t e = reset_barrier(c, s);
-    if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
-    {
-        PhaseScope ps(c, PH_JUMP, s);
-        int grid = coop_grid(c, k_jump, (geo.N + NTHR - 1) / NTHR);
-        e = launch_coop(k_jump, grid, s, geo.N, w.par, w.aux, tune_rr(c), c->status, tune_jump_cap(c),
-                        tune_timeout_ns(c));
-        c->launches += 1;
-    }
-    if (e != cudaSuccess) return set_cuda_error(c, e, "jump launch");
-    {
-        PhaseScope ps(c, PH_COMPACT, s);
-        const int nblk = (geo.N + CHUNK - 1) / CHUNK;
-        k_flags<<<nblk, NTHR, 0, s>>>(geo.N, w.par, w.aux, w.st, w.blk);
-        k_scan<<<1, 1024, 0, s>>>(w.blk, nblk, w.kcount);
-        k_assign<<<nblk, NTHR, 0, s>>>(geo.N, w.par, w.aux, w.st, w.blk);
-        k_label<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo.N, w.par, w.aux, labels);
-        c->launches += 4;
-        if (count) {
-            k_copy_int<<<1, 32, 0, s>>>(w.kcount, count);
-            c->launches += 1;
-        }
-    }
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "watershed launch");
 }
+
+template <typename T, int CONN> static ws_status run_segment(ws_context *c, const void *grad, const Geo &geo, int NL,
+                                                             int32_t *levels, int32_t *counts, cudaStream_t s)
+{
+    Workspace &w = c->w;
+    ws_status st;
+    // distinct minimal plateaux are never adjacent, so K0 <= ceil(N / 2)
+    if (NL > 1 && (st = ensure_regions(c, (size_t)geo.N / 2 + 2, NL - 1)) != WS_OK) return st;
+    if ((st = run_core<T, CONN>(c, (const T *)grad, geo, NL > 1, s)) != WS_OK) return st;
+    if (NL > 1) {
+        if ((st = run_levels(c, NL, w.aux, w.counters + CNT_ROOTS, counts, s)) != WS_OK) return st;
+    } else if (counts) {
+        k_copy_int<<<1, 32, 0, s>>>(w.counters + CNT_ROOTS, counts);
+        c->launches += 1;
+    }
+    if ((st = run_write(c, geo, NL, levels, s)) != WS_OK) return st;
+    if (NL > 1) return run_cleanup(c, s);
+    return WS_OK;
+}
+
+template <typename T, int CONN> static ws_status run_plateau_distance(ws_context *c, const void *grad,
+                                                                      const Geo &geo, int32_t *dist,
+                                                                      cudaStream_t s)
+{
+    const TileGeo tg = tiles_for<CONN>(geo);
+    ws_status st = run_front<T, CONN>(c, (const T *)grad, geo, tg, s);
+    if (st != WS_OK) return st;
+    k_dist_out2<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo, tg, c->w.par, c->w.dist, c->w.plat, dist);
+    c->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "plateau distance");
+}
+
+// ---------------------------------------------------------------------------
+// waterfall above caller-provided level-0 labels
+// ---------------------------------------------------------------------------
 
 template <typename T, int CONN> static ws_status run_waterfall(ws_context *c, const int32_t *labels0,
                                                                const void *grad, const Geo &geo, int NL,
                                                                int32_t *levels, int32_t *counts, size_t kmax,
                                                                cudaStream_t s)
 {
-    // levels: NL-1 planes.  c->w.kcount holds K0 (set by the watershed, or by
-    // the caller of this function from the labels); K0 <= kmax.
+    // levels: NL-1 planes.  c->w.kcount holds K0 (from the labels); K0 <= kmax.
     Workspace &w = c->w;
     if (NL <= 1) {
         if (counts) {
@@ -165,38 +296,20 @@ template <typename T, int CONN> static ws_status run_waterfall(ws_context *c, co
                                                              (unsigned long long)(w.edge_cap - 1), c->status);
         c->launches += 1;
     }
-    cudaError_t e = reset_barrier(c, s);
-    if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
-    {
-        PhaseScope ps(c, PH_LEVELS, s);
-        int grid = coop_grid(c, k_levels, c->num_sms * 4);
-        if (grid > 4096) grid = 4096;
-        e = launch_coop(k_levels, grid, s, (const unsigned long long *)w.keys, (const uint32_t *)w.vals,
-                        (const int32_t *)w.slots, (const int32_t *)w.ecount, (const int32_t *)w.kcount, NL, w.gmap,
-                        w.kmax, w.newmin, w.uf, w.rank, w.bsum, counts, c->status, tune_timeout_ns(c));
-        c->launches += 1;
-    }
-    if (e != cudaSuccess) return set_cuda_error(c, e, "levels launch");
+    if ((st = run_levels(c, NL, nullptr, w.kcount, counts, s)) != WS_OK) return st;
     {
         PhaseScope ps(c, PH_LEVEL_WRITE, s);
         k_level_write<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo.N, labels0, w.gmap, w.kmax, NL - 1, levels);
         c->launches += 1;
     }
-    {
-        PhaseScope ps(c, PH_CLEANUP, s);
-        k_hash_clear<<<pixel_grid(c, (long long)geo.N / 4 + 1), NTHR, 0, s>>>(w.keys, w.vals, w.slots, w.ecount);
-        k_reset_count<<<1, 32, 0, s>>>(w.ecount, c->status);
-        c->launches += 2;
-    }
-    e = cudaGetLastError();
-    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "waterfall launch");
+    return run_cleanup(c, s);
 }
 
 template <typename T, int CONN> struct Inst {
     static const Launchers *get()
     {
         static const Launchers L = {&run_watershed<T, CONN>, &run_step1<T, CONN>, &run_plateau_distance<T, CONN>,
-                                    &run_waterfall<T, CONN>};
+                                    &run_waterfall<T, CONN>, &run_segment<T, CONN>};
         return &L;
     }
 };

@@ -1,0 +1,711 @@
+// ws_tiles.cuh -- the fused, tiled watershed pipeline of libws.
+//
+// The image is cut into tiles (2D 64 x 32 pixels, 3D 32 x 16 x 16 voxels);
+// one CTA owns one tile.  Pixel work runs in three passes over HBM, with the
+// sparse plateau work (Alg. 1 step II, step IV) and the small region-graph
+// work in between:
+//
+//   k_init      Alg. 1 step I (Eq. 1) on the tile + 1-pixel halo staged in
+//               shared memory, then step III *inside the tile*: every pixel
+//               follows its arrows through shared memory until the path
+//               leaves the tile, reaches a minimum, or reaches a plateau
+//               pixel.  Writes that end point (par), flags tiles that hold
+//               plateau pixels and lists the minima.
+//   k_plateau2  step II distances on the listed plateau tiles only (in-tile
+//               relaxation with a frozen halo, device-wide rounds; the fixed
+//               point of Alg. 3)
+//   k_resolve2  step II pointer choice, step IV Union of minimal plateaux
+//   k_jump2     step III for plateau tiles (pointer jumping rounds), lists
+//               the minimal-plateau roots
+//   k_label     per tile: final root of every pixel (chasing the few
+//               tile-to-tile hops left), smallest pixel index per basin, and
+//               Alg. 5 step V on pixel pairs (pass values, deduplicated in a
+//               shared-memory hash before the global region table)
+//   k_rank_*    canonical ids: rank of every basin's smallest pixel index
+//               among all of them, by a bitmap over pixel indices
+//   k_write     per pixel: canonical id of its root and its id on every
+//               waterfall level, one pass writing all NL planes
+#pragma once
+
+#include "ws_kernels.cuh"
+
+namespace ws {
+
+template <int CONN> struct TT;
+template <> struct TT<4> {
+    static constexpr int TX = 64, TY = 32, TZ = 1, NT = 256;
+};
+template <> struct TT<8> {
+    static constexpr int TX = 64, TY = 32, TZ = 1, NT = 256;
+};
+template <> struct TT<6> {
+    static constexpr int TX = 32, TY = 16, TZ = 16, NT = 512;
+};
+
+template <int CONN> struct TC {
+    static constexpr int TX = TT<CONN>::TX, TY = TT<CONN>::TY, TZ = TT<CONN>::TZ, NT = TT<CONN>::NT;
+    static constexpr bool D3 = TZ > 1;
+    static constexpr int NPIX = TX * TY * TZ;
+    static constexpr int PER = NPIX / NT;
+    // halo box on both sides (k_init, k_plateau2)
+    static constexpr int HX = TX + 2, HY = TY + 2, HZ = D3 ? TZ + 2 : 1;
+    static constexpr int HS = HX * HY * HZ;
+    // forward box of k_label: +1 on every axis, and -1 in x for 8-connectivity
+    static constexpr int BXL = CONN == 8 ? 1 : 0;
+    static constexpr int BX = TX + 1 + BXL, BY = TY + 1, BZ = D3 ? TZ + 1 : 1;
+    static constexpr int BS = BX * BY * BZ;
+    static constexpr int HASH = 1024;  // shared-memory edge slots per CTA
+};
+
+inline TileGeo make_tiles(const Geo &g, int TX, int TY, int TZ)
+{
+    TileGeo t;
+    t.TX = TX;
+    t.TY = TY;
+    t.TZ = TZ;
+    t.ntx = (g.W + TX - 1) / TX;
+    t.nty = (g.H + TY - 1) / TY;
+    t.ntz = (g.D + TZ - 1) / TZ;
+    t.ntiles = t.ntx * t.nty * t.ntz;
+    return t;
+}
+
+template <int CONN> inline TileGeo tiles_for(const Geo &g)
+{
+    return make_tiles(g, TT<CONN>::TX, TT<CONN>::TY, TT<CONN>::TZ);
+}
+
+// counters[] slots in the workspace
+enum { CNT_TILES = 0, CNT_ROOTS = 1, CNT_K0 = 2, CNT_NGROUPS = 3 };
+
+__device__ __forceinline__ int enc_final(int g) { return -1 - g; }
+__device__ __forceinline__ int dec_final(int e) { return -1 - e; }
+
+template <int CONN>
+__device__ __forceinline__ void tile_origin(const TileGeo &tg, int t, int &x0, int &y0, int &z0)
+{
+    const int tx = t % tg.ntx, ty = (t / tg.ntx) % tg.nty, tz = t / (tg.ntx * tg.nty);
+    x0 = tx * TT<CONN>::TX;
+    y0 = ty * TT<CONN>::TY;
+    z0 = tz * TT<CONN>::TZ;
+}
+
+__device__ __forceinline__ int tile_of(const TileGeo &tg, int x, int y, int z)
+{
+    return ((z / tg.TZ) * tg.nty + y / tg.TY) * tg.ntx + x / tg.TX;
+}
+
+// state codes kept in registers by k_init
+enum : int { ST0 = 0, ST1 = 1, STP = 2, STOUT = 3 };
+
+// ---------------------------------------------------------------------------
+// k_init: step I + in-tile path reduction
+// ---------------------------------------------------------------------------
+
+template <typename T, int CONN>
+__global__ void __launch_bounds__(TT<CONN>::NT) k_init(const T *__restrict__ g, Geo geo, TileGeo tg,
+                                                       int32_t *__restrict__ par, int32_t *__restrict__ mi,
+                                                       int32_t *__restrict__ dist, uint8_t *__restrict__ plat,
+                                                       uint8_t *__restrict__ act, int32_t *__restrict__ tlist,
+                                                       int32_t *__restrict__ roots, int32_t *counters)
+{
+    using C = TC<CONN>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *gs = (T *)smem;
+    int *nx = (int *)(smem + ((C::HS * sizeof(T) + 15) & ~15));
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int t = blockIdx.x;
+    int x0, y0, z0;
+    tile_origin<CONN>(tg, t, x0, y0, z0);
+
+    for (int i = tid; i < C::HS; i += C::NT) {
+        const int hx = i % C::HX, hy = (i / C::HX) % C::HY, hz = i / (C::HX * C::HY);
+        const int x = x0 - 1 + hx, y = y0 - 1 + hy, z = C::D3 ? z0 - 1 + hz : 0;
+        T v = 0;
+        if (x >= 0 && x < geo.W && y >= 0 && y < geo.H && z >= 0 && z < geo.D) v = g[(z * geo.H + y) * geo.W + x];
+        gs[i] = v;
+    }
+    __syncthreads();
+
+    int st[C::PER];
+    int plateau = 0;
+#pragma unroll
+    for (int k = 0; k < C::PER; k++) {
+        const int i = tid + k * C::NT;
+        const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+        if (x >= geo.W || y >= geo.H || z >= geo.D) {
+            st[k] = STOUT;
+            nx[i] = enc_final(0);
+            continue;
+        }
+        const int p = (z * geo.H + y) * geo.W + x;
+        const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * C::HX + lx + 1;
+        const unsigned gp = gs[h];
+        unsigned m = 0xffffffffu;
+        int qn = -1;
+#pragma unroll
+        for (int n = 0; n < Nb<CONN>::n; n++) {
+            const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
+            if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
+            const unsigned v = gs[h + (Nb<CONN>::dz(n) * C::HY + Nb<CONN>::dy(n)) * C::HX + Nb<CONN>::dx(n)];
+            if (v <= m) {  // ascending index order: ties go to the later (larger) neighbour
+                m = v;
+                qn = n;
+            }
+        }
+        if (qn < 0 || m > gp) {
+            st[k] = ST1;
+            nx[i] = enc_final(p);
+        } else if (m < gp) {
+            st[k] = ST0;
+            const int lxx = lx + Nb<CONN>::dx(qn), lyy = ly + Nb<CONN>::dy(qn), lzz = lz + Nb<CONN>::dz(qn);
+            if (lxx >= 0 && lxx < C::TX && lyy >= 0 && lyy < C::TY && lzz >= 0 && lzz < C::TZ)
+                nx[i] = (lzz * C::TY + lyy) * C::TX + lxx;
+            else
+                nx[i] = enc_final(p + (Nb<CONN>::dz(qn) * geo.H + Nb<CONN>::dy(qn)) * geo.W + Nb<CONN>::dx(qn));
+        } else {
+            st[k] = STP;  // plateau pixel: resolved by step II / step IV
+            nx[i] = enc_final(p);
+            plateau = 1;
+        }
+    }
+    __syncthreads();
+
+    // step III inside the tile: follow arrows through shared memory
+    volatile int *vnx = nx;
+#pragma unroll
+    for (int k = 0; k < C::PER; k++) {
+        const int i = tid + k * C::NT;
+        int c = vnx[i];
+        if (c < 0) continue;
+        for (int guard = 0; c >= 0 && guard < C::NPIX; guard++) c = vnx[c];
+        vnx[i] = c;
+    }
+
+    int nroot = 0;
+#pragma unroll
+    for (int k = 0; k < C::PER; k++) {
+        const int i = tid + k * C::NT;
+        if (st[k] == STOUT) continue;
+        const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+        const int p = ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
+        par[p] = dec_final(vnx[i]);
+        if (st[k] != ST0) mi[p] = 0x7fffffff;
+        nroot += st[k] == ST1;
+    }
+    // list the strict minima (roots known now)
+#pragma unroll
+    for (int k = 0; k < C::PER; k++) {
+        const bool isr = st[k] == ST1;
+        const unsigned b = __ballot_sync(0xffffffffu, isr);
+        if (!b) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(counters + CNT_ROOTS, __popc(b));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (isr) {
+            const int i = tid + k * C::NT;
+            const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+            roots[base + __popc(b & ((1u << lane) - 1u))] = ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
+        }
+    }
+    (void)nroot;
+    if (__syncthreads_or(plateau)) {
+#pragma unroll
+        for (int k = 0; k < C::PER; k++) {
+            if (st[k] == STOUT) continue;
+            const int i = tid + k * C::NT;
+            const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+            const int p = ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
+            dist[p] = st[k] == ST0 ? 0 : (st[k] == ST1 ? -2 : INF_D);
+        }
+        if (tid == 0) {
+            plat[t] = 1;
+            act[t] = 1;
+            tlist[atomicAdd(counters + CNT_TILES, 1)] = t;
+        }
+    } else if (tid == 0) {
+        plat[t] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_plateau2: step II distances on plateau tiles (cooperative)
+// ---------------------------------------------------------------------------
+
+template <typename T, int CONN>
+__global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const T *__restrict__ g, Geo geo, TileGeo tg,
+                                                           int32_t *dist, const uint8_t *__restrict__ plat,
+                                                           uint8_t *act, const int32_t *__restrict__ tlist,
+                                                           const int32_t *counters, DevStatus *status,
+                                                           int round_cap, unsigned long long timeout_ns)
+{
+    using C = TC<CONN>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int *gs = (int *)smem;
+    int *ds = gs + C::HS;
+    __shared__ int flag_s;
+    const int tid = threadIdx.x;
+    const int ntl = counters[CNT_TILES];
+    uint8_t *act0 = act, *act1 = act + tg.ntiles;
+
+    for (int r = 0;; r++) {
+        uint8_t *cur = (r & 1) ? act1 : act0;
+        uint8_t *nxt = (r & 1) ? act0 : act1;
+        if (blockIdx.x == 0 && tid == 0) status->changed[(r + 1) % 3] = 0;
+        for (int j = blockIdx.x; j < ntl; j += gridDim.x) {
+            const int t = tlist[j];
+            __syncthreads();
+            if (tid == 0) {
+                flag_s = *(volatile uint8_t *)(cur + t);
+                if (flag_s) cur[t] = 0;
+            }
+            __syncthreads();
+            if (!flag_s) continue;
+            int x0, y0, z0;
+            tile_origin<CONN>(tg, t, x0, y0, z0);
+            for (int i = tid; i < C::HS; i += C::NT) {
+                const int hx = i % C::HX, hy = (i / C::HX) % C::HY, hz = i / (C::HX * C::HY);
+                const int x = x0 - 1 + hx, y = y0 - 1 + hy, z = C::D3 ? z0 - 1 + hz : 0;
+                if (x >= 0 && x < geo.W && y >= 0 && y < geo.H && z >= 0 && z < geo.D) {
+                    const int q = (z * geo.H + y) * geo.W + x;
+                    gs[i] = (int)g[q];
+                    // a pixel of a tile without plateau pixels that is equal to a
+                    // plateau neighbour has a lower neighbour: distance 0
+                    ds[i] = plat[tile_of(tg, x, y, z)] ? __ldcg(dist + q) : 0;
+                } else {
+                    gs[i] = -1;
+                    ds[i] = INF_D;
+                }
+            }
+            __syncthreads();
+            int orig[C::PER];
+#pragma unroll
+            for (int k = 0; k < C::PER; k++) {
+                const int i = tid + k * C::NT;
+                const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+                orig[k] = ds[((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * C::HX + lx + 1];
+            }
+            for (int it = 0; it < 4 * C::NPIX + 8; it++) {
+                int ch = 0;
+#pragma unroll
+                for (int k = 0; k < C::PER; k++) {
+                    const int i = tid + k * C::NT;
+                    const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+                    const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * C::HX + lx + 1;
+                    const int gv = gs[h];
+                    const int d = ds[h];
+                    if (gv < 0 || d <= 0) continue;
+                    int best = d;
+#pragma unroll
+                    for (int n = 0; n < Nb<CONN>::n; n++) {
+                        const int hn = h + (Nb<CONN>::dz(n) * C::HY + Nb<CONN>::dy(n)) * C::HX + Nb<CONN>::dx(n);
+                        if (gs[hn] == gv) best = imin(best, ds[hn] + 1);
+                    }
+                    if (best < d) {
+                        ds[h] = best;
+                        ch = 1;
+                    }
+                }
+                if (!__syncthreads_or(ch)) break;
+            }
+            int border = 0;
+#pragma unroll
+            for (int k = 0; k < C::PER; k++) {
+                const int i = tid + k * C::NT;
+                const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+                const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * C::HX + lx + 1;
+                if (ds[h] != orig[k]) {
+                    __stcg(dist + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx, ds[h]);
+                    if (lx == 0 || lx == C::TX - 1 || ly == 0 || ly == C::TY - 1 ||
+                        (C::D3 && (lz == 0 || lz == C::TZ - 1)))
+                        border = 1;
+                }
+            }
+            if (__syncthreads_or(border) && tid == 0) {
+                const int tx = t % tg.ntx, ty = (t / tg.ntx) % tg.nty, tz = t / (tg.ntx * tg.nty);
+                for (int dz = (C::D3 ? -1 : 0); dz <= (C::D3 ? 1 : 0); dz++)
+                    for (int dy = -1; dy <= 1; dy++)
+                        for (int dx = -1; dx <= 1; dx++) {
+                            const int ax = tx + dx, ay = ty + dy, az = tz + dz;
+                            if (ax < 0 || ax >= tg.ntx || ay < 0 || ay >= tg.nty || az < 0 || az >= tg.ntz)
+                                continue;
+                            const int nt = (az * tg.nty + ay) * tg.ntx + ax;
+                            if (nt != t && plat[nt]) nxt[nt] = 1;
+                        }
+                atomicAdd(&status->changed[r % 3], 1);
+            }
+        }
+        __threadfence();
+        if (!grid_barrier(status, timeout_ns)) return;
+        if (*(volatile int *)&status->changed[r % 3] == 0) {
+            if (blockIdx.x == 0 && tid == 0) status->rounds_plateau = r + 1;
+            return;
+        }
+        if (r + 1 >= round_cap) {
+            if (blockIdx.x == 0 && tid == 0) record_error(status, DEV_NONCONVERGED, 2);
+            return;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_resolve2: step II pointer choice and step IV Union on plateau tiles
+// ---------------------------------------------------------------------------
+
+template <typename T, int CONN>
+__global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const T *__restrict__ g, Geo geo, TileGeo tg,
+                                                           int32_t *par, const int32_t *__restrict__ dist,
+                                                           const uint8_t *__restrict__ plat,
+                                                           const int32_t *__restrict__ tlist,
+                                                           const int32_t *counters, DevStatus *status)
+{
+    using C = TC<CONN>;
+    const int ntl = counters[CNT_TILES];
+    for (int j = blockIdx.x; j < ntl; j += gridDim.x) {
+        int x0, y0, z0;
+        tile_origin<CONN>(tg, tlist[j], x0, y0, z0);
+        for (int i = threadIdx.x; i < C::NPIX; i += C::NT) {
+            const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+            const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+            if (x >= geo.W || y >= geo.H || z >= geo.D) continue;
+            const int p = (z * geo.H + y) * geo.W + x;
+            const int d = dist[p];
+            if (d <= 0) continue;   // state 0 or minimum
+            const unsigned gp = g[p];
+            if (d < INF_D) {
+                int best = -1;
+#pragma unroll
+                for (int n = 0; n < Nb<CONN>::n; n++) {
+                    const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
+                    if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
+                    const int q = (zz * geo.H + yy) * geo.W + xx;
+                    if (g[q] != gp) continue;
+                    const int dq = plat[tile_of(tg, xx, yy, zz)] ? dist[q] : 0;
+                    if (dq == d - 1 && q > best) best = q;
+                }
+                if (best < 0) {
+                    record_error(status, DEV_NONCONVERGED, 7);
+                    best = p;
+                }
+                par[p] = best;
+            } else {
+#pragma unroll
+                for (int n = Half<CONN>::first; n < Nb<CONN>::n; n++) {
+                    const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
+                    if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
+                    if (!plat[tile_of(tg, xx, yy, zz)]) continue;
+                    const int q = (zz * geo.H + yy) * geo.W + xx;
+                    if (dist[q] >= INF_D && g[q] == gp) uf_union(par, p, q, status);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_jump2: step III on plateau tiles (cooperative), lists minimal-plateau roots
+// ---------------------------------------------------------------------------
+
+template <int CONN>
+__global__ void __launch_bounds__(NTHR) k_jump2(Geo geo, TileGeo tg, int32_t *par, const int32_t *__restrict__ dist,
+                                                const int32_t *__restrict__ tlist, int32_t *counters,
+                                                int32_t *roots, int RR, DevStatus *status, int round_cap,
+                                                unsigned long long timeout_ns)
+{
+    using C = TC<CONN>;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const long long total = (long long)counters[CNT_TILES] * C::NPIX;
+    const long long stride = (long long)gridDim.x * NTHR;
+    const long long iters = (total + stride - 1) / stride;
+    for (int r = 0;; r++) {
+        if (blockIdx.x == 0 && tid == 0) status->changed[(r + 1) % 3] = 0;
+        int ch = 0;
+        for (long long it = 0; it < iters; it++) {
+            const long long e = it * stride + (long long)blockIdx.x * NTHR + tid;
+            if (e >= total) continue;
+            int x0, y0, z0;
+            tile_origin<CONN>(tg, tlist[e / C::NPIX], x0, y0, z0);
+            const int i = (int)(e % C::NPIX);
+            const int x = x0 + i % C::TX, y = y0 + (i / C::TX) % C::TY, z = z0 + i / (C::TX * C::TY);
+            if (x >= geo.W || y >= geo.H || z >= geo.D) continue;
+            const int p = (z * geo.H + y) * geo.W + x;
+            const int l0 = __ldcg(par + p);
+            int l = l0;
+            for (int k = 0; k < RR; k++) {
+                const int l2 = __ldcg(par + l);
+                if (l2 == l) break;
+                l = l2;
+            }
+            if (l != l0) {
+                __stcg(par + p, l);
+                ch = 1;
+            }
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, ch);
+        if (lane == 0 && b) atomicAdd(&status->changed[r % 3], 1);
+        __threadfence();
+        if (!grid_barrier(status, timeout_ns)) return;
+        if (*(volatile int *)&status->changed[r % 3] == 0) {
+            if (blockIdx.x == 0 && tid == 0) status->rounds_jump = r + 1;
+            break;
+        }
+        if (r + 1 >= round_cap) {
+            if (blockIdx.x == 0 && tid == 0) record_error(status, DEV_NONCONVERGED, 5);
+            return;
+        }
+    }
+    // roots of minimal plateaux
+    for (long long it = 0; it < iters; it++) {
+        const long long e = it * stride + (long long)blockIdx.x * NTHR + tid;
+        bool isr = false;
+        int p = 0;
+        if (e < total) {
+            int x0, y0, z0;
+            tile_origin<CONN>(tg, tlist[e / C::NPIX], x0, y0, z0);
+            const int i = (int)(e % C::NPIX);
+            const int x = x0 + i % C::TX, y = y0 + (i / C::TX) % C::TY, z = z0 + i / (C::TX * C::TY);
+            if (x < geo.W && y < geo.H && z < geo.D) {
+                p = (z * geo.H + y) * geo.W + x;
+                isr = dist[p] >= INF_D && __ldcg(par + p) == p;
+            }
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, isr);
+        if (!b) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(counters + CNT_ROOTS, __popc(b));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (isr) roots[base + __popc(b & ((1u << lane) - 1u))] = p;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_label: final roots, smallest index per basin, pass values (Alg. 5 step V)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int chase_root(int32_t *par, int r, DevStatus *status)
+{
+    for (int guard = 0; guard < (1 << 22); guard++) {
+        const int u = par[r];
+        if (u == r) return r;
+        r = u;
+    }
+    record_error(status, DEV_NONCONVERGED, 9);
+    return r;
+}
+
+__device__ __forceinline__ void smem_edge_insert(unsigned long long key, unsigned h, unsigned long long *hk,
+                                                 unsigned *hv, int nslots, unsigned long long *keys,
+                                                 uint32_t *vals, int32_t *slots, int32_t *ecount,
+                                                 unsigned long long gmask, DevStatus *status)
+{
+    unsigned s = (unsigned)(mix64(key) & (unsigned long long)(nslots - 1));
+    for (int probe = 0; probe < 32; probe++) {
+        unsigned long long k = hk[s];
+        if (k == key) {
+            atomicMin(hv + s, h);
+            return;
+        }
+        if (k == EMPTY_KEY) {
+            unsigned long long old = atomicCAS(hk + s, EMPTY_KEY, key);
+            if (old == EMPTY_KEY || old == key) {
+                atomicMin(hv + s, h);
+                return;
+            }
+        }
+        s = (s + 1) & (nslots - 1);
+    }
+    edge_insert(key, h, keys, vals, slots, ecount, gmask, status);  // CTA table crowded
+}
+
+template <typename T, int CONN>
+__global__ void __launch_bounds__(TT<CONN>::NT) k_label(const T *__restrict__ g, Geo geo, TileGeo tg, int32_t *par,
+                                                        int32_t *mi, int do_rag, unsigned long long *keys,
+                                                        uint32_t *vals, int32_t *slots, int32_t *ecount,
+                                                        unsigned long long gmask, DevStatus *status)
+{
+    using C = TC<CONN>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *hk = (unsigned long long *)smem;
+    unsigned *hv = (unsigned *)(hk + C::HASH);
+    int *rt = (int *)(hv + C::HASH);
+    T *gb = (T *)(rt + C::BS);
+    const int tid = threadIdx.x, lane = tid & 31;
+    int x0, y0, z0;
+    tile_origin<CONN>(tg, blockIdx.x, x0, y0, z0);
+    if (do_rag)
+        for (int i = tid; i < C::HASH; i += C::NT) {
+            hk[i] = EMPTY_KEY;
+            hv[i] = 0xffffffffu;
+        }
+    // roots of the tile and of its forward halo
+    for (int i = tid; i < C::BS; i += C::NT) {
+        const int bx = i % C::BX, by = (i / C::BX) % C::BY, bz = i / (C::BX * C::BY);
+        const int x = x0 - C::BXL + bx, y = y0 + by, z = z0 + bz;
+        int r = -1;
+        T v = 0;
+        if (x >= 0 && x < geo.W && y < geo.H && z < geo.D) {
+            const int q = (z * geo.H + y) * geo.W + x;
+            r = chase_root(par, par[q], status);
+            if (do_rag) v = g[q];
+        }
+        rt[i] = r;
+        gb[i] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < C::PER; k++) {
+        const int i = tid + k * C::NT;
+        const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+        const bool in = x < geo.W && y < geo.H && z < geo.D;
+        const int b = (lz * C::BY + ly) * C::BX + lx + C::BXL;
+        const int r = in ? rt[b] : -1;
+        const int p = in ? (z * geo.H + y) * geo.W + x : 0;
+        if (in) par[p] = r;
+        // smallest pixel index of each basin: lanes are consecutive x, so the
+        // lowest lane of a group holds its smallest index
+        const unsigned grp = __match_any_sync(0xffffffffu, r);
+        if (in && lane == __ffs(grp) - 1) atomicMin(mi + r, p);
+        if (!do_rag || !in) continue;
+        const unsigned gp = gb[b];
+#pragma unroll
+        for (int n = Half<CONN>::first; n < Nb<CONN>::n; n++) {
+            const int bq = b + (Nb<CONN>::dz(n) * C::BY + Nb<CONN>::dy(n)) * C::BX + Nb<CONN>::dx(n);
+            const int rq = rt[bq];
+            if (rq < 0 || rq == r) continue;
+            const unsigned gq = gb[bq];
+            const unsigned long long key = r < rq ? ((unsigned long long)(unsigned)r << 32) | (unsigned)rq
+                                                  : ((unsigned long long)(unsigned)rq << 32) | (unsigned)r;
+            smem_edge_insert(key, gp > gq ? gp : gq, hk, hv, C::HASH, keys, vals, slots, ecount, gmask, status);
+        }
+    }
+    if (!do_rag) return;
+    __syncthreads();
+    for (int i = tid; i < C::HASH; i += C::NT)
+        if (hk[i] != EMPTY_KEY) edge_insert(hk[i], hv[i], keys, vals, slots, ecount, gmask, status);
+}
+
+// ---------------------------------------------------------------------------
+// canonical ids by rank of each basin's smallest pixel index
+// ---------------------------------------------------------------------------
+
+static __global__ void __launch_bounds__(NTHR) k_rank_mark(const int32_t *__restrict__ roots,
+                                                           const int32_t *counters, const int32_t *__restrict__ mi,
+                                                           int32_t *__restrict__ rootm, unsigned *bitmap)
+{
+    const int n = counters[CNT_ROOTS];
+    for (int j = blockIdx.x * NTHR + threadIdx.x; j < n; j += gridDim.x * NTHR) {
+        const int m = mi[roots[j]];
+        rootm[j] = m;
+        atomicOr(bitmap + (m >> 5), 1u << (m & 31));
+    }
+}
+
+// popcount of each group of 32 bitmap words (1024 pixel indices) -> gcnt
+static __global__ void __launch_bounds__(NTHR) k_rank_groups(const unsigned *__restrict__ bitmap, int nwords,
+                                                             int32_t *__restrict__ gcnt, int ngroups)
+{
+    const int gi = blockIdx.x * (NTHR / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (gi >= ngroups) return;
+    const int w = gi * 32 + lane;
+    int c = w < nwords ? __popc(bitmap[w]) : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if (lane == 0) gcnt[gi] = c;
+}
+
+// id[root] = number of basins whose smallest index is below this basin's
+static __global__ void __launch_bounds__(NTHR) k_rank_assign(const int32_t *__restrict__ roots,
+                                                             const int32_t *counters,
+                                                             const int32_t *__restrict__ rootm,
+                                                             const unsigned *__restrict__ bitmap,
+                                                             const int32_t *__restrict__ gpre, int32_t *idmap)
+{
+    const int n = counters[CNT_ROOTS];
+    for (int j = blockIdx.x * NTHR + threadIdx.x; j < n; j += gridDim.x * NTHR) {
+        const int m = rootm[j];
+        const int w = m >> 5, gi = w >> 5;
+        int rank = gpre[gi];
+        for (int u = gi * 32; u < w; u++) rank += __popc(bitmap[u]);
+        rank += __popc(bitmap[w] & ((1u << (m & 31)) - 1u));
+        idmap[roots[j]] = rank;
+    }
+}
+
+static __global__ void __launch_bounds__(NTHR) k_rank_clear(const int32_t *counters, const int32_t *__restrict__ rootm,
+                                                            unsigned *bitmap)
+{
+    const int n = counters[CNT_ROOTS];
+    for (int j = blockIdx.x * NTHR + threadIdx.x; j < n; j += gridDim.x * NTHR) bitmap[rootm[j] >> 5] = 0u;
+}
+
+// Step II distances as ws_plateau_distance reports them: 0 for state-0
+// pixels, the distance for reached plateau pixels, -1 otherwise.
+static __global__ void __launch_bounds__(NTHR) k_dist_out2(Geo geo, TileGeo tg, const int32_t *__restrict__ par,
+                                                           const int32_t *__restrict__ dist,
+                                                           const uint8_t *__restrict__ plat, int32_t *__restrict__ out)
+{
+    for (int p = blockIdx.x * NTHR + threadIdx.x; p < geo.N; p += gridDim.x * NTHR) {
+        const int z = p / geo.HW, r = p - z * geo.HW, y = r / geo.W, x = r - y * geo.W;
+        int v;
+        if (plat[tile_of(tg, x, y, z)]) {
+            v = dist[p];
+            if (v >= INF_D || v < 0) v = -1;
+        } else {
+            v = par[p] == p ? -1 : 0;   // a minimum, or a pixel with a lower neighbour
+        }
+        out[p] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_write: one pass writing the canonical level-0 id and every waterfall level
+// ---------------------------------------------------------------------------
+
+static __global__ void __launch_bounds__(NTHR) k_write_vec(int N, const int32_t *__restrict__ par,
+                                                           const int32_t *__restrict__ idmap,
+                                                           const int32_t *__restrict__ gmap, size_t kstride, int NL,
+                                                           int32_t *__restrict__ out)
+{
+    const int n4 = N >> 2;
+    for (int v = blockIdx.x * NTHR + threadIdx.x; v < n4; v += gridDim.x * NTHR) {
+        const int4 r = __ldcs(reinterpret_cast<const int4 *>(par) + v);
+        int4 c;
+        c.x = idmap[r.x];
+        c.y = idmap[r.y];
+        c.z = idmap[r.z];
+        c.w = idmap[r.w];
+        __stcs(reinterpret_cast<int4 *>(out) + v, c);
+        for (int k = 1; k < NL; k++) {
+            const int32_t *gm = gmap + (size_t)(k - 1) * kstride;
+            int4 o;
+            o.x = gm[c.x];
+            o.y = gm[c.y];
+            o.z = gm[c.z];
+            o.w = gm[c.w];
+            __stcs(reinterpret_cast<int4 *>(out + (size_t)k * N) + v, o);
+        }
+    }
+    // tail (N % 4 pixels)
+    const int p = (n4 << 2) + blockIdx.x * NTHR + threadIdx.x;
+    if (blockIdx.x == 0 && p < N) {
+        const int c = idmap[par[p]];
+        out[p] = c;
+        for (int k = 1; k < NL; k++) out[(size_t)k * N + p] = gmap[(size_t)(k - 1) * kstride + c];
+    }
+}
+
+static __global__ void __launch_bounds__(NTHR) k_write_scalar(int N, const int32_t *__restrict__ par,
+                                                              const int32_t *__restrict__ idmap,
+                                                              const int32_t *__restrict__ gmap, size_t kstride,
+                                                              int NL, int32_t *__restrict__ out)
+{
+    for (int p = blockIdx.x * NTHR + threadIdx.x; p < N; p += gridDim.x * NTHR) {
+        const int c = idmap[par[p]];
+        out[p] = c;
+        for (int k = 1; k < NL; k++) out[(size_t)k * N + p] = gmap[(size_t)(k - 1) * kstride + c];
+    }
+}
+
+}  // namespace ws
