@@ -4,6 +4,7 @@
 #pragma once
 
 #include <stddef.h>
+#include <string.h>
 
 #include "ws_tiles.cuh"
 
@@ -85,10 +86,23 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
     if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
     {
         PhaseScope ps(c, PH_STEP1, s);
-        const size_t smem = align16((size_t)C::HS * sizeof(T)) + (size_t)C::NPIX * 4;
-        if ((e = allow_smem(k_init<T, CONN>, smem)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
-        k_init<T, CONN><<<tg.ntiles, C::NT, smem, s>>>(g, geo, tg, w.par, w.aux, w.dist, w.plat, w.act, w.tlist,
-                                                       w.roots, w.counters);
+        using B = InitBox<T, CONN>;
+        CUtensorMap tm;
+        const bool tma = make_tmap_3d(&tm, g, sizeof(T), geo.W, geo.H, geo.D, B::RW, C::HY, C::HZ);
+        if (tma) {
+            if ((e = allow_smem(k_init<T, CONN, true>, B::SMEM_TMA)) != cudaSuccess)
+                return set_cuda_error(c, e, "smem attribute");
+            const int grid = coop_grid(c, k_init<T, CONN, true>, C::NT, B::SMEM_TMA, tg.ntiles);
+            k_init<T, CONN, true><<<grid, C::NT, B::SMEM_TMA, s>>>(tm, g, geo, tg, w.par, w.aux, w.dist, w.plat, w.act,
+                                                                   w.tlist, w.roots, w.counters, c->status);
+        } else {
+            memset(&tm, 0, sizeof tm);
+            if ((e = allow_smem(k_init<T, CONN, false>, B::SMEM_PLAIN)) != cudaSuccess)
+                return set_cuda_error(c, e, "smem attribute");
+            k_init<T, CONN, false><<<tg.ntiles, C::NT, B::SMEM_PLAIN, s>>>(tm, g, geo, tg, w.par, w.aux, w.dist, w.plat,
+                                                                          w.act, w.tlist, w.roots, w.counters,
+                                                                          c->status);
+        }
         c->launches += 1;
     }
     {
@@ -144,12 +158,26 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const T
     }
     {
         PhaseScope ps(c, PH_RAG, s);
-        const size_t smem = (size_t)C::HASH * 12 + (size_t)C::BS * 4 + align16((size_t)C::BS * sizeof(T));
-        if ((e = allow_smem(k_label<T, CONN>, smem)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
-        k_label<T, CONN><<<tg.ntiles, C::NT, smem, s>>>(g, geo, tg, w.par, w.aux, do_rag ? 1 : 0, w.keys, w.vals,
-                                                        w.slots, w.ecount,
-                                                        (unsigned long long)(w.edge_cap ? w.edge_cap - 1 : 0),
-                                                        c->status);
+        using B = LabelBox<T, CONN>;
+        CUtensorMap tmp, tmg;
+        const bool tma = make_tmap_3d(&tmp, w.par, 4, geo.W, geo.H, geo.D, B::RWP, C::BY, C::BZ) &&
+                         make_tmap_3d(&tmg, g, sizeof(T), geo.W, geo.H, geo.D, B::RWG, C::BY, C::BZ);
+        const unsigned long long gmask = w.edge_cap ? w.edge_cap - 1 : 0;
+        if (tma) {
+            if ((e = allow_smem(k_label<T, CONN, true>, B::SMEM)) != cudaSuccess)
+                return set_cuda_error(c, e, "smem attribute");
+            k_label<T, CONN, true><<<tg.ntiles, C::NT, B::SMEM, s>>>(tmp, tmg, g, geo, tg, w.par, w.aux, do_rag ? 1 : 0,
+                                                                     w.keys, w.vals, w.slots, w.ecount, gmask,
+                                                                     c->status);
+        } else {
+            memset(&tmp, 0, sizeof tmp);
+            memset(&tmg, 0, sizeof tmg);
+            if ((e = allow_smem(k_label<T, CONN, false>, B::SMEM)) != cudaSuccess)
+                return set_cuda_error(c, e, "smem attribute");
+            k_label<T, CONN, false><<<tg.ntiles, C::NT, B::SMEM, s>>>(tmp, tmg, g, geo, tg, w.par, w.aux,
+                                                                      do_rag ? 1 : 0, w.keys, w.vals, w.slots,
+                                                                      w.ecount, gmask, c->status);
+        }
         c->launches += 1;
     }
     {

@@ -28,6 +28,7 @@
 #pragma once
 
 #include "ws_kernels.cuh"
+#include "ws_tma.cuh"
 
 namespace ws {
 
@@ -41,6 +42,7 @@ template <> struct TT<8> {
 template <> struct TT<6> {
     static constexpr int TX = 32, TY = 16, TZ = 16, NT = 512;
 };
+
 
 template <int CONN> struct TC {
     static constexpr int TX = TT<CONN>::TX, TY = TT<CONN>::TY, TZ = TT<CONN>::TZ, NT = TT<CONN>::NT;
@@ -102,130 +104,194 @@ enum : int { ST0 = 0, ST1 = 1, STP = 2, STOUT = 3 };
 // k_init: step I + in-tile path reduction
 // ---------------------------------------------------------------------------
 
-template <typename T, int CONN>
-__global__ void __launch_bounds__(TT<CONN>::NT) k_init(const T *__restrict__ g, Geo geo, TileGeo tg,
-                                                       int32_t *__restrict__ par, int32_t *__restrict__ mi,
-                                                       int32_t *__restrict__ dist, uint8_t *__restrict__ plat,
-                                                       uint8_t *__restrict__ act, int32_t *__restrict__ tlist,
-                                                       int32_t *__restrict__ roots, int32_t *counters)
-{
+// Shared-memory box of k_init: the tile plus a one-pixel halo in y and z and
+// an x halo widened to 16 bytes on each side (the TMA alignment unit), so a
+// row of the box starts on a 16-byte boundary in global memory.
+template <typename T, int CONN> struct InitBox {
     using C = TC<CONN>;
-    extern __shared__ __align__(16) unsigned char smem[];
-    T *gs = (T *)smem;
-    int *nx = (int *)(smem + ((C::HS * sizeof(T) + 15) & ~15));
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int t = blockIdx.x;
+    static constexpr int A = 16 / (int)sizeof(T);   // x offset of the tile inside the box
+    static constexpr int RW = C::TX + 2 * A;         // row pitch (elements)
+    static constexpr int ELEMS = RW * C::HY * C::HZ;
+    static constexpr int BYTES = ELEMS * (int)sizeof(T);
+    static constexpr int STAGE = (BYTES + 127) & ~127;
+    static constexpr int SMEM_TMA = 2 * STAGE + C::NPIX * 4;   // two stages + in-tile arrows
+    static constexpr int SMEM_PLAIN = STAGE + C::NPIX * 4;
+};
+
+template <typename T, int CONN, bool TMA>
+__device__ __forceinline__ void init_issue(const CUtensorMap *tm, T *dst, uint64_t *bar, const TileGeo &tg, int t)
+{
+    using B = InitBox<T, CONN>;
     int x0, y0, z0;
     tile_origin<CONN>(tg, t, x0, y0, z0);
+    mbar_arrive_expect_tx(bar, B::BYTES);
+    tma_load_3d(dst, tm, x0 - B::A, y0 - 1, TC<CONN>::D3 ? z0 - 1 : 0, bar);
+}
 
-    for (int i = tid; i < C::HS; i += C::NT) {
-        const int hx = i % C::HX, hy = (i / C::HX) % C::HY, hz = i / (C::HX * C::HY);
-        const int x = x0 - 1 + hx, y = y0 - 1 + hy, z = C::D3 ? z0 - 1 + hz : 0;
-        T v = 0;
-        if (x >= 0 && x < geo.W && y >= 0 && y < geo.H && z >= 0 && z < geo.D) v = g[(z * geo.H + y) * geo.W + x];
-        gs[i] = v;
+template <typename T, int CONN, bool TMA>
+__global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ CUtensorMap tm, const T *__restrict__ g,
+                                                       Geo geo, TileGeo tg, int32_t *__restrict__ par,
+                                                       int32_t *__restrict__ mi, int32_t *__restrict__ dist,
+                                                       uint8_t *__restrict__ plat, uint8_t *__restrict__ act,
+                                                       int32_t *__restrict__ tlist, int32_t *__restrict__ roots,
+                                                       int32_t *counters, DevStatus *status)
+{
+    using C = TC<CONN>;
+    using B = InitBox<T, CONN>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[2];
+    int *nx = (int *)(smem + (TMA ? 2 : 1) * B::STAGE);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int G = gridDim.x;
+
+    if (TMA) {
+        if (tid == 0) {
+            mbar_init(&bars[0], 1);
+            mbar_init(&bars[1], 1);
+            mbar_fence_init();
+            const int t0 = blockIdx.x;
+            if (t0 < tg.ntiles) init_issue<T, CONN, TMA>(&tm, (T *)smem, &bars[0], tg, t0);
+            if (t0 + G < tg.ntiles) init_issue<T, CONN, TMA>(&tm, (T *)(smem + B::STAGE), &bars[1], tg, t0 + G);
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
-    int st[C::PER];
-    int plateau = 0;
-#pragma unroll
-    for (int k = 0; k < C::PER; k++) {
-        const int i = tid + k * C::NT;
-        const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
-        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-        if (x >= geo.W || y >= geo.H || z >= geo.D) {
-            st[k] = STOUT;
-            nx[i] = enc_final(0);
-            continue;
-        }
-        const int p = (z * geo.H + y) * geo.W + x;
-        const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * C::HX + lx + 1;
-        const unsigned gp = gs[h];
-        unsigned m = 0xffffffffu;
-        int qn = -1;
-#pragma unroll
-        for (int n = 0; n < Nb<CONN>::n; n++) {
-            const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
-            if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
-            const unsigned v = gs[h + (Nb<CONN>::dz(n) * C::HY + Nb<CONN>::dy(n)) * C::HX + Nb<CONN>::dx(n)];
-            if (v <= m) {  // ascending index order: ties go to the later (larger) neighbour
-                m = v;
-                qn = n;
-            }
-        }
-        if (qn < 0 || m > gp) {
-            st[k] = ST1;
-            nx[i] = enc_final(p);
-        } else if (m < gp) {
-            st[k] = ST0;
-            const int lxx = lx + Nb<CONN>::dx(qn), lyy = ly + Nb<CONN>::dy(qn), lzz = lz + Nb<CONN>::dz(qn);
-            if (lxx >= 0 && lxx < C::TX && lyy >= 0 && lyy < C::TY && lzz >= 0 && lzz < C::TZ)
-                nx[i] = (lzz * C::TY + lyy) * C::TX + lxx;
-            else
-                nx[i] = enc_final(p + (Nb<CONN>::dz(qn) * geo.H + Nb<CONN>::dy(qn)) * geo.W + Nb<CONN>::dx(qn));
+    int j = 0;
+    for (int t = blockIdx.x; t < tg.ntiles; t += G, j++) {
+        const int s = TMA ? (j & 1) : 0;
+        T *gs = (T *)(smem + s * B::STAGE);
+        int x0, y0, z0;
+        tile_origin<CONN>(tg, t, x0, y0, z0);
+        if (TMA) {
+            const bool ok = mbar_wait(&bars[s], (unsigned)((j >> 1) & 1), status);
+            if (__syncthreads_or(!ok)) return;
         } else {
-            st[k] = STP;  // plateau pixel: resolved by step II / step IV
-            nx[i] = enc_final(p);
-            plateau = 1;
+            // loads are issued in batches of LB before any of them is used
+            constexpr int LPT = (B::ELEMS + C::NT - 1) / C::NT;
+            constexpr int LB = 12;
+#pragma unroll
+            for (int k0 = 0; k0 < LPT; k0 += LB) {
+                unsigned v[LB];
+#pragma unroll
+                for (int kk = 0; kk < LB; kk++) {
+                    const int i = tid + (k0 + kk) * C::NT;
+                    const int hx = i % B::RW, hy = (i / B::RW) % C::HY, hz = i / (B::RW * C::HY);
+                    const int x = x0 - B::A + hx, y = y0 - 1 + hy, z = C::D3 ? z0 - 1 + hz : 0;
+                    v[kk] = 0;
+                    if (k0 + kk < LPT && i < B::ELEMS && x >= 0 && x < geo.W && y >= 0 && y < geo.H && z >= 0 &&
+                        z < geo.D)
+                        v[kk] = __ldg(g + (z * geo.H + y) * geo.W + x);
+                }
+#pragma unroll
+                for (int kk = 0; kk < LB; kk++) {
+                    const int i = tid + (k0 + kk) * C::NT;
+                    if (k0 + kk < LPT && i < B::ELEMS) gs[i] = (T)v[kk];
+                }
+            }
+            __syncthreads();
         }
-    }
-    __syncthreads();
 
-    // step III inside the tile: follow arrows through shared memory
-    volatile int *vnx = nx;
-#pragma unroll
-    for (int k = 0; k < C::PER; k++) {
-        const int i = tid + k * C::NT;
-        int c = vnx[i];
-        if (c < 0) continue;
-        for (int guard = 0; c >= 0 && guard < C::NPIX; guard++) c = vnx[c];
-        vnx[i] = c;
-    }
-
-    int nroot = 0;
-#pragma unroll
-    for (int k = 0; k < C::PER; k++) {
-        const int i = tid + k * C::NT;
-        if (st[k] == STOUT) continue;
-        const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
-        const int p = ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
-        par[p] = dec_final(vnx[i]);
-        if (st[k] != ST0) mi[p] = 0x7fffffff;
-        nroot += st[k] == ST1;
-    }
-    // list the strict minima (roots known now)
-#pragma unroll
-    for (int k = 0; k < C::PER; k++) {
-        const bool isr = st[k] == ST1;
-        const unsigned b = __ballot_sync(0xffffffffu, isr);
-        if (!b) continue;
-        int base = 0;
-        if (lane == 0) base = atomicAdd(counters + CNT_ROOTS, __popc(b));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (isr) {
-            const int i = tid + k * C::NT;
-            const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
-            roots[base + __popc(b & ((1u << lane) - 1u))] = ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
-        }
-    }
-    (void)nroot;
-    if (__syncthreads_or(plateau)) {
+        int st[C::PER];
+        int plateau = 0;
 #pragma unroll
         for (int k = 0; k < C::PER; k++) {
-            if (st[k] == STOUT) continue;
             const int i = tid + k * C::NT;
             const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+            const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+            if (x >= geo.W || y >= geo.H || z >= geo.D) {
+                st[k] = STOUT;
+                nx[i] = enc_final(0);
+                continue;
+            }
+            const int p = (z * geo.H + y) * geo.W + x;
+            const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * B::RW + lx + B::A;
+            const unsigned gp = gs[h];
+            unsigned m = 0xffffffffu;
+            int qn = -1;
+#pragma unroll
+            for (int n = 0; n < Nb<CONN>::n; n++) {
+                const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
+                if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
+                const unsigned v = gs[h + (Nb<CONN>::dz(n) * C::HY + Nb<CONN>::dy(n)) * B::RW + Nb<CONN>::dx(n)];
+                if (v <= m) {  // ascending index order: ties go to the later (larger) neighbour
+                    m = v;
+                    qn = n;
+                }
+            }
+            if (qn < 0 || m > gp) {
+                st[k] = ST1;
+                nx[i] = enc_final(p);
+            } else if (m < gp) {
+                st[k] = ST0;
+                const int lxx = lx + Nb<CONN>::dx(qn), lyy = ly + Nb<CONN>::dy(qn), lzz = lz + Nb<CONN>::dz(qn);
+                if (lxx >= 0 && lxx < C::TX && lyy >= 0 && lyy < C::TY && lzz >= 0 && lzz < C::TZ)
+                    nx[i] = (lzz * C::TY + lyy) * C::TX + lxx;
+                else
+                    nx[i] = enc_final(p + (Nb<CONN>::dz(qn) * geo.H + Nb<CONN>::dy(qn)) * geo.W + Nb<CONN>::dx(qn));
+            } else {
+                st[k] = STP;  // plateau pixel: resolved by step II / step IV
+                nx[i] = enc_final(p);
+                plateau = 1;
+            }
+        }
+        __syncthreads();  // the gradient box of stage s is no longer read
+        if (TMA && tid == 0 && t + 2 * G < tg.ntiles)
+            init_issue<T, CONN, TMA>(&tm, gs, &bars[s], tg, t + 2 * G);
+
+        // step III inside the tile: follow arrows through shared memory
+        volatile int *vnx = nx;
+#pragma unroll
+        for (int k = 0; k < C::PER; k++) {
+            const int i = tid + k * C::NT;
+            int c = vnx[i];
+            if (c < 0) continue;
+            for (int guard = 0; c >= 0 && guard < C::NPIX; guard++) c = vnx[c];
+            vnx[i] = c;
+        }
+
+#pragma unroll
+        for (int k = 0; k < C::PER; k++) {
+            const int i = tid + k * C::NT;
+            if (st[k] == STOUT) continue;
+            const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
             const int p = ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
-            dist[p] = st[k] == ST0 ? 0 : (st[k] == ST1 ? -2 : INF_D);
+            par[p] = dec_final(vnx[i]);
+            if (st[k] != ST0) mi[p] = 0x7fffffff;
         }
-        if (tid == 0) {
-            plat[t] = 1;
-            act[t] = 1;
-            tlist[atomicAdd(counters + CNT_TILES, 1)] = t;
+        // list the strict minima (roots known now)
+#pragma unroll
+        for (int k = 0; k < C::PER; k++) {
+            const bool isr = st[k] == ST1;
+            const unsigned b = __ballot_sync(0xffffffffu, isr);
+            if (!b) continue;
+            int base = 0;
+            if (lane == 0) base = atomicAdd(counters + CNT_ROOTS, __popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (isr) {
+                const int i = tid + k * C::NT;
+                const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+                roots[base + __popc(b & ((1u << lane) - 1u))] = ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
+            }
         }
-    } else if (tid == 0) {
-        plat[t] = 0;
+        if (__syncthreads_or(plateau)) {
+#pragma unroll
+            for (int k = 0; k < C::PER; k++) {
+                if (st[k] == STOUT) continue;
+                const int i = tid + k * C::NT;
+                const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+                const int p = ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
+                dist[p] = st[k] == ST0 ? 0 : (st[k] == ST1 ? -2 : INF_D);
+            }
+            if (tid == 0) {
+                plat[t] = 1;
+                act[t] = 1;
+                tlist[atomicAdd(counters + CNT_TILES, 1)] = t;
+            }
+        } else if (tid == 0) {
+            plat[t] = 0;
+        }
+        // (the __syncthreads_or above also orders this tile's nx reads before
+        // the next tile's nx writes)
     }
 }
 
@@ -241,7 +307,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const T *__restrict__
                                                            int round_cap, unsigned long long timeout_ns)
 {
     using C = TC<CONN>;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     int *gs = (int *)smem;
     int *ds = gs + C::HS;
     __shared__ int flag_s;
@@ -483,17 +549,6 @@ __global__ void __launch_bounds__(NTHR) k_jump2(Geo geo, TileGeo tg, int32_t *pa
 // k_label: final roots, smallest index per basin, pass values (Alg. 5 step V)
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ int chase_root(int32_t *par, int r, DevStatus *status)
-{
-    for (int guard = 0; guard < (1 << 22); guard++) {
-        const int u = par[r];
-        if (u == r) return r;
-        r = u;
-    }
-    record_error(status, DEV_NONCONVERGED, 9);
-    return r;
-}
-
 __device__ __forceinline__ void smem_edge_insert(unsigned long long key, unsigned h, unsigned long long *hk,
                                                  unsigned *hv, int nslots, unsigned long long *keys,
                                                  uint32_t *vals, int32_t *slots, int32_t *ecount,
@@ -518,39 +573,104 @@ __device__ __forceinline__ void smem_edge_insert(unsigned long long key, unsigne
     edge_insert(key, h, keys, vals, slots, ecount, gmask, status);  // CTA table crowded
 }
 
-template <typename T, int CONN>
-__global__ void __launch_bounds__(TT<CONN>::NT) k_label(const T *__restrict__ g, Geo geo, TileGeo tg, int32_t *par,
+// Shared-memory layout of k_label: the CTA's edge hash, then the path-end /
+// root box and the gradient box of the tile's forward neighbourhood, each
+// row widened to start on a 16-byte boundary.
+template <typename T, int CONN> struct LabelBox {
+    using C = TC<CONN>;
+    static constexpr int AP = 4;                        // int32 per 16 bytes
+    static constexpr int RWP = C::TX + 2 * AP;          // par box: x from x0 - 4
+    static constexpr int AG = 16 / (int)sizeof(T);
+    static constexpr int RWG = C::TX + 2 * AG;          // grad box: x from x0 - AG
+    static constexpr int PBYTES = RWP * C::BY * C::BZ * 4;
+    static constexpr int GBYTES = RWG * C::BY * C::BZ * (int)sizeof(T);
+    static constexpr int OFF_P = C::HASH * 12;          // multiple of 128
+    static constexpr int OFF_G = OFF_P + ((PBYTES + 127) & ~127);
+    static constexpr int SMEM = OFF_G + ((GBYTES + 127) & ~127);
+};
+
+template <typename T, int CONN, bool TMA>
+__global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ CUtensorMap tmp,
+                                                        const __grid_constant__ CUtensorMap tmg,
+                                                        const T *__restrict__ g, Geo geo, TileGeo tg, int32_t *par,
                                                         int32_t *mi, int do_rag, unsigned long long *keys,
                                                         uint32_t *vals, int32_t *slots, int32_t *ecount,
                                                         unsigned long long gmask, DevStatus *status)
 {
     using C = TC<CONN>;
-    extern __shared__ __align__(16) unsigned char smem[];
+    using B = LabelBox<T, CONN>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
     unsigned long long *hk = (unsigned long long *)smem;
     unsigned *hv = (unsigned *)(hk + C::HASH);
-    int *rt = (int *)(hv + C::HASH);
-    T *gb = (T *)(rt + C::BS);
+    int *pb = (int *)(smem + B::OFF_P);
+    T *gb = (T *)(smem + B::OFF_G);
     const int tid = threadIdx.x, lane = tid & 31;
     int x0, y0, z0;
     tile_origin<CONN>(tg, blockIdx.x, x0, y0, z0);
+    if (TMA) {
+        if (tid == 0) {
+            mbar_init(&bar, 1);
+            mbar_fence_init();
+            mbar_arrive_expect_tx(&bar, B::PBYTES + (do_rag ? B::GBYTES : 0));
+            tma_load_3d(pb, &tmp, x0 - B::AP, y0, z0, &bar);
+            if (do_rag) tma_load_3d(gb, &tmg, x0 - B::AG, y0, z0, &bar);
+        }
+    }
     if (do_rag)
         for (int i = tid; i < C::HASH; i += C::NT) {
             hk[i] = EMPTY_KEY;
             hv[i] = 0xffffffffu;
         }
-    // roots of the tile and of its forward halo
-    for (int i = tid; i < C::BS; i += C::NT) {
-        const int bx = i % C::BX, by = (i / C::BX) % C::BY, bz = i / (C::BX * C::BY);
-        const int x = x0 - C::BXL + bx, y = y0 + by, z = z0 + bz;
-        int r = -1;
-        T v = 0;
-        if (x >= 0 && x < geo.W && y < geo.H && z < geo.D) {
-            const int q = (z * geo.H + y) * geo.W + x;
-            r = chase_root(par, par[q], status);
-            if (do_rag) v = g[q];
+    // roots of the tile and of its forward halo: all path ends of this thread
+    // are read first, then chased to their roots in lock step, so the thread
+    // keeps LPB independent gathers in flight per hop
+    {
+        constexpr int LPB = (C::BS + C::NT - 1) / C::NT;
+        int r[LPB];
+        if (TMA) {
+            const bool ok = mbar_wait(&bar, 0, status);
+            if (__syncthreads_or(!ok)) return;
         }
-        rt[i] = r;
-        gb[i] = v;
+#pragma unroll
+        for (int k = 0; k < LPB; k++) {
+            const int i = tid + k * C::NT;
+            const int bx = i % C::BX, by = (i / C::BX) % C::BY, bz = i / (C::BX * C::BY);
+            const int x = x0 - C::BXL + bx, y = y0 + by, z = z0 + bz;
+            r[k] = -1;
+            if (i < C::BS && x >= 0 && x < geo.W && y < geo.H && z < geo.D) {
+                if (TMA) {
+                    r[k] = pb[(bz * C::BY + by) * B::RWP + bx + B::AP - C::BXL];
+                } else {
+                    const int q = (z * geo.H + y) * geo.W + x;
+                    r[k] = par[q];
+                    if (do_rag) gb[(bz * C::BY + by) * B::RWG + bx + B::AG - C::BXL] = g[q];
+                }
+            }
+        }
+        unsigned live = 0;
+#pragma unroll
+        for (int k = 0; k < LPB; k++) live |= (r[k] >= 0 ? 1u : 0u) << k;
+        for (int hop = 0; live && hop < (1 << 22); hop++) {
+            int u[LPB];
+#pragma unroll
+            for (int k = 0; k < LPB; k++) u[k] = (live >> k) & 1u ? par[r[k]] : r[k];
+#pragma unroll
+            for (int k = 0; k < LPB; k++) {
+                if (u[k] == r[k]) live &= ~(1u << k);
+                r[k] = u[k];
+            }
+        }
+        if (live) record_error(status, DEV_NONCONVERGED, 9);
+        __syncthreads();   // every thread has read its path ends from the box
+#pragma unroll
+        for (int k = 0; k < LPB; k++) {
+            const int i = tid + k * C::NT;
+            if (i < C::BS) {
+                const int bx = i % C::BX, by = (i / C::BX) % C::BY, bz = i / (C::BX * C::BY);
+                pb[(bz * C::BY + by) * B::RWP + bx + B::AP - C::BXL] = r[k];
+            }
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -559,8 +679,9 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const T *__restrict__ g,
         const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
         const bool in = x < geo.W && y < geo.H && z < geo.D;
-        const int b = (lz * C::BY + ly) * C::BX + lx + C::BXL;
-        const int r = in ? rt[b] : -1;
+        const int bp = (lz * C::BY + ly) * B::RWP + lx + B::AP;
+        const int bg = (lz * C::BY + ly) * B::RWG + lx + B::AG;
+        const int r = in ? pb[bp] : -1;
         const int p = in ? (z * geo.H + y) * geo.W + x : 0;
         if (in) par[p] = r;
         // smallest pixel index of each basin: lanes are consecutive x, so the
@@ -568,13 +689,14 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const T *__restrict__ g,
         const unsigned grp = __match_any_sync(0xffffffffu, r);
         if (in && lane == __ffs(grp) - 1) atomicMin(mi + r, p);
         if (!do_rag || !in) continue;
-        const unsigned gp = gb[b];
+        const unsigned gp = gb[bg];
 #pragma unroll
         for (int n = Half<CONN>::first; n < Nb<CONN>::n; n++) {
-            const int bq = b + (Nb<CONN>::dz(n) * C::BY + Nb<CONN>::dy(n)) * C::BX + Nb<CONN>::dx(n);
-            const int rq = rt[bq];
-            if (rq < 0 || rq == r) continue;
-            const unsigned gq = gb[bq];
+            const int dn = Nb<CONN>::dz(n) * C::BY + Nb<CONN>::dy(n);
+            const int rq = pb[bp + dn * B::RWP + Nb<CONN>::dx(n)];
+            const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
+            if (xx < 0 || xx >= geo.W || yy >= geo.H || zz >= geo.D || rq == r) continue;
+            const unsigned gq = gb[bg + dn * B::RWG + Nb<CONN>::dx(n)];
             const unsigned long long key = r < rq ? ((unsigned long long)(unsigned)r << 32) | (unsigned)rq
                                                   : ((unsigned long long)(unsigned)rq << 32) | (unsigned)r;
             smem_edge_insert(key, gp > gq ? gp : gq, hk, hv, C::HASH, keys, vals, slots, ecount, gmask, status);
@@ -668,31 +790,41 @@ static __global__ void __launch_bounds__(NTHR) k_write_vec(int N, const int32_t 
                                                            const int32_t *__restrict__ gmap, size_t kstride, int NL,
                                                            int32_t *__restrict__ out)
 {
+    constexpr int U = 4;   // int4 vectors per thread per iteration (loads issued together)
     const int n4 = N >> 2;
-    for (int v = blockIdx.x * NTHR + threadIdx.x; v < n4; v += gridDim.x * NTHR) {
-        const int4 r = __ldcs(reinterpret_cast<const int4 *>(par) + v);
-        int4 c;
-        c.x = idmap[r.x];
-        c.y = idmap[r.y];
-        c.z = idmap[r.z];
-        c.w = idmap[r.w];
-        __stcs(reinterpret_cast<int4 *>(out) + v, c);
+    const int stride = gridDim.x * NTHR;
+    for (int v0 = blockIdx.x * NTHR + threadIdx.x; v0 < n4; v0 += stride * U) {
+        int4 c[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int v = v0 + u * stride;
+            c[u] = v < n4 ? __ldcs(reinterpret_cast<const int4 *>(par) + v) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            c[u].x = idmap[c[u].x];
+            c[u].y = idmap[c[u].y];
+            c[u].z = idmap[c[u].z];
+            c[u].w = idmap[c[u].w];
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int v = v0 + u * stride;
+            if (v < n4) __stcs(reinterpret_cast<int4 *>(out) + v, c[u]);
+        }
         for (int k = 1; k < NL; k++) {
             const int32_t *gm = gmap + (size_t)(k - 1) * kstride;
-            int4 o;
-            o.x = gm[c.x];
-            o.y = gm[c.y];
-            o.z = gm[c.z];
-            o.w = gm[c.w];
-            __stcs(reinterpret_cast<int4 *>(out + (size_t)k * N) + v, o);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int v = v0 + u * stride;
+                int4 o;
+                o.x = gm[c[u].x];
+                o.y = gm[c[u].y];
+                o.z = gm[c[u].z];
+                o.w = gm[c[u].w];
+                if (v < n4) __stcs(reinterpret_cast<int4 *>(out + (size_t)k * N) + v, o);
+            }
         }
-    }
-    // tail (N % 4 pixels)
-    const int p = (n4 << 2) + blockIdx.x * NTHR + threadIdx.x;
-    if (blockIdx.x == 0 && p < N) {
-        const int c = idmap[par[p]];
-        out[p] = c;
-        for (int k = 1; k < NL; k++) out[(size_t)k * N + p] = gmap[(size_t)(k - 1) * kstride + c];
     }
 }
 

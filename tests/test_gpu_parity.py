@@ -163,8 +163,11 @@ def test_watershed_blobs_256(ctx, conn, shift):
     assert np.array_equal(host(l_d), L)
 
 
-def test_watershed_distance_volume(ctx):
-    v = synth.distance_volume(40, 50, 60, 30, seed=3)
+@pytest.mark.parametrize("shape", [(40, 50, 60), (24, 40, 64), (17, 33, 96)])
+def test_watershed_distance_volume(ctx, shape):
+    """W = 64 and 96 rows are 16-byte multiples (TMA staging); W = 60 is not
+    (plain-load staging)."""
+    v = synth.distance_volume(*shape, 30, seed=3)
     L, K = oracle.watershed(v, 6)
     l_d, k_d = ctx.watershed(dev(v), 6)
     ctx.check()
@@ -224,8 +227,9 @@ def test_waterfall_random(ctx, seed):
         assert np.array_equal(host(lv_d), lv)
 
 
-def test_segment_3d(ctx):
-    v = synth.distance_volume(30, 40, 50, 25, seed=8)
+@pytest.mark.parametrize("shape", [(30, 40, 50), (20, 35, 72)])
+def test_segment_3d(ctx, shape):
+    v = synth.distance_volume(*shape, 25, seed=8)
     levels, counts = oracle.segment(v, 6, 6)
     lv_d, c_d = ctx.segment(dev(v), 6, 6)
     ctx.check()
