@@ -401,6 +401,7 @@ static __global__ void __launch_bounds__(NTHR) k_levels(const unsigned long long
                 a0 = idmap[a0];
                 b0 = idmap[b0];
             }
+            if ((unsigned)a0 >= (unsigned)K0 || (unsigned)b0 >= (unsigned)K0) continue;  // only after a device error
             unsigned h = vals[s];
             int A = gm ? __ldcg(gm + a0) : a0, B = gm ? __ldcg(gm + b0) : b0;
             if (A != B) {
@@ -418,6 +419,7 @@ static __global__ void __launch_bounds__(NTHR) k_levels(const unsigned long long
                 a0 = idmap[a0];
                 b0 = idmap[b0];
             }
+            if ((unsigned)a0 >= (unsigned)K0 || (unsigned)b0 >= (unsigned)K0) continue;  // only after a device error
             unsigned h = vals[s];
             int A = gm ? __ldcg(gm + a0) : a0, B = gm ? __ldcg(gm + b0) : b0;
             if (A != B && (h == __ldcg(newmin + A) || h == __ldcg(newmin + B))) uf_union(uf, A, B, status);

@@ -185,7 +185,7 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const T
         const int ng = (int)((geo.N + 1023) / 1024), nw = (int)((geo.N + 31) / 32);
         const int nch = (ng + SCAN_CHUNK - 1) / SCAN_CHUNK;
         const int rg = c->num_sms * 4;
-        k_rank_mark<<<rg, NTHR, 0, s>>>(w.roots, w.counters, w.aux, w.rootm, w.bitmap);
+        k_rank_mark<<<rg, NTHR, 0, s>>>(geo.N, w.roots, w.counters, w.aux, w.rootm, w.bitmap, c->status);
         k_rank_groups<<<(ng + NTHR / 32 - 1) / (NTHR / 32), NTHR, 0, s>>>(w.bitmap, nw, w.gcnt, ng);
         k_scan_chunks<<<nch, NTHR, 0, s>>>(w.gcnt, ng, w.csum);
         k_scan<<<1, 1024, 0, s>>>(w.csum, nch, nullptr);
@@ -206,9 +206,10 @@ static inline ws_status run_write(ws_context *c, const Geo &geo, int NL, int32_t
     const bool vec = (geo.N % 4 == 0) && (((uintptr_t)out & 15) == 0);
     const int grid = pixel_grid(c, vec ? geo.N / 4 : geo.N);
     if (vec)
-        k_write_vec<<<grid, NTHR, 0, s>>>(geo.N, w.par, w.aux, w.gmap, w.kmax, NL, out);
+        k_write_vec<<<grid, NTHR, 0, s>>>(geo.N, w.par, w.aux, w.gmap, w.kmax, NL, w.counters + CNT_ROOTS, out);
     else
-        k_write_scalar<<<grid, NTHR, 0, s>>>(geo.N, w.par, w.aux, w.gmap, w.kmax, NL, out);
+        k_write_scalar<<<grid, NTHR, 0, s>>>(geo.N, w.par, w.aux, w.gmap, w.kmax, NL, w.counters + CNT_ROOTS,
+                                              out);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "write launch");

@@ -712,13 +712,19 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
 // canonical ids by rank of each basin's smallest pixel index
 // ---------------------------------------------------------------------------
 
-static __global__ void __launch_bounds__(NTHR) k_rank_mark(const int32_t *__restrict__ roots,
+static __global__ void __launch_bounds__(NTHR) k_rank_mark(int N, const int32_t *__restrict__ roots,
                                                            const int32_t *counters, const int32_t *__restrict__ mi,
-                                                           int32_t *__restrict__ rootm, unsigned *bitmap)
+                                                           int32_t *__restrict__ rootm, unsigned *bitmap,
+                                                           DevStatus *status)
 {
     const int n = counters[CNT_ROOTS];
     for (int j = blockIdx.x * NTHR + threadIdx.x; j < n; j += gridDim.x * NTHR) {
         const int m = mi[roots[j]];
+        if (m < 0 || m >= N) {  // only after an earlier device error
+            rootm[j] = -1;
+            record_error(status, DEV_NONCONVERGED, 10);
+            continue;
+        }
         rootm[j] = m;
         atomicOr(bitmap + (m >> 5), 1u << (m & 31));
     }
@@ -747,6 +753,10 @@ static __global__ void __launch_bounds__(NTHR) k_rank_assign(const int32_t *__re
     const int n = counters[CNT_ROOTS];
     for (int j = blockIdx.x * NTHR + threadIdx.x; j < n; j += gridDim.x * NTHR) {
         const int m = rootm[j];
+        if (m < 0) {
+            idmap[roots[j]] = -1;
+            continue;
+        }
         const int w = m >> 5, gi = w >> 5;
         int rank = gpre[gi];
         for (int u = gi * 32; u < w; u++) rank += __popc(bitmap[u]);
@@ -759,7 +769,8 @@ static __global__ void __launch_bounds__(NTHR) k_rank_clear(const int32_t *count
                                                             unsigned *bitmap)
 {
     const int n = counters[CNT_ROOTS];
-    for (int j = blockIdx.x * NTHR + threadIdx.x; j < n; j += gridDim.x * NTHR) bitmap[rootm[j] >> 5] = 0u;
+    for (int j = blockIdx.x * NTHR + threadIdx.x; j < n; j += gridDim.x * NTHR)
+        if (rootm[j] >= 0) bitmap[rootm[j] >> 5] = 0u;
 }
 
 // Step II distances as ws_plateau_distance reports them: 0 for state-0
@@ -785,13 +796,25 @@ static __global__ void __launch_bounds__(NTHR) k_dist_out2(Geo geo, TileGeo tg, 
 // k_write: one pass writing the canonical level-0 id and every waterfall level
 // ---------------------------------------------------------------------------
 
+// Canonical id of a root; ids outside [0, K0) can only come from an earlier
+// device error and are written as -1 instead of being used as an index.
+__device__ __forceinline__ int safe_id(const int32_t *__restrict__ idmap, int r, int K0)
+{
+    const int c = idmap[r];
+    return (unsigned)c < (unsigned)K0 ? c : -1;
+}
+
+__device__ __forceinline__ int level_id(const int32_t *__restrict__ gm, int c) { return c >= 0 ? gm[c] : -1; }
+
 static __global__ void __launch_bounds__(NTHR) k_write_vec(int N, const int32_t *__restrict__ par,
                                                            const int32_t *__restrict__ idmap,
                                                            const int32_t *__restrict__ gmap, size_t kstride, int NL,
+                                                           const int32_t *__restrict__ k0_ptr,
                                                            int32_t *__restrict__ out)
 {
     constexpr int U = 4;   // int4 vectors per thread per iteration (loads issued together)
     const int n4 = N >> 2;
+    const int K0 = *k0_ptr;
     const int stride = gridDim.x * NTHR;
     for (int v0 = blockIdx.x * NTHR + threadIdx.x; v0 < n4; v0 += stride * U) {
         int4 c[U];
@@ -800,12 +823,15 @@ static __global__ void __launch_bounds__(NTHR) k_write_vec(int N, const int32_t 
             const int v = v0 + u * stride;
             c[u] = v < n4 ? __ldcs(reinterpret_cast<const int4 *>(par) + v) : make_int4(0, 0, 0, 0);
         }
+        // lanes past the end (v >= n4) gather nothing and store nothing
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            c[u].x = idmap[c[u].x];
-            c[u].y = idmap[c[u].y];
-            c[u].z = idmap[c[u].z];
-            c[u].w = idmap[c[u].w];
+            if (v0 + u * stride < n4) {
+                c[u].x = safe_id(idmap, c[u].x, K0);
+                c[u].y = safe_id(idmap, c[u].y, K0);
+                c[u].z = safe_id(idmap, c[u].z, K0);
+                c[u].w = safe_id(idmap, c[u].w, K0);
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
@@ -817,12 +843,13 @@ static __global__ void __launch_bounds__(NTHR) k_write_vec(int N, const int32_t 
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int v = v0 + u * stride;
+                if (v >= n4) continue;
                 int4 o;
-                o.x = gm[c[u].x];
-                o.y = gm[c[u].y];
-                o.z = gm[c[u].z];
-                o.w = gm[c[u].w];
-                if (v < n4) __stcs(reinterpret_cast<int4 *>(out + (size_t)k * N) + v, o);
+                o.x = level_id(gm, c[u].x);
+                o.y = level_id(gm, c[u].y);
+                o.z = level_id(gm, c[u].z);
+                o.w = level_id(gm, c[u].w);
+                __stcs(reinterpret_cast<int4 *>(out + (size_t)k * N) + v, o);
             }
         }
     }
@@ -831,12 +858,14 @@ static __global__ void __launch_bounds__(NTHR) k_write_vec(int N, const int32_t 
 static __global__ void __launch_bounds__(NTHR) k_write_scalar(int N, const int32_t *__restrict__ par,
                                                               const int32_t *__restrict__ idmap,
                                                               const int32_t *__restrict__ gmap, size_t kstride,
-                                                              int NL, int32_t *__restrict__ out)
+                                                              int NL, const int32_t *__restrict__ k0_ptr,
+                                                              int32_t *__restrict__ out)
 {
+    const int K0 = *k0_ptr;
     for (int p = blockIdx.x * NTHR + threadIdx.x; p < N; p += gridDim.x * NTHR) {
-        const int c = idmap[par[p]];
+        const int c = safe_id(idmap, par[p], K0);
         out[p] = c;
-        for (int k = 1; k < NL; k++) out[(size_t)k * N + p] = gmap[(size_t)(k - 1) * kstride + c];
+        for (int k = 1; k < NL; k++) out[(size_t)k * N + p] = level_id(gmap + (size_t)(k - 1) * kstride, c);
     }
 }
 
