@@ -629,6 +629,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
         constexpr int LPB = (C::BS + C::NT - 1) / C::NT;
         int r[LPB];
         if (TMA) {
+            __syncthreads();  // the barrier is initialised before anyone polls it
             const bool ok = mbar_wait(&bar, 0, status);
             if (__syncthreads_or(!ok)) return;
         }
