@@ -128,6 +128,63 @@ __device__ __forceinline__ void init_issue(const CUtensorMap *tm, T *dst, uint64
     tma_load_3d(dst, tm, x0 - B::A, y0 - 1, TC<CONN>::D3 ? z0 - 1 : 0, bar);
 }
 
+// Step I (Eq. 1) for this thread's pixels of one tile, from the gradient box
+// in shared memory: writes the in-tile arrow (local index), the path end
+// (encoded global index), and the state; returns 1 if a plateau pixel was
+// seen.  CHECK = false skips the neighbour bounds tests (interior tiles).
+template <typename T, int CONN, bool CHECK>
+__device__ __forceinline__ int init_step1(const T *gs, int *nx, int (&st)[TC<CONN>::PER], int tid, int x0, int y0,
+                                          int z0, const Geo &geo)
+{
+    using C = TC<CONN>;
+    using B = InitBox<T, CONN>;
+    int plateau = 0;
+#pragma unroll
+    for (int k = 0; k < C::PER; k++) {
+        const int i = tid + k * C::NT;
+        const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+        if (CHECK && (x >= geo.W || y >= geo.H || z >= geo.D)) {
+            st[k] = STOUT;
+            nx[i] = enc_final(0);
+            continue;
+        }
+        const int p = (z * geo.H + y) * geo.W + x;
+        const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * B::RW + lx + B::A;
+        const unsigned gp = gs[h];
+        unsigned m = 0xffffffffu;
+        int qn = -1;
+#pragma unroll
+        for (int n = 0; n < Nb<CONN>::n; n++) {
+            if (CHECK) {
+                const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
+                if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
+            }
+            const unsigned v = gs[h + (Nb<CONN>::dz(n) * C::HY + Nb<CONN>::dy(n)) * B::RW + Nb<CONN>::dx(n)];
+            if (v <= m) {  // ascending index order: ties go to the later (larger) neighbour
+                m = v;
+                qn = n;
+            }
+        }
+        if (qn < 0 || m > gp) {
+            st[k] = ST1;
+            nx[i] = enc_final(p);
+        } else if (m < gp) {
+            st[k] = ST0;
+            const int lxx = lx + Nb<CONN>::dx(qn), lyy = ly + Nb<CONN>::dy(qn), lzz = lz + Nb<CONN>::dz(qn);
+            if (lxx >= 0 && lxx < C::TX && lyy >= 0 && lyy < C::TY && lzz >= 0 && lzz < C::TZ)
+                nx[i] = (lzz * C::TY + lyy) * C::TX + lxx;
+            else
+                nx[i] = enc_final(p + (Nb<CONN>::dz(qn) * geo.H + Nb<CONN>::dy(qn)) * geo.W + Nb<CONN>::dx(qn));
+        } else {
+            st[k] = STP;  // plateau pixel: resolved by step II / step IV
+            nx[i] = enc_final(p);
+            plateau = 1;
+        }
+    }
+    return plateau;
+}
+
 template <typename T, int CONN, bool TMA>
 __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ CUtensorMap tm, const T *__restrict__ g,
                                                        Geo geo, TileGeo tg, int32_t *__restrict__ par,
@@ -193,60 +250,34 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
 
         int st[C::PER];
         int plateau = 0;
-#pragma unroll
-        for (int k = 0; k < C::PER; k++) {
-            const int i = tid + k * C::NT;
-            const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
-            const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-            if (x >= geo.W || y >= geo.H || z >= geo.D) {
-                st[k] = STOUT;
-                nx[i] = enc_final(0);
-                continue;
-            }
-            const int p = (z * geo.H + y) * geo.W + x;
-            const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * B::RW + lx + B::A;
-            const unsigned gp = gs[h];
-            unsigned m = 0xffffffffu;
-            int qn = -1;
-#pragma unroll
-            for (int n = 0; n < Nb<CONN>::n; n++) {
-                const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
-                if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
-                const unsigned v = gs[h + (Nb<CONN>::dz(n) * C::HY + Nb<CONN>::dy(n)) * B::RW + Nb<CONN>::dx(n)];
-                if (v <= m) {  // ascending index order: ties go to the later (larger) neighbour
-                    m = v;
-                    qn = n;
-                }
-            }
-            if (qn < 0 || m > gp) {
-                st[k] = ST1;
-                nx[i] = enc_final(p);
-            } else if (m < gp) {
-                st[k] = ST0;
-                const int lxx = lx + Nb<CONN>::dx(qn), lyy = ly + Nb<CONN>::dy(qn), lzz = lz + Nb<CONN>::dz(qn);
-                if (lxx >= 0 && lxx < C::TX && lyy >= 0 && lyy < C::TY && lzz >= 0 && lzz < C::TZ)
-                    nx[i] = (lzz * C::TY + lyy) * C::TX + lxx;
-                else
-                    nx[i] = enc_final(p + (Nb<CONN>::dz(qn) * geo.H + Nb<CONN>::dy(qn)) * geo.W + Nb<CONN>::dx(qn));
-            } else {
-                st[k] = STP;  // plateau pixel: resolved by step II / step IV
-                nx[i] = enc_final(p);
-                plateau = 1;
-            }
-        }
+        // a tile whose halo lies inside the image needs no neighbour bounds checks
+        const bool interior = x0 >= 1 && x0 + C::TX < geo.W && y0 >= 1 && y0 + C::TY < geo.H &&
+                              (!C::D3 || (z0 >= 1 && z0 + C::TZ < geo.D));
+        if (interior)
+            plateau = init_step1<T, CONN, false>(gs, nx, st, tid, x0, y0, z0, geo);
+        else
+            plateau = init_step1<T, CONN, true>(gs, nx, st, tid, x0, y0, z0, geo);
         __syncthreads();  // the gradient box of stage s is no longer read
         if (TMA && tid == 0 && t + 2 * G < tg.ntiles)
             init_issue<T, CONN, TMA>(&tm, gs, &bars[s], tg, t + 2 * G);
 
-        // step III inside the tile: follow arrows through shared memory
+        // step III inside the tile: pointer doubling through shared memory
+        // (in place: every value read is the pointer of a pixel further down
+        // the same path, or the path's end), until no pointer stays in the tile
         volatile int *vnx = nx;
+        for (int round = 0; round < 32; round++) {
+            int more = 0;
 #pragma unroll
-        for (int k = 0; k < C::PER; k++) {
-            const int i = tid + k * C::NT;
-            int c = vnx[i];
-            if (c < 0) continue;
-            for (int guard = 0; c >= 0 && guard < C::NPIX; guard++) c = vnx[c];
-            vnx[i] = c;
+            for (int k = 0; k < C::PER; k++) {
+                const int i = tid + k * C::NT;
+                const int c = vnx[i];
+                if (c >= 0) {
+                    const int c2 = vnx[c];
+                    vnx[i] = c2;
+                    more |= c2 >= 0;
+                }
+            }
+            if (!__syncthreads_or(more)) break;
         }
 
 #pragma unroll
@@ -255,7 +286,8 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
             if (st[k] == STOUT) continue;
             const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
             const int p = ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
-            par[p] = dec_final(vnx[i]);
+            const int e = vnx[i];
+            par[p] = e < 0 ? dec_final(e) : p;  // e >= 0 cannot survive 32 doubling rounds
             if (st[k] != ST0) mi[p] = 0x7fffffff;
         }
         // list the strict minima (roots known now)
@@ -689,18 +721,32 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
         // lowest lane of a group holds its smallest index
         const unsigned grp = __match_any_sync(0xffffffffu, r);
         if (in && lane == __ffs(grp) - 1) atomicMin(mi + r, p);
-        if (!do_rag || !in) continue;
-        const unsigned gp = gb[bg];
+        if (!do_rag) continue;
+        const unsigned gp = in ? gb[bg] : 0u;
 #pragma unroll
         for (int n = Half<CONN>::first; n < Nb<CONN>::n; n++) {
             const int dn = Nb<CONN>::dz(n) * C::BY + Nb<CONN>::dy(n);
-            const int rq = pb[bp + dn * B::RWP + Nb<CONN>::dx(n)];
             const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
-            if (xx < 0 || xx >= geo.W || yy >= geo.H || zz >= geo.D || rq == r) continue;
-            const unsigned gq = gb[bg + dn * B::RWG + Nb<CONN>::dx(n)];
-            const unsigned long long key = r < rq ? ((unsigned long long)(unsigned)r << 32) | (unsigned)rq
-                                                  : ((unsigned long long)(unsigned)rq << 32) | (unsigned)r;
-            smem_edge_insert(key, gp > gq ? gp : gq, hk, hv, C::HASH, keys, vals, slots, ecount, gmask, status);
+            bool has = false;
+            unsigned long long key = 0;
+            unsigned h = 0;
+            if (in && xx >= 0 && xx < geo.W && yy < geo.H && zz < geo.D) {
+                const int rq = pb[bp + dn * B::RWP + Nb<CONN>::dx(n)];
+                if (rq != r) {
+                    has = true;
+                    const unsigned gq = gb[bg + dn * B::RWG + Nb<CONN>::dx(n)];
+                    key = r < rq ? ((unsigned long long)(unsigned)r << 32) | (unsigned)rq
+                                 : ((unsigned long long)(unsigned)rq << 32) | (unsigned)r;
+                    h = gp > gq ? gp : gq;
+                }
+            }
+            // lanes along one boundary share a key: one insert per key per warp
+            const unsigned m = __ballot_sync(0xffffffffu, has);
+            if (!has) continue;
+            const unsigned grp2 = __match_any_sync(m, key);
+            const unsigned hmin = __reduce_min_sync(grp2, h);
+            if (lane == __ffs(grp2) - 1)
+                smem_edge_insert(key, hmin, hk, hv, C::HASH, keys, vals, slots, ecount, gmask, status);
         }
     }
     if (!do_rag) return;
