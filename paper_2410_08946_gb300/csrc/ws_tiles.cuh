@@ -132,13 +132,25 @@ __device__ __forceinline__ void init_issue(const CUtensorMap *tm, T *dst, uint64
 // in shared memory: writes the in-tile arrow (local index), the path end
 // (encoded global index), and the state; returns 1 if a plateau pixel was
 // seen.  CHECK = false skips the neighbour bounds tests (interior tiles).
+// The thread's pixels are slots k = 0..PER-1 of one column of the tile (the
+// z column in 3D, every NT/TX-th row in 2D); in 3D the column and its four
+// side columns are read once into registers and the z neighbours reused.
 template <typename T, int CONN, bool CHECK>
 __device__ __forceinline__ int init_step1(const T *gs, int *nx, int (&st)[TC<CONN>::PER], int tid, int x0, int y0,
                                           int z0, const Geo &geo)
 {
     using C = TC<CONN>;
     using B = InitBox<T, CONN>;
+    constexpr bool COL = C::D3 && C::NT == C::TX * C::TY;  // slot k is z = k of column tid
     int plateau = 0;
+    unsigned cz[C::PER + 2];
+    if (COL) {
+        const int lx = tid % C::TX, ly = tid / C::TX;
+        const int h0 = (ly + 1) * B::RW + lx + B::A;   // box index of (lx, ly, z = -1)
+        constexpr int SZ = C::HY * B::RW;
+#pragma unroll
+        for (int k = 0; k < C::PER + 2; k++) cz[k] = gs[h0 + k * SZ];
+    }
 #pragma unroll
     for (int k = 0; k < C::PER; k++) {
         const int i = tid + k * C::NT;
@@ -151,7 +163,7 @@ __device__ __forceinline__ int init_step1(const T *gs, int *nx, int (&st)[TC<CON
         }
         const int p = (z * geo.H + y) * geo.W + x;
         const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * B::RW + lx + B::A;
-        const unsigned gp = gs[h];
+        const unsigned gp = COL ? cz[k + 1] : (unsigned)gs[h];
         unsigned m = 0xffffffffu;
         int qn = -1;
 #pragma unroll
@@ -160,7 +172,12 @@ __device__ __forceinline__ int init_step1(const T *gs, int *nx, int (&st)[TC<CON
                 const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
                 if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
             }
-            const unsigned v = gs[h + (Nb<CONN>::dz(n) * C::HY + Nb<CONN>::dy(n)) * B::RW + Nb<CONN>::dx(n)];
+            unsigned v;
+            if (COL && (n == 0 || n == Nb<CONN>::n - 1)) {
+                v = n == 0 ? cz[k] : cz[k + 2];   // z - 1, z + 1 from the register column
+            } else {
+                v = gs[h + (Nb<CONN>::dz(n) * C::HY + Nb<CONN>::dy(n)) * B::RW + Nb<CONN>::dx(n)];
+            }
             if (v <= m) {  // ascending index order: ties go to the later (larger) neighbour
                 m = v;
                 qn = n;
@@ -581,7 +598,7 @@ __global__ void __launch_bounds__(NTHR) k_jump2(Geo geo, TileGeo tg, int32_t *pa
 // k_label: final roots, smallest index per basin, pass values (Alg. 5 step V)
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void smem_edge_insert(unsigned long long key, unsigned h, unsigned long long *hk,
+static __device__ __noinline__ void smem_edge_insert(unsigned long long key, unsigned h, unsigned long long *hk,
                                                  unsigned *hv, int nslots, unsigned long long *keys,
                                                  uint32_t *vals, int32_t *slots, int32_t *ecount,
                                                  unsigned long long gmask, DevStatus *status)
@@ -706,7 +723,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
         }
     }
     __syncthreads();
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < C::PER; k++) {
         const int i = tid + k * C::NT;
         const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
@@ -717,10 +734,11 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
         const int r = in ? pb[bp] : -1;
         const int p = in ? (z * geo.H + y) * geo.W + x : 0;
         if (in) par[p] = r;
-        // smallest pixel index of each basin: lanes are consecutive x, so the
-        // lowest lane of a group holds its smallest index
-        const unsigned grp = __match_any_sync(0xffffffffu, r);
-        if (in && lane == __ffs(grp) - 1) atomicMin(mi + r, p);
+        // smallest pixel index of each basin: lanes are consecutive x of one
+        // row, so the first lane of every run of equal roots holds the run's
+        // smallest index (a basin met in several runs takes several atomics)
+        const int rprev = __shfl_up_sync(0xffffffffu, r, 1);
+        if (in && (lane == 0 || rprev != r)) atomicMin(mi + r, p);
         if (!do_rag) continue;
         const unsigned gp = in ? gb[bg] : 0u;
 #pragma unroll
