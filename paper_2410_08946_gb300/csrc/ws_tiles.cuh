@@ -598,28 +598,31 @@ __global__ void __launch_bounds__(NTHR) k_jump2(Geo geo, TileGeo tg, int32_t *pa
 // k_label: final roots, smallest index per basin, pass values (Alg. 5 step V)
 // ---------------------------------------------------------------------------
 
-static __device__ __noinline__ void smem_edge_insert(unsigned long long key, unsigned h, unsigned long long *hk,
-                                                 unsigned *hv, int nslots, unsigned long long *keys,
-                                                 uint32_t *vals, int32_t *slots, int32_t *ecount,
-                                                 unsigned long long gmask, DevStatus *status)
+// Insert (key, h) into the CTA's edge hash (min of h per key).  The slot is
+// read before any atomic: lanes that find their key already present with a
+// pass value <= h issue no atomic at all.  A crowded CTA table falls back to
+// the global region table.
+static __device__ __noinline__ void smem_edge_insert(unsigned a, unsigned b, unsigned h, unsigned long long *hk,
+                                                     unsigned *hv, int nslots, unsigned long long *keys,
+                                                     uint32_t *vals, int32_t *slots, int32_t *ecount,
+                                                     unsigned long long gmask, DevStatus *status)
 {
-    unsigned s = (unsigned)(mix64(key) & (unsigned long long)(nslots - 1));
+    const unsigned long long key = ((unsigned long long)a << 32) | b;
+    unsigned s = (a * 0x9E3779B1u) ^ (b * 0x85EBCA77u);
+    s = (s ^ (s >> 15)) & (unsigned)(nslots - 1);
     for (int probe = 0; probe < 32; probe++) {
         unsigned long long k = hk[s];
+        if (k == EMPTY_KEY) {
+            k = atomicCAS(hk + s, EMPTY_KEY, key);
+            if (k == EMPTY_KEY) k = key;
+        }
         if (k == key) {
-            atomicMin(hv + s, h);
+            if (h < hv[s]) atomicMin(hv + s, h);
             return;
         }
-        if (k == EMPTY_KEY) {
-            unsigned long long old = atomicCAS(hk + s, EMPTY_KEY, key);
-            if (old == EMPTY_KEY || old == key) {
-                atomicMin(hv + s, h);
-                return;
-            }
-        }
-        s = (s + 1) & (nslots - 1);
+        s = (s + 1) & (unsigned)(nslots - 1);
     }
-    edge_insert(key, h, keys, vals, slots, ecount, gmask, status);  // CTA table crowded
+    edge_insert(key, h, keys, vals, slots, ecount, gmask, status);
 }
 
 // Shared-memory layout of k_label: the CTA's edge hash, then the path-end /
@@ -739,32 +742,18 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
         // smallest index (a basin met in several runs takes several atomics)
         const int rprev = __shfl_up_sync(0xffffffffu, r, 1);
         if (in && (lane == 0 || rprev != r)) atomicMin(mi + r, p);
-        if (!do_rag) continue;
-        const unsigned gp = in ? gb[bg] : 0u;
+        if (!do_rag || !in) continue;
+        const unsigned gp = gb[bg];
 #pragma unroll
         for (int n = Half<CONN>::first; n < Nb<CONN>::n; n++) {
             const int dn = Nb<CONN>::dz(n) * C::BY + Nb<CONN>::dy(n);
             const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
-            bool has = false;
-            unsigned long long key = 0;
-            unsigned h = 0;
-            if (in && xx >= 0 && xx < geo.W && yy < geo.H && zz < geo.D) {
-                const int rq = pb[bp + dn * B::RWP + Nb<CONN>::dx(n)];
-                if (rq != r) {
-                    has = true;
-                    const unsigned gq = gb[bg + dn * B::RWG + Nb<CONN>::dx(n)];
-                    key = r < rq ? ((unsigned long long)(unsigned)r << 32) | (unsigned)rq
-                                 : ((unsigned long long)(unsigned)rq << 32) | (unsigned)r;
-                    h = gp > gq ? gp : gq;
-                }
-            }
-            // lanes along one boundary share a key: one insert per key per warp
-            const unsigned m = __ballot_sync(0xffffffffu, has);
-            if (!has) continue;
-            const unsigned grp2 = __match_any_sync(m, key);
-            const unsigned hmin = __reduce_min_sync(grp2, h);
-            if (lane == __ffs(grp2) - 1)
-                smem_edge_insert(key, hmin, hk, hv, C::HASH, keys, vals, slots, ecount, gmask, status);
+            if (xx < 0 || xx >= geo.W || yy >= geo.H || zz >= geo.D) continue;
+            const int rq = pb[bp + dn * B::RWP + Nb<CONN>::dx(n)];
+            if (rq == r) continue;
+            const unsigned gq = gb[bg + dn * B::RWG + Nb<CONN>::dx(n)];
+            const unsigned lo = (unsigned)(r < rq ? r : rq), hi = (unsigned)(r < rq ? rq : r);
+            smem_edge_insert(lo, hi, gp > gq ? gp : gq, hk, hv, C::HASH, keys, vals, slots, ecount, gmask, status);
         }
     }
     if (!do_rag) return;
