@@ -47,17 +47,16 @@ FALLBACK_HBM_GBS = 6800.0
 # Algorithmic bytes per voxel of each phase (minimal input + output of the
 # function the phase computes; b = 2 bytes per uint16 sample).
 PHASE_BYTES = {
-    "step1": 2 + 4,            # read G, write the arrow
-    "jump": 4 + 4,             # read arrows, write roots
-    "compact": 4 + 4,          # read roots, write canonical labels
-    "rag": 4 + 2,              # read labels and G
-    "level_write": 4 + 4 * (NL - 1),   # read L0, write NL-1 planes
-    "resolve_union": 2 + 4,    # read G (plateau pixels), write arrows
-    "plateau": 2 + 4,
+    "step1": 2 + 4,              # k_init: read G, write the in-tile path end
+    "rag": 4 + 2 + 4,            # k_label: read path ends and G, write roots
+    "level_write": 4 + 4 * NL,   # k_write_vec: read roots, write NL label planes
+    "plateau": 2 + 4,            # k_plateau2 (plateau tiles only)
+    "resolve_union": 2 + 4,      # k_resolve2 (plateau tiles only)
+    "jump": 4 + 4,               # k_jump2 (plateau tiles only)
 }
-KERNEL_OF_PHASE = {"step1": "k_step1", "plateau": "k_plateau", "resolve_union": "k_resolve_union",
-                   "jump": "k_jump", "compact": "k_flags/k_scan/k_assign/k_label", "rag": "k_rag",
-                   "levels": "k_levels", "level_write": "k_level_write", "cleanup": "k_hash_clear"}
+KERNEL_OF_PHASE = {"step1": "k_init", "plateau": "k_plateau2", "resolve_union": "k_resolve2",
+                   "jump": "k_jump2", "compact": "k_rank_*", "rag": "k_label", "levels": "k_levels",
+                   "level_write": "k_write_vec", "cleanup": "k_hash_clear"}
 
 
 def workload_name(side):
