@@ -222,6 +222,39 @@ ws_status ws_plateau_distance(ws_context *ctx, const void *grad_d, ws_dtype dtyp
                               const ws_shape *shape, int connectivity, int32_t *dist_d,
                               ws_stream_t stream);
 
+/* ------------------------------------------------------------------------ */
+/* watershed without device-memory allocation                                */
+/* ------------------------------------------------------------------------ */
+
+/* Largest image, in pixels, that ws_watershed_static accepts. */
+#define WS_STATIC_MAX_PIXELS 524288
+
+/*
+ * The result of ws_watershed (the same labels and the same count) for callers
+ * that cannot allocate device memory: hosts that reserve all of the GPU's
+ * memory for their own allocator, and latency-critical loops that cannot
+ * afford the device-wide synchronisation of cudaMalloc and cudaFree.  The
+ * paper has no counterpart: this is a deployment variant of the watershed.
+ *
+ * It needs no ws_context and allocates nothing.  All of its scratch lives in
+ * one fixed device array inside the library (about 8.3 MB), which every GPU
+ * that loads the library holds until the process exits.
+ *   - Images of at most WS_STATIC_MAX_PIXELS pixels; a larger image returns
+ *     WS_ERR_INVALID and enqueues nothing (use ws_watershed instead).
+ *   - grad_d, dtype, shape, connectivity, labels_d as in ws_watershed.
+ *     count_d is required: it receives K, or -1 if the device detected an
+ *     error during the call (an iteration or time limit reached).
+ *   - Runs on the current device.  The first call on each device looks up the
+ *     array's device address (cudaGetSymbolAddress) and keeps it; make that
+ *     first call before any stream capture.
+ *   - Every call uses the same array: calls whose work overlaps on the GPU
+ *     (on different streams, or from different host threads) race and
+ *     corrupt each other's results.  Issue them one after another on one
+ *     stream, or synchronise between them.
+ */
+ws_status ws_watershed_static(const void *grad_d, ws_dtype dtype, const ws_shape *shape, int connectivity,
+                              int32_t *labels_d, int32_t *count_d, ws_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif
