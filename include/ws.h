@@ -199,6 +199,47 @@ ws_status ws_segment_host(ws_context *ctx, const void *grad_h, ws_dtype dtype, c
                           ws_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* batches                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* One image of a batch. */
+typedef struct {
+    const void *grad_d;   /* gradient samples [N], the batch's dtype */
+    ws_shape shape;       /* its own size; every image of a batch has the same ndim */
+    int32_t *levels_d;    /* int32 [NL*N] output, level 0 first (as ws_segment) */
+    int32_t *counts_d;    /* int32 [NL] output (may be NULL) */
+} ws_item;
+
+/*
+ * ws_segment for n images of uneven sizes at once (the hierarchy of Alg. 4
+ * for each image).  The images are processed together: their pixels and tiles
+ * are concatenated in the context's workspace and each phase is one launch
+ * over all of them, so small images do not leave the GPU idle.  Every image's
+ * result is exactly what ws_segment returns for it alone.
+ *   items         n descriptors (host memory, read during the call)
+ *   dtype, connectivity, NL   shared by all images
+ * The images' pixels must total below 2^31.
+ */
+ws_status ws_segment_batch(ws_context *ctx, int n, const ws_item *items, ws_dtype dtype, int connectivity, int NL,
+                           ws_stream_t stream);
+
+typedef struct ws_graph ws_graph;
+
+/*
+ * Records ws_segment_batch for this exact batch (same buffers) into a CUDA
+ * graph: one eager run sizes the workspace and uploads the image descriptors
+ * into memory owned by the graph, then the pipeline is captured.  Replaying it
+ * with ws_graph_launch costs one graph launch per batch.  The graph uses the
+ * context's workspace: calls on the context that grow the workspace
+ * invalidate it (ws_graph_launch then returns WS_ERR_INVALID), and calls
+ * whose work overlaps a replay on the device race with it.
+ */
+ws_status ws_graph_create(ws_context *ctx, int n, const ws_item *items, ws_dtype dtype, int connectivity, int NL,
+                          ws_stream_t stream, ws_graph **out);
+ws_status ws_graph_launch(ws_graph *g, ws_stream_t stream);
+void ws_graph_destroy(ws_graph *g);
+
+/* ------------------------------------------------------------------------ */
 /* step-level entry points (for parity checks of individual steps)           */
 /* ------------------------------------------------------------------------ */
 

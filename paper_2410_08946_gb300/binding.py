@@ -33,6 +33,11 @@ class ws_shape(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int32), ("pad_", ctypes.c_int32), ("dims", ctypes.c_int64 * 3)]
 
 
+class ws_item(ctypes.Structure):
+    _fields_ = [("grad_d", ctypes.c_void_p), ("shape", ws_shape), ("levels_d", ctypes.c_void_p),
+                ("counts_d", ctypes.c_void_p)]
+
+
 class ws_tuning(ctypes.Structure):
     _fields_ = [("plateau_round_cap", ctypes.c_int32), ("jump_round_cap", ctypes.c_int32),
                 ("jumps_per_round", ctypes.c_int32), ("barrier_timeout_ms", ctypes.c_int32),
@@ -80,6 +85,10 @@ def load(path: str = LIB_PATH):
             "ws_phase_name": ([I], ctypes.c_char_p),
             "ws_context_phase_times": ([P, P, P, I], I),
             "ws_context_launches": ([P], ctypes.c_ulonglong),
+            "ws_segment_batch": ([P, I, ctypes.POINTER(ws_item), I, I, I, P], I),
+            "ws_graph_create": ([P, I, ctypes.POINTER(ws_item), I, I, I, P, ctypes.POINTER(P)], I),
+            "ws_graph_launch": ([P, P], I),
+            "ws_graph_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -246,6 +255,38 @@ class Context:
                                      int(NL), _dev(levels), _dev(counts), _stream(stream)))
         return levels, counts
 
+    def _items(self, grads, NL, levels=None, counts=None):
+        import torch
+        n = len(grads)
+        if levels is None:
+            levels = [torch.empty((NL,) + tuple(g.shape), dtype=torch.int32, device=g.device) for g in grads]
+        if counts is None:
+            counts = [torch.empty(NL, dtype=torch.int32, device=g.device) for g in grads]
+        arr = (ws_item * n)()
+        for i, g in enumerate(grads):
+            arr[i].grad_d = _dev(g)
+            arr[i].shape = _shape_of(g.shape)
+            arr[i].levels_d = _dev(levels[i])
+            arr[i].counts_d = _dev(counts[i])
+        dt = _dtype_code(grads[0])
+        if any(_dtype_code(g) != dt for g in grads):
+            raise TypeError("every image of a batch must have the same dtype")
+        return arr, dt, levels, counts
+
+    def segment_batch(self, grads, conn: int, NL: int, levels=None, counts=None, stream=None):
+        """ws_segment for a list of images at once; returns (levels list, counts list)."""
+        arr, dt, levels, counts = self._items(grads, NL, levels, counts)
+        self._ok(self.lib.ws_segment_batch(self.handle, len(grads), arr, dt, int(conn), int(NL), _stream(stream)))
+        return levels, counts
+
+    def graph(self, grads, conn: int, NL: int, levels=None, counts=None, stream=None):
+        """Records the batch into a CUDA graph; returns a BatchGraph (with .levels, .counts)."""
+        arr, dt, levels, counts = self._items(grads, NL, levels, counts)
+        h = ctypes.c_void_p()
+        self._ok(self.lib.ws_graph_create(self.handle, len(grads), arr, dt, int(conn), int(NL), _stream(stream),
+                                          ctypes.byref(h)))
+        return BatchGraph(self, h, levels, counts)
+
     def segment_host(self, grad_h, conn: int, NL: int, levels_h=None, counts_h=None, stream=None):
         """grad_h, levels_h, counts_h: CPU tensors (pinned for speed).  Blocks until done."""
         import torch
@@ -260,3 +301,24 @@ class Context:
                                           ctypes.byref(sh), int(conn), int(NL), ctypes.c_void_p(levels_h.data_ptr()),
                                           ctypes.c_void_p(counts_h.data_ptr()), _stream(stream)))
         return levels_h, counts_h
+
+
+class BatchGraph:
+    """A batch recorded as a CUDA graph (ws_graph_create); launch() replays it."""
+
+    def __init__(self, ctx, handle, levels, counts):
+        self.ctx, self.handle, self.levels, self.counts = ctx, handle, levels, counts
+
+    def launch(self, stream=None):
+        self.ctx._ok(self.ctx.lib.ws_graph_launch(self.handle, _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.ws_graph_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "ws_internal.h"
 
@@ -35,6 +36,8 @@ static ws_status set_error(ws_context *c, ws_status st, const char *msg)
     return st;
 }
 
+ws_status set_error_msg(ws_context *c, ws_status st, const char *msg) { return set_error(c, st, msg); }
+
 template <typename P> static ws_status dalloc(ws_context *c, P **p, size_t bytes)
 {
     if (c->budget && c->held + bytes > c->budget) {
@@ -51,6 +54,7 @@ template <typename P> static ws_status dalloc(ws_context *c, P **p, size_t bytes
         return set_cuda_error(c, e, "cudaMalloc");
     }
     c->held += bytes;
+    c->generation++;
     *p = (P *)q;
     return WS_OK;
 }
@@ -186,6 +190,19 @@ static const char *const PHASE_NAMES[NPHASE] = {"step1",       "plateau", "resol
                                                 "compact",     "rag",     "levels",        "level_write",
                                                 "cleanup",     "gradient", "copy"};
 
+ws_status ensure_batch(ws_context *c, size_t n)
+{
+    Workspace &w = c->w;
+    if (n <= w.nbatch) return WS_OK;
+    dfree(c, &w.descs, w.nbatch * kDescBytes);
+    dfree(c, &w.rbase, (w.nbatch + 1) * 4);
+    w.nbatch = 0;
+    ws_status st;
+    if ((st = dalloc(c, (uint8_t **)&w.descs, n * kDescBytes)) || (st = dalloc(c, &w.rbase, (n + 1) * 4))) return st;
+    w.nbatch = n;
+    return WS_OK;
+}
+
 const Launchers *launchers(int dtype, int conn)
 {
     if (dtype == WS_U8) return launchers_u8(conn);
@@ -298,7 +315,7 @@ void ws_context_destroy(ws_context *c)
     void *ptrs[] = {w.par,   w.aux,    w.dist,   w.plat,   w.act,    w.tlist,  w.roots,  w.rootm,
                     w.counters, w.bitmap, w.gcnt, w.csum,   w.keys,   w.vals,   w.slots,  w.ecount,
                     w.gmap,  w.newmin, w.uf,     w.rank,   w.bsum,   w.kcount, w.grad_stage, w.levels_stage,
-                    w.counts_stage};
+                    w.counts_stage, w.descs, w.rbase};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &r : c->prof.pending) {
@@ -515,6 +532,120 @@ ws_status ws_segment_host(ws_context *c, const void *grad_h, ws_dtype dtype, con
     }
     if (e != cudaSuccess) return set_cuda_error(c, e, "D2H copy");
     return ws_context_check(c, stream);
+}
+
+static ws_status prep_batch(ws_context *c, int n, const ws_item *items, ws_dtype dtype, int conn, int NL,
+                            std::vector<Geo> &geos, const Launchers **L)
+{
+    if (!c) return WS_ERR_INVALID;
+    c->err.clear();
+    if (n < 1 || !items) return set_error(c, WS_ERR_INVALID, "empty batch");
+    if (NL < 1) return set_error(c, WS_ERR_INVALID, "NL must be >= 1");
+    geos.resize((size_t)n);
+    for (int i = 0; i < n; i++) {
+        ws_status st = make_geo(c, &items[i].shape, &geos[i]);
+        if (st) return st;
+        if (items[i].shape.ndim != items[0].shape.ndim) return set_error(c, WS_ERR_INVALID, "mixed ndim in a batch");
+        if (!items[i].grad_d || !items[i].levels_d) return set_error(c, WS_ERR_INVALID, "NULL buffer in a batch item");
+    }
+    ws_status st = check_conn(c, &items[0].shape, conn);
+    if (st) return st;
+    if (dtype != WS_U8 && dtype != WS_U16) return set_error(c, WS_ERR_INVALID, "dtype must be WS_U8 or WS_U16");
+    cudaSetDevice(c->device);
+    *L = launchers(dtype, conn);
+    if (!*L) return set_error(c, WS_ERR_UNSUPPORTED, "no pipeline for this dtype / connectivity");
+    return WS_OK;
+}
+
+ws_status ws_segment_batch(ws_context *c, int n, const ws_item *items, ws_dtype dtype, int conn, int NL,
+                           ws_stream_t stream)
+{
+    std::vector<Geo> geos;
+    const Launchers *L = nullptr;
+    ws_status st = prep_batch(c, n, items, dtype, conn, NL, geos, &L);
+    if (st) return st;
+    return L->segment_batch(c, n, geos.data(), items, NL, nullptr, (cudaStream_t)stream);
+}
+
+struct ws_graph {
+    ws_context *ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void *descs = nullptr;        // the batch's image descriptors (owned)
+    unsigned long long generation = 0;
+};
+
+void ws_graph_destroy(ws_graph *g)
+{
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->descs) cudaFree(g->descs);
+    delete g;
+}
+
+ws_status ws_graph_create(ws_context *c, int n, const ws_item *items, ws_dtype dtype, int conn, int NL,
+                          ws_stream_t stream, ws_graph **out)
+{
+    if (!out) return WS_ERR_INVALID;
+    *out = nullptr;
+    std::vector<Geo> geos;
+    const Launchers *L = nullptr;
+    ws_status st = prep_batch(c, n, items, dtype, conn, NL, geos, &L);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // eager run: sizes the workspace and checks the batch
+    if ((st = L->segment_batch(c, n, geos.data(), items, NL, nullptr, s))) return st;
+    if ((st = ws_context_check(c, stream))) return st;
+    ws_graph *g = new (std::nothrow) ws_graph();
+    if (!g) return WS_ERR_OOM;
+    g->ctx = c;
+    std::vector<unsigned char> host(L->desc_bytes * (size_t)n);
+    L->descs(n, geos.data(), items, host.data());
+    cudaError_t e = cudaMalloc(&g->descs, host.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g->descs, host.data(), host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        ws_graph_destroy(g);
+        return set_cuda_error(c, e, "graph descriptors");
+    }
+    cudaStream_t cap = nullptr;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        if (cap) cudaStreamDestroy(cap);
+        ws_graph_destroy(g);
+        return set_cuda_error(c, e, "begin capture");
+    }
+    const int prof = c->prof.on;
+    c->prof.on = 0;
+    const unsigned long long gen = c->generation;
+    st = L->segment_batch(c, n, geos.data(), items, NL, g->descs, cap);
+    c->prof.on = prof;
+    e = cudaStreamEndCapture(cap, &g->graph);
+    cudaStreamDestroy(cap);
+    if (st == WS_OK && e == cudaSuccess && c->generation != gen)
+        st = set_error(c, WS_ERR_INVALID, "workspace changed during capture");
+    if (st != WS_OK || e != cudaSuccess) {
+        ws_graph_destroy(g);
+        return st != WS_OK ? st : set_cuda_error(c, e, "capture");
+    }
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+        ws_graph_destroy(g);
+        return set_cuda_error(c, e, "graph instantiate");
+    }
+    g->generation = gen;
+    *out = g;
+    return WS_OK;
+}
+
+ws_status ws_graph_launch(ws_graph *g, ws_stream_t stream)
+{
+    if (!g || !g->exec) return WS_ERR_INVALID;
+    if (g->ctx->generation != g->generation)
+        return set_error(g->ctx, WS_ERR_INVALID, "the context's workspace changed since the graph was recorded");
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? WS_OK : set_cuda_error(g->ctx, e, "graph launch");
 }
 
 }  // extern "C"

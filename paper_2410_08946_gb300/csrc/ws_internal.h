@@ -41,6 +41,9 @@ struct Workspace {
     uint32_t *bitmap = nullptr;   // one bit per pixel index (kept zero)     [nwords]
     int32_t *gcnt = nullptr;      // popcount per 32-word group, then prefix [ngroups]
     int32_t *csum = nullptr;      // scan chunk sums                         [nchunks + 1]
+    size_t nbatch = 0;
+    void *descs = nullptr;        // image descriptors of a batch            [nbatch]
+    int32_t *rbase = nullptr;     // global id of each image's first basin   [nbatch + 1]
     // region adjacency hash table
     size_t edge_cap = 0;            // power of two
     unsigned long long *keys = nullptr;  // (a << 32 | b), empty = ~0
@@ -103,6 +106,7 @@ struct ws_context {
     ws::Workspace w;
     int num_sms = 0;
     unsigned long long launches = 0;  // kernels enqueued by this context
+    unsigned long long generation = 0; // bumped whenever workspace is reallocated
     ws::Prof prof;
 };
 
@@ -118,6 +122,9 @@ struct PhaseScope {
     ~PhaseScope();
 };
 
+// Bytes reserved per image descriptor of a batch (>= sizeof(ImgDesc)).
+constexpr size_t kDescBytes = 128;
+
 // Effective tuning values.
 int tune_plateau_cap(const ws_context *c);
 int tune_jump_cap(const ws_context *c);
@@ -128,6 +135,8 @@ unsigned long long tune_timeout_ns(const ws_context *c);
 ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles);
 ws_status ensure_edges(ws_context *c, size_t cap);
 ws_status ensure_regions(ws_context *c, size_t kmax, int levels);
+ws_status ensure_batch(ws_context *c, size_t n);
+ws_status set_error_msg(ws_context *c, ws_status st, const char *msg);
 ws_status set_cuda_error(ws_context *c, cudaError_t e, const char *what);
 
 // Launchers instantiated per (sample type, connectivity).
@@ -142,6 +151,10 @@ struct Launchers {
                            int32_t *levels, int32_t *counts, size_t kmax, cudaStream_t);
     ws_status (*segment)(ws_context *, const void *grad, const Geo &, int NL, int32_t *levels, int32_t *counts,
                          cudaStream_t);
+    ws_status (*segment_batch)(ws_context *, int n, const Geo *geos, const ws_item *items, int NL,
+                               const void *descs_dev, cudaStream_t);
+    size_t desc_bytes;                // sizeof one image descriptor
+    void (*descs)(int n, const Geo *geos, const ws_item *items, void *out);  // host descriptors, desc_bytes each
 };
 
 // dtype: 0 = u8, 1 = u16; conn: 4, 8, 6.  Returns nullptr when unsupported.

@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <string.h>
 
+#include <vector>
+
 #include "ws_tiles.cuh"
 
 namespace ws {
@@ -68,19 +70,52 @@ template <typename T, int CONN> static ws_status run_step1(ws_context *c, const 
 }
 
 // ---------------------------------------------------------------------------
-// the tiled watershed core
+// the tiled watershed core (one image, or a batch of images)
 // ---------------------------------------------------------------------------
+
+static_assert(sizeof(ImgDesc) <= kDescBytes, "image descriptor larger than its workspace slot");
+
+template <int CONN> static ImgDesc make_desc(const Geo &g, int base, int tile0, const void *grad, int32_t *out,
+                                             int32_t *counts)
+{
+    const TileGeo tg = tiles_for<CONN>(g);
+    ImgDesc d{};
+    d.W = g.W;
+    d.H = g.H;
+    d.D = g.D;
+    d.HW = g.HW;
+    d.N = g.N;
+    d.base = base;
+    d.tile0 = tile0;
+    d.ntx = tg.ntx;
+    d.nty = tg.nty;
+    d.ntz = tg.ntz;
+    d.grad = grad;
+    d.out = out;
+    d.counts = counts;
+    return d;
+}
+
+template <int CONN> static Batch single_batch(const Geo &g, const void *grad, int32_t *out, int32_t *counts)
+{
+    Batch b{};
+    b.one = make_desc<CONN>(g, 0, 0, grad, out, counts);
+    b.d = nullptr;
+    b.n = 1;
+    b.ntiles = b.one.ntx * b.one.nty * b.one.ntz;
+    b.npix = g.N;
+    return b;
+}
 
 // Steps I and II: leaves in-tile path ends in w.par, step II distances of
 // the plateau tiles in w.dist, the plateau tiles in w.tlist.
-template <typename T, int CONN> static ws_status run_front(ws_context *c, const T *g, const Geo &geo,
-                                                           const TileGeo &tg, cudaStream_t s)
+template <typename T, int CONN> static ws_status run_front(ws_context *c, const Batch &b, cudaStream_t s)
 {
     using C = TC<CONN>;
     Workspace &w = c->w;
-    ws_status st = ensure_pixels(c, geo.N, tg.ntiles);
+    ws_status st = ensure_pixels(c, b.npix, b.ntiles);
     if (st != WS_OK) return st;
-    cudaError_t e = cudaMemsetAsync(w.act, 0, 2 * (size_t)tg.ntiles, s);
+    cudaError_t e = cudaMemsetAsync(w.act, 0, 2 * (size_t)b.ntiles, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 16, s);
     if (e == cudaSuccess) e = reset_barrier(c, s);
     if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
@@ -88,20 +123,20 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
         PhaseScope ps(c, PH_STEP1, s);
         using B = InitBox<T, CONN>;
         CUtensorMap tm;
-        const bool tma = make_tmap_3d(&tm, g, sizeof(T), geo.W, geo.H, geo.D, B::RW, C::HY, C::HZ);
+        const bool tma = !b.d && make_tmap_3d(&tm, b.one.grad, sizeof(T), b.one.W, b.one.H, b.one.D, B::RW, C::HY,
+                                              C::HZ);
         if (tma) {
             if ((e = allow_smem(k_init<T, CONN, true>, B::SMEM_TMA)) != cudaSuccess)
                 return set_cuda_error(c, e, "smem attribute");
-            const int grid = coop_grid(c, k_init<T, CONN, true>, C::NT, B::SMEM_TMA, tg.ntiles);
-            k_init<T, CONN, true><<<grid, C::NT, B::SMEM_TMA, s>>>(tm, g, geo, tg, w.par, w.aux, w.dist, w.plat, w.act,
+            const int grid = coop_grid(c, k_init<T, CONN, true>, C::NT, B::SMEM_TMA, b.ntiles);
+            k_init<T, CONN, true><<<grid, C::NT, B::SMEM_TMA, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act,
                                                                    w.tlist, w.roots, w.counters, c->status);
         } else {
             memset(&tm, 0, sizeof tm);
             if ((e = allow_smem(k_init<T, CONN, false>, B::SMEM_PLAIN)) != cudaSuccess)
                 return set_cuda_error(c, e, "smem attribute");
-            k_init<T, CONN, false><<<tg.ntiles, C::NT, B::SMEM_PLAIN, s>>>(tm, g, geo, tg, w.par, w.aux, w.dist, w.plat,
-                                                                          w.act, w.tlist, w.roots, w.counters,
-                                                                          c->status);
+            k_init<T, CONN, false><<<b.ntiles, C::NT, B::SMEM_PLAIN, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act,
+                                                                         w.tlist, w.roots, w.counters, c->status);
         }
         c->launches += 1;
     }
@@ -109,8 +144,8 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
         PhaseScope ps(c, PH_PLATEAU, s);
         const size_t smem = (size_t)C::HS * 8;
         if ((e = allow_smem(k_plateau2<T, CONN>, smem)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
-        const int grid = coop_grid(c, k_plateau2<T, CONN>, C::NT, smem, tg.ntiles);
-        e = launch_coop(k_plateau2<T, CONN>, grid, C::NT, smem, s, g, geo, tg, w.dist, (const uint8_t *)w.plat, w.act,
+        const int grid = coop_grid(c, k_plateau2<T, CONN>, C::NT, smem, b.ntiles);
+        e = launch_coop(k_plateau2<T, CONN>, grid, C::NT, smem, s, b, w.dist, (const uint8_t *)w.plat, w.act,
                         (const int32_t *)w.tlist, (const int32_t *)w.counters, c->status, tune_plateau_cap(c),
                         tune_timeout_ns(c));
         c->launches += 1;
@@ -119,38 +154,35 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
     return WS_OK;
 }
 
-// Whole watershed: roots in w.par, canonical id of every root in w.aux,
-// K0 in w.counters[CNT_ROOTS]; with do_rag, the region table holds every
-// adjacent pair of basins (keyed by root pixel) with its pass value.
-template <typename T, int CONN> static ws_status run_core(ws_context *c, const T *g, const Geo &geo, bool do_rag,
-                                                          cudaStream_t s)
+// Whole watershed of a batch: roots in w.par, global canonical id of every
+// root in w.aux (ids ordered image by image), total K0 in
+// w.counters[CNT_ROOTS]; with do_rag, the region table holds every adjacent
+// pair of basins (keyed by root pixel) with its pass value.
+template <typename T, int CONN> static ws_status run_core(ws_context *c, const Batch &b, bool do_rag, cudaStream_t s)
 {
     using C = TC<CONN>;
-    const TileGeo tg = tiles_for<CONN>(geo);
-    ws_status st = run_front<T, CONN>(c, g, geo, tg, s);
+    ws_status st = run_front<T, CONN>(c, b, s);
     if (st != WS_OK) return st;
     Workspace &w = c->w;
     cudaError_t e = cudaSuccess;
     {
         PhaseScope ps(c, PH_RESOLVE, s);
-        const int grid = tg.ntiles < c->num_sms * 8 ? tg.ntiles : c->num_sms * 8;
-        k_resolve2<T, CONN><<<grid, C::NT, 0, s>>>(g, geo, tg, w.par, w.dist, w.plat, w.tlist, w.counters,
-                                                   c->status);
+        const int grid = b.ntiles < c->num_sms * 8 ? b.ntiles : c->num_sms * 8;
+        k_resolve2<T, CONN><<<grid, C::NT, 0, s>>>(b, w.par, w.dist, w.plat, w.tlist, w.counters, c->status);
         c->launches += 1;
     }
     if ((e = reset_barrier(c, s)) != cudaSuccess) return set_cuda_error(c, e, "memset");
     {
         PhaseScope ps(c, PH_JUMP, s);
         const int grid = coop_grid(c, k_jump2<CONN>, NTHR, 0, c->num_sms * 8);
-        e = launch_coop(k_jump2<CONN>, grid, NTHR, 0, s, geo, tg, w.par, (const int32_t *)w.dist,
-                        (const int32_t *)w.tlist, w.counters, w.roots, tune_rr(c), c->status, tune_jump_cap(c),
-                        tune_timeout_ns(c));
+        e = launch_coop(k_jump2<CONN>, grid, NTHR, 0, s, b, w.par, (const int32_t *)w.dist, (const int32_t *)w.tlist,
+                        w.counters, w.roots, tune_rr(c), c->status, tune_jump_cap(c), tune_timeout_ns(c));
         c->launches += 1;
         if (e != cudaSuccess) return set_cuda_error(c, e, "jump launch");
     }
     if (do_rag) {
         const int halfn = Nb<CONN>::n / 2;
-        size_t want = (size_t)geo.N * halfn / 8;
+        size_t want = (size_t)b.npix * halfn / 8;
         if (c->tun.edge_capacity > 0) want = (size_t)c->tun.edge_capacity;
         size_t cap = 1 << 16;
         while (cap < want && cap < ((size_t)1 << 28)) cap <<= 1;
@@ -160,45 +192,63 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const T
         PhaseScope ps(c, PH_RAG, s);
         using B = LabelBox<T, CONN>;
         CUtensorMap tmp, tmg;
-        const bool tma = make_tmap_3d(&tmp, w.par, 4, geo.W, geo.H, geo.D, B::RWP, C::BY, C::BZ) &&
-                         make_tmap_3d(&tmg, g, sizeof(T), geo.W, geo.H, geo.D, B::RWG, C::BY, C::BZ);
+        const bool tma = !b.d && make_tmap_3d(&tmp, w.par, 4, b.one.W, b.one.H, b.one.D, B::RWP, C::BY, C::BZ) &&
+                         make_tmap_3d(&tmg, b.one.grad, sizeof(T), b.one.W, b.one.H, b.one.D, B::RWG, C::BY, C::BZ);
         const unsigned long long gmask = w.edge_cap ? w.edge_cap - 1 : 0;
         if (tma) {
             if ((e = allow_smem(k_label<T, CONN, true>, B::SMEM)) != cudaSuccess)
                 return set_cuda_error(c, e, "smem attribute");
-            k_label<T, CONN, true><<<tg.ntiles, C::NT, B::SMEM, s>>>(tmp, tmg, g, geo, tg, w.par, w.aux, do_rag ? 1 : 0,
-                                                                     w.keys, w.vals, w.slots, w.ecount, gmask,
-                                                                     c->status);
+            k_label<T, CONN, true><<<b.ntiles, C::NT, B::SMEM, s>>>(tmp, tmg, b, w.par, w.aux, do_rag ? 1 : 0, w.keys,
+                                                                    w.vals, w.slots, w.ecount, gmask, c->status);
         } else {
             memset(&tmp, 0, sizeof tmp);
             memset(&tmg, 0, sizeof tmg);
             if ((e = allow_smem(k_label<T, CONN, false>, B::SMEM)) != cudaSuccess)
                 return set_cuda_error(c, e, "smem attribute");
-            k_label<T, CONN, false><<<tg.ntiles, C::NT, B::SMEM, s>>>(tmp, tmg, g, geo, tg, w.par, w.aux,
-                                                                      do_rag ? 1 : 0, w.keys, w.vals, w.slots,
-                                                                      w.ecount, gmask, c->status);
+            k_label<T, CONN, false><<<b.ntiles, C::NT, B::SMEM, s>>>(tmp, tmg, b, w.par, w.aux, do_rag ? 1 : 0,
+                                                                     w.keys, w.vals, w.slots, w.ecount, gmask,
+                                                                     c->status);
         }
         c->launches += 1;
     }
     {
         PhaseScope ps(c, PH_COMPACT, s);
-        const int ng = (int)((geo.N + 1023) / 1024), nw = (int)((geo.N + 31) / 32);
+        const int ng = (int)((b.npix + 1023) / 1024), nw = (int)((b.npix + 31) / 32);
         const int nch = (ng + SCAN_CHUNK - 1) / SCAN_CHUNK;
         const int rg = c->num_sms * 4;
-        k_rank_mark<<<rg, NTHR, 0, s>>>(geo.N, w.roots, w.counters, w.aux, w.rootm, w.bitmap, c->status);
+        k_rank_mark<<<rg, NTHR, 0, s>>>(b.npix, w.roots, w.counters, w.aux, w.rootm, w.bitmap, c->status);
         k_rank_groups<<<(ng + NTHR / 32 - 1) / (NTHR / 32), NTHR, 0, s>>>(w.bitmap, nw, w.gcnt, ng);
         k_scan_chunks<<<nch, NTHR, 0, s>>>(w.gcnt, ng, w.csum);
         k_scan<<<1, 1024, 0, s>>>(w.csum, nch, nullptr);
         k_scan_add<<<nch, NTHR, 0, s>>>(w.gcnt, ng, w.csum);
         k_rank_assign<<<rg, NTHR, 0, s>>>(w.roots, w.counters, w.rootm, w.bitmap, w.gcnt, w.aux);
+        c->launches += 6;
+        if (b.d) {
+            k_rank_bases<<<(b.n + NTHR) / NTHR, NTHR, 0, s>>>(b, w.bitmap, w.gcnt, w.counters, w.rbase);
+            c->launches += 1;
+        }
         k_rank_clear<<<rg, NTHR, 0, s>>>(w.counters, w.rootm, w.bitmap);
-        c->launches += 7;
+        c->launches += 1;
     }
     e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "watershed launch");
 }
 
-// One pass writing level 0 (canonical ids) and levels 1..NL-1.
+// Descriptors of a batch, as run_segment_batch builds them (for callers that
+// upload them once, e.g. before capturing a graph).
+template <int CONN> static void batch_descs(int n, const Geo *geos, const ws_item *items, std::vector<ImgDesc> &out)
+{
+    out.resize((size_t)n);
+    long long npix = 0, ntiles = 0;
+    for (int i = 0; i < n; i++) {
+        out[i] = make_desc<CONN>(geos[i], (int)npix, (int)ntiles, items[i].grad_d, items[i].levels_d,
+                                 items[i].counts_d);
+        npix += geos[i].N;
+        ntiles += (long long)out[i].ntx * out[i].nty * out[i].ntz;
+    }
+}
+
+// One pass writing level 0 (canonical ids) and levels 1..NL-1 of one image.
 static inline ws_status run_write(ws_context *c, const Geo &geo, int NL, int32_t *out, cudaStream_t s)
 {
     Workspace &w = c->w;
@@ -247,7 +297,8 @@ static inline ws_status run_cleanup(ws_context *c, cudaStream_t s)
 template <typename T, int CONN> static ws_status run_watershed(ws_context *c, const void *grad, const Geo &geo,
                                                                int32_t *labels, int32_t *count, cudaStream_t s)
 {
-    ws_status st = run_core<T, CONN>(c, (const T *)grad, geo, false, s);
+    const Batch b = single_batch<CONN>(geo, grad, labels, nullptr);
+    ws_status st = run_core<T, CONN>(c, b, false, s);
     if (st != WS_OK) return st;
     if ((st = run_write(c, geo, 1, labels, s)) != WS_OK) return st;
     if (count) {
@@ -265,7 +316,8 @@ template <typename T, int CONN> static ws_status run_segment(ws_context *c, cons
     ws_status st;
     // distinct minimal plateaux are never adjacent, so K0 <= ceil(N / 2)
     if (NL > 1 && (st = ensure_regions(c, (size_t)geo.N / 2 + 2, NL - 1)) != WS_OK) return st;
-    if ((st = run_core<T, CONN>(c, (const T *)grad, geo, NL > 1, s)) != WS_OK) return st;
+    const Batch b = single_batch<CONN>(geo, grad, levels, counts);
+    if ((st = run_core<T, CONN>(c, b, NL > 1, s)) != WS_OK) return st;
     if (NL > 1) {
         if ((st = run_levels(c, NL, w.aux, w.counters + CNT_ROOTS, counts, s)) != WS_OK) return st;
     } else if (counts) {
@@ -277,14 +329,62 @@ template <typename T, int CONN> static ws_status run_segment(ws_context *c, cons
     return WS_OK;
 }
 
+// A batch of images (same dtype and connectivity) in one launch per phase:
+// the images' pixels and tiles are concatenated in the workspace.
+// descs_dev: device copy of the descriptors made by the caller (graph
+// capture), or nullptr to upload them into the workspace here.
+template <typename T, int CONN> static ws_status run_segment_batch(ws_context *c, int n, const Geo *geos,
+                                                                   const ws_item *items, int NL, const void *descs_dev,
+                                                                   cudaStream_t s)
+{
+    Workspace &w = c->w;
+    std::vector<ImgDesc> descs((size_t)n);
+    long long npix = 0, ntiles = 0, kmax = 0;
+    for (int i = 0; i < n; i++) {
+        descs[i] = make_desc<CONN>(geos[i], (int)npix, (int)ntiles, items[i].grad_d, items[i].levels_d,
+                                   items[i].counts_d);
+        npix += geos[i].N;
+        ntiles += (long long)descs[i].ntx * descs[i].nty * descs[i].ntz;
+        kmax += geos[i].N / 2 + 1;
+    }
+    if (npix >= 0x7fffffffLL || ntiles >= 0x7fffffffLL)
+        return set_error_msg(c, WS_ERR_INVALID, "batch too large: the images' pixels must total below 2^31");
+    ws_status st;
+    if ((st = ensure_batch(c, (size_t)n)) != WS_OK) return st;
+    if (NL > 1 && (st = ensure_regions(c, (size_t)kmax + 2, NL - 1)) != WS_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (!descs_dev) {
+        e = cudaMemcpyAsync(w.descs, descs.data(), sizeof(ImgDesc) * (size_t)n, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return set_cuda_error(c, e, "descriptor upload");
+    }
+    Batch b{};
+    b.d = (const ImgDesc *)(descs_dev ? descs_dev : w.descs);
+    b.n = n;
+    b.ntiles = (int)ntiles;
+    b.npix = (int)npix;
+    if ((st = run_core<T, CONN>(c, b, NL > 1, s)) != WS_OK) return st;
+    if (NL > 1 && (st = run_levels(c, NL, w.aux, w.counters + CNT_ROOTS, nullptr, s)) != WS_OK) return st;
+    {
+        PhaseScope ps(c, PH_LEVEL_WRITE, s);
+        k_write_batch<<<pixel_grid(c, b.npix), NTHR, 0, s>>>(b, w.par, w.aux, w.gmap, w.kmax, NL, w.rbase,
+                                                             w.counters + CNT_ROOTS);
+        k_counts_batch<<<(n + NTHR - 1) / NTHR, NTHR, 0, s>>>(b, w.gmap, w.kmax, NL, w.rbase);
+        c->launches += 2;
+    }
+    if (NL > 1) return run_cleanup(c, s);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "batch launch");
+}
+
 template <typename T, int CONN> static ws_status run_plateau_distance(ws_context *c, const void *grad,
                                                                       const Geo &geo, int32_t *dist,
                                                                       cudaStream_t s)
 {
-    const TileGeo tg = tiles_for<CONN>(geo);
-    ws_status st = run_front<T, CONN>(c, (const T *)grad, geo, tg, s);
+    const Batch b = single_batch<CONN>(geo, grad, nullptr, nullptr);
+    ws_status st = run_front<T, CONN>(c, b, s);
     if (st != WS_OK) return st;
-    k_dist_out2<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo, tg, c->w.par, c->w.dist, c->w.plat, dist);
+    k_dist_out2<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo, tiles_for<CONN>(geo), c->w.par, c->w.dist, c->w.plat,
+                                                      dist);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "plateau distance");
@@ -334,11 +434,19 @@ template <typename T, int CONN> static ws_status run_waterfall(ws_context *c, co
     return run_cleanup(c, s);
 }
 
+template <int CONN> static void descs_host(int n, const Geo *geos, const ws_item *items, void *out)
+{
+    std::vector<ImgDesc> v;
+    batch_descs<CONN>(n, geos, items, v);
+    memcpy(out, v.data(), sizeof(ImgDesc) * (size_t)n);
+}
+
 template <typename T, int CONN> struct Inst {
     static const Launchers *get()
     {
         static const Launchers L = {&run_watershed<T, CONN>, &run_step1<T, CONN>, &run_plateau_distance<T, CONN>,
-                                    &run_waterfall<T, CONN>, &run_segment<T, CONN>};
+                                    &run_waterfall<T, CONN>, &run_segment<T, CONN>,
+                                    &run_segment_batch<T, CONN>, sizeof(ImgDesc), &descs_host<CONN>};
         return &L;
     }
 };

@@ -83,15 +83,91 @@ enum { CNT_TILES = 0, CNT_ROOTS = 1, CNT_K0 = 2, CNT_NGROUPS = 3 };
 __device__ __forceinline__ int enc_final(int g) { return -1 - g; }
 __device__ __forceinline__ int dec_final(int e) { return -1 - e; }
 
-template <int CONN>
-__device__ __forceinline__ void tile_origin(const TileGeo &tg, int t, int &x0, int &y0, int &z0)
+// One image of a batch.  Images are concatenated in the workspace: pixel p
+// of image i has the global index base + p, its tiles are tile0 ...
+// tile0 + ntx*nty*ntz - 1 of the global tile space.
+struct ImgDesc {
+    int W, H, D, HW, N;
+    int base;                 // first global pixel index
+    int tile0;                // first global tile index
+    int ntx, nty, ntz;
+    int pad_[2];
+    const void *grad;         // gradient samples [N]
+    int32_t *out;             // NL label planes, plane stride N
+    int32_t *counts;          // NL region counts (may be null)
+};
+
+// A batch: one image inline (d == nullptr), or n descriptors in device memory.
+struct Batch {
+    ImgDesc one;
+    const ImgDesc *d;
+    int n;
+    int ntiles;               // tiles of all images
+    int npix;                 // pixels of all images
+};
+
+__device__ __forceinline__ ImgDesc img_desc(const Batch &b, int i) { return b.d ? b.d[i] : b.one; }
+
+// image owning global tile t / global pixel g (binary search over the batch)
+__device__ __forceinline__ int img_of_tile(const Batch &b, int t)
 {
-    const int tx = t % tg.ntx, ty = (t / tg.ntx) % tg.nty, tz = t / (tg.ntx * tg.nty);
-    x0 = tx * TT<CONN>::TX;
-    y0 = ty * TT<CONN>::TY;
-    z0 = tz * TT<CONN>::TZ;
+    if (!b.d) return 0;
+    int lo = 0, hi = b.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&b.d[mid].tile0) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int img_of_pixel(const Batch &b, int g)
+{
+    if (!b.d) return 0;
+    int lo = 0, hi = b.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&b.d[mid].base) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
+// Everything a CTA needs about the tile it works on.
+struct TileCtx {
+    Geo geo;                  // the image's geometry
+    TileGeo tg;               // the image's tiling (tile ids local to the image)
+    int base, tile0;          // global offsets of the image
+    int x0, y0, z0;           // tile origin in the image
+    const void *grad;
+};
+
+template <int CONN> __device__ __forceinline__ TileCtx tile_ctx(const Batch &b, int t)
+{
+    const ImgDesc d = img_desc(b, img_of_tile(b, t));
+    TileCtx c;
+    c.geo.W = d.W;
+    c.geo.H = d.H;
+    c.geo.D = d.D;
+    c.geo.HW = d.HW;
+    c.geo.N = d.N;
+    c.tg.TX = TT<CONN>::TX;
+    c.tg.TY = TT<CONN>::TY;
+    c.tg.TZ = TT<CONN>::TZ;
+    c.tg.ntx = d.ntx;
+    c.tg.nty = d.nty;
+    c.tg.ntz = d.ntz;
+    c.tg.ntiles = d.ntx * d.nty * d.ntz;
+    c.base = d.base;
+    c.tile0 = d.tile0;
+    const int lt = t - d.tile0;
+    c.x0 = (lt % d.ntx) * TT<CONN>::TX;
+    c.y0 = ((lt / d.ntx) % d.nty) * TT<CONN>::TY;
+    c.z0 = (lt / (d.ntx * d.nty)) * TT<CONN>::TZ;
+    c.grad = d.grad;
+    return c;
+}
+
+// local tile id of pixel (x, y, z) of an image
 __device__ __forceinline__ int tile_of(const TileGeo &tg, int x, int y, int z)
 {
     return ((z / tg.TZ) * tg.nty + y / tg.TY) * tg.ntx + x / tg.TX;
@@ -119,13 +195,12 @@ template <typename T, int CONN> struct InitBox {
 };
 
 template <typename T, int CONN, bool TMA>
-__device__ __forceinline__ void init_issue(const CUtensorMap *tm, T *dst, uint64_t *bar, const TileGeo &tg, int t)
+__device__ __forceinline__ void init_issue(const CUtensorMap *tm, T *dst, uint64_t *bar, const Batch &b, int t)
 {
     using B = InitBox<T, CONN>;
-    int x0, y0, z0;
-    tile_origin<CONN>(tg, t, x0, y0, z0);
+    const TileCtx tc = tile_ctx<CONN>(b, t);
     mbar_arrive_expect_tx(bar, B::BYTES);
-    tma_load_3d(dst, tm, x0 - B::A, y0 - 1, TC<CONN>::D3 ? z0 - 1 : 0, bar);
+    tma_load_3d(dst, tm, tc.x0 - B::A, tc.y0 - 1, TC<CONN>::D3 ? tc.z0 - 1 : 0, bar);
 }
 
 // Step I (Eq. 1) for this thread's pixels of one tile, from the gradient box
@@ -137,7 +212,7 @@ __device__ __forceinline__ void init_issue(const CUtensorMap *tm, T *dst, uint64
 // side columns are read once into registers and the z neighbours reused.
 template <typename T, int CONN, bool CHECK>
 __device__ __forceinline__ int init_step1(const T *gs, int *nx, int (&st)[TC<CONN>::PER], int tid, int x0, int y0,
-                                          int z0, const Geo &geo)
+                                          int z0, const Geo &geo, int base)
 {
     using C = TC<CONN>;
     using B = InitBox<T, CONN>;
@@ -161,7 +236,7 @@ __device__ __forceinline__ int init_step1(const T *gs, int *nx, int (&st)[TC<CON
             nx[i] = enc_final(0);
             continue;
         }
-        const int p = (z * geo.H + y) * geo.W + x;
+        const int p = base + (z * geo.H + y) * geo.W + x;   // global index
         const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * B::RW + lx + B::A;
         const unsigned gp = COL ? cz[k + 1] : (unsigned)gs[h];
         unsigned m = 0xffffffffu;
@@ -203,12 +278,11 @@ __device__ __forceinline__ int init_step1(const T *gs, int *nx, int (&st)[TC<CON
 }
 
 template <typename T, int CONN, bool TMA>
-__global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ CUtensorMap tm, const T *__restrict__ g,
-                                                       Geo geo, TileGeo tg, int32_t *__restrict__ par,
-                                                       int32_t *__restrict__ mi, int32_t *__restrict__ dist,
-                                                       uint8_t *__restrict__ plat, uint8_t *__restrict__ act,
-                                                       int32_t *__restrict__ tlist, int32_t *__restrict__ roots,
-                                                       int32_t *counters, DevStatus *status)
+__global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ CUtensorMap tm, const Batch b,
+                                                       int32_t *__restrict__ par, int32_t *__restrict__ mi,
+                                                       int32_t *__restrict__ dist, uint8_t *__restrict__ plat,
+                                                       uint8_t *__restrict__ act, int32_t *__restrict__ tlist,
+                                                       int32_t *__restrict__ roots, int32_t *counters, DevStatus *status)
 {
     using C = TC<CONN>;
     using B = InitBox<T, CONN>;
@@ -218,24 +292,26 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
     const int tid = threadIdx.x, lane = tid & 31;
     const int G = gridDim.x;
 
-    if (TMA) {
+    if (TMA) {  // a single image (b.one); two tiles in flight per CTA
         if (tid == 0) {
             mbar_init(&bars[0], 1);
             mbar_init(&bars[1], 1);
             mbar_fence_init();
             const int t0 = blockIdx.x;
-            if (t0 < tg.ntiles) init_issue<T, CONN, TMA>(&tm, (T *)smem, &bars[0], tg, t0);
-            if (t0 + G < tg.ntiles) init_issue<T, CONN, TMA>(&tm, (T *)(smem + B::STAGE), &bars[1], tg, t0 + G);
+            if (t0 < b.ntiles) init_issue<T, CONN, TMA>(&tm, (T *)smem, &bars[0], b, t0);
+            if (t0 + G < b.ntiles) init_issue<T, CONN, TMA>(&tm, (T *)(smem + B::STAGE), &bars[1], b, t0 + G);
         }
         __syncthreads();
     }
 
     int j = 0;
-    for (int t = blockIdx.x; t < tg.ntiles; t += G, j++) {
+    for (int t = blockIdx.x; t < b.ntiles; t += G, j++) {
         const int s = TMA ? (j & 1) : 0;
         T *gs = (T *)(smem + s * B::STAGE);
-        int x0, y0, z0;
-        tile_origin<CONN>(tg, t, x0, y0, z0);
+        const TileCtx tc = tile_ctx<CONN>(b, t);
+        const Geo &geo = tc.geo;
+        const int x0 = tc.x0, y0 = tc.y0, z0 = tc.z0, base = tc.base;
+        const T *g = (const T *)tc.grad;
         if (TMA) {
             const bool ok = mbar_wait(&bars[s], (unsigned)((j >> 1) & 1), status);
             if (__syncthreads_or(!ok)) return;
@@ -271,12 +347,12 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
         const bool interior = x0 >= 1 && x0 + C::TX < geo.W && y0 >= 1 && y0 + C::TY < geo.H &&
                               (!C::D3 || (z0 >= 1 && z0 + C::TZ < geo.D));
         if (interior)
-            plateau = init_step1<T, CONN, false>(gs, nx, st, tid, x0, y0, z0, geo);
+            plateau = init_step1<T, CONN, false>(gs, nx, st, tid, x0, y0, z0, geo, base);
         else
-            plateau = init_step1<T, CONN, true>(gs, nx, st, tid, x0, y0, z0, geo);
+            plateau = init_step1<T, CONN, true>(gs, nx, st, tid, x0, y0, z0, geo, base);
         __syncthreads();  // the gradient box of stage s is no longer read
-        if (TMA && tid == 0 && t + 2 * G < tg.ntiles)
-            init_issue<T, CONN, TMA>(&tm, gs, &bars[s], tg, t + 2 * G);
+        if (TMA && tid == 0 && t + 2 * G < b.ntiles)
+            init_issue<T, CONN, TMA>(&tm, gs, &bars[s], b, t + 2 * G);
 
         // step III inside the tile: pointer doubling through shared memory
         // (in place: every value read is the pointer of a pixel further down
@@ -302,7 +378,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
             const int i = tid + k * C::NT;
             if (st[k] == STOUT) continue;
             const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
-            const int p = ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
+            const int p = base + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
             const int e = vnx[i];
             par[p] = e < 0 ? dec_final(e) : p;  // e >= 0 cannot survive 32 doubling rounds
             if (st[k] != ST0) mi[p] = 0x7fffffff;
@@ -311,15 +387,15 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
 #pragma unroll
         for (int k = 0; k < C::PER; k++) {
             const bool isr = st[k] == ST1;
-            const unsigned b = __ballot_sync(0xffffffffu, isr);
-            if (!b) continue;
-            int base = 0;
-            if (lane == 0) base = atomicAdd(counters + CNT_ROOTS, __popc(b));
-            base = __shfl_sync(0xffffffffu, base, 0);
+            const unsigned bb = __ballot_sync(0xffffffffu, isr);
+            if (!bb) continue;
+            int rb = 0;
+            if (lane == 0) rb = atomicAdd(counters + CNT_ROOTS, __popc(bb));
+            rb = __shfl_sync(0xffffffffu, rb, 0);
             if (isr) {
                 const int i = tid + k * C::NT;
                 const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
-                roots[base + __popc(b & ((1u << lane) - 1u))] = ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
+                roots[rb + __popc(bb & ((1u << lane) - 1u))] = base + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
             }
         }
         if (__syncthreads_or(plateau)) {
@@ -328,7 +404,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
                 if (st[k] == STOUT) continue;
                 const int i = tid + k * C::NT;
                 const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
-                const int p = ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
+                const int p = base + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
                 dist[p] = st[k] == ST0 ? 0 : (st[k] == ST1 ? -2 : INF_D);
             }
             if (tid == 0) {
@@ -349,11 +425,10 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
 // ---------------------------------------------------------------------------
 
 template <typename T, int CONN>
-__global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const T *__restrict__ g, Geo geo, TileGeo tg,
-                                                           int32_t *dist, const uint8_t *__restrict__ plat,
+__global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const Batch b, int32_t *dist, const uint8_t *__restrict__ plat,
                                                            uint8_t *act, const int32_t *__restrict__ tlist,
-                                                           const int32_t *counters, DevStatus *status,
-                                                           int round_cap, unsigned long long timeout_ns)
+                                                           const int32_t *counters, DevStatus *status, int round_cap,
+                                                           unsigned long long timeout_ns)
 {
     using C = TC<CONN>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -362,7 +437,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const T *__restrict__
     __shared__ int flag_s;
     const int tid = threadIdx.x;
     const int ntl = counters[CNT_TILES];
-    uint8_t *act0 = act, *act1 = act + tg.ntiles;
+    uint8_t *act0 = act, *act1 = act + b.ntiles;
 
     for (int r = 0;; r++) {
         uint8_t *cur = (r & 1) ? act1 : act0;
@@ -377,8 +452,10 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const T *__restrict__
             }
             __syncthreads();
             if (!flag_s) continue;
-            int x0, y0, z0;
-            tile_origin<CONN>(tg, t, x0, y0, z0);
+            const TileCtx tc = tile_ctx<CONN>(b, t);
+            const Geo &geo = tc.geo;
+            const T *g = (const T *)tc.grad;
+            const int x0 = tc.x0, y0 = tc.y0, z0 = tc.z0;
             for (int i = tid; i < C::HS; i += C::NT) {
                 const int hx = i % C::HX, hy = (i / C::HX) % C::HY, hz = i / (C::HX * C::HY);
                 const int x = x0 - 1 + hx, y = y0 - 1 + hy, z = C::D3 ? z0 - 1 + hz : 0;
@@ -387,7 +464,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const T *__restrict__
                     gs[i] = (int)g[q];
                     // a pixel of a tile without plateau pixels that is equal to a
                     // plateau neighbour has a lower neighbour: distance 0
-                    ds[i] = plat[tile_of(tg, x, y, z)] ? __ldcg(dist + q) : 0;
+                    ds[i] = plat[tc.tile0 + tile_of(tc.tg, x, y, z)] ? __ldcg(dist + tc.base + q) : 0;
                 } else {
                     gs[i] = -1;
                     ds[i] = INF_D;
@@ -431,21 +508,23 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const T *__restrict__
                 const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
                 const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * C::HX + lx + 1;
                 if (ds[h] != orig[k]) {
-                    __stcg(dist + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx, ds[h]);
+                    __stcg(dist + tc.base + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx, ds[h]);
                     if (lx == 0 || lx == C::TX - 1 || ly == 0 || ly == C::TY - 1 ||
                         (C::D3 && (lz == 0 || lz == C::TZ - 1)))
                         border = 1;
                 }
             }
             if (__syncthreads_or(border) && tid == 0) {
-                const int tx = t % tg.ntx, ty = (t / tg.ntx) % tg.nty, tz = t / (tg.ntx * tg.nty);
+                const TileGeo &tg = tc.tg;
+                const int lt = t - tc.tile0;
+                const int tx = lt % tg.ntx, ty = (lt / tg.ntx) % tg.nty, tz = lt / (tg.ntx * tg.nty);
                 for (int dz = (C::D3 ? -1 : 0); dz <= (C::D3 ? 1 : 0); dz++)
                     for (int dy = -1; dy <= 1; dy++)
                         for (int dx = -1; dx <= 1; dx++) {
                             const int ax = tx + dx, ay = ty + dy, az = tz + dz;
                             if (ax < 0 || ax >= tg.ntx || ay < 0 || ay >= tg.nty || az < 0 || az >= tg.ntz)
                                 continue;
-                            const int nt = (az * tg.nty + ay) * tg.ntx + ax;
+                            const int nt = tc.tile0 + (az * tg.nty + ay) * tg.ntx + ax;
                             if (nt != t && plat[nt]) nxt[nt] = 1;
                         }
                 atomicAdd(&status->changed[r % 3], 1);
@@ -469,8 +548,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const T *__restrict__
 // ---------------------------------------------------------------------------
 
 template <typename T, int CONN>
-__global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const T *__restrict__ g, Geo geo, TileGeo tg,
-                                                           int32_t *par, const int32_t *__restrict__ dist,
+__global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const Batch b, int32_t *par, const int32_t *__restrict__ dist,
                                                            const uint8_t *__restrict__ plat,
                                                            const int32_t *__restrict__ tlist,
                                                            const int32_t *counters, DevStatus *status)
@@ -478,14 +556,15 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const T *__restrict__
     using C = TC<CONN>;
     const int ntl = counters[CNT_TILES];
     for (int j = blockIdx.x; j < ntl; j += gridDim.x) {
-        int x0, y0, z0;
-        tile_origin<CONN>(tg, tlist[j], x0, y0, z0);
+        const TileCtx tc = tile_ctx<CONN>(b, tlist[j]);
+        const Geo &geo = tc.geo;
+        const T *g = (const T *)tc.grad;
         for (int i = threadIdx.x; i < C::NPIX; i += C::NT) {
             const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
-            const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+            const int x = tc.x0 + lx, y = tc.y0 + ly, z = tc.z0 + lz;
             if (x >= geo.W || y >= geo.H || z >= geo.D) continue;
             const int p = (z * geo.H + y) * geo.W + x;
-            const int d = dist[p];
+            const int d = dist[tc.base + p];
             if (d <= 0) continue;   // state 0 or minimum
             const unsigned gp = g[p];
             if (d < INF_D) {
@@ -496,22 +575,22 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const T *__restrict__
                     if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
                     const int q = (zz * geo.H + yy) * geo.W + xx;
                     if (g[q] != gp) continue;
-                    const int dq = plat[tile_of(tg, xx, yy, zz)] ? dist[q] : 0;
+                    const int dq = plat[tc.tile0 + tile_of(tc.tg, xx, yy, zz)] ? dist[tc.base + q] : 0;
                     if (dq == d - 1 && q > best) best = q;
                 }
                 if (best < 0) {
                     record_error(status, DEV_NONCONVERGED, 7);
                     best = p;
                 }
-                par[p] = best;
+                par[tc.base + p] = tc.base + best;
             } else {
 #pragma unroll
                 for (int n = Half<CONN>::first; n < Nb<CONN>::n; n++) {
                     const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
                     if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
-                    if (!plat[tile_of(tg, xx, yy, zz)]) continue;
+                    if (!plat[tc.tile0 + tile_of(tc.tg, xx, yy, zz)]) continue;
                     const int q = (zz * geo.H + yy) * geo.W + xx;
-                    if (dist[q] >= INF_D && g[q] == gp) uf_union(par, p, q, status);
+                    if (dist[tc.base + q] >= INF_D && g[q] == gp) uf_union(par, tc.base + p, tc.base + q, status);
                 }
             }
         }
@@ -523,7 +602,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const T *__restrict__
 // ---------------------------------------------------------------------------
 
 template <int CONN>
-__global__ void __launch_bounds__(NTHR) k_jump2(Geo geo, TileGeo tg, int32_t *par, const int32_t *__restrict__ dist,
+__global__ void __launch_bounds__(NTHR) k_jump2(const Batch b, int32_t *par, const int32_t *__restrict__ dist,
                                                 const int32_t *__restrict__ tlist, int32_t *counters,
                                                 int32_t *roots, int RR, DevStatus *status, int round_cap,
                                                 unsigned long long timeout_ns)
@@ -539,12 +618,11 @@ __global__ void __launch_bounds__(NTHR) k_jump2(Geo geo, TileGeo tg, int32_t *pa
         for (long long it = 0; it < iters; it++) {
             const long long e = it * stride + (long long)blockIdx.x * NTHR + tid;
             if (e >= total) continue;
-            int x0, y0, z0;
-            tile_origin<CONN>(tg, tlist[e / C::NPIX], x0, y0, z0);
+            const TileCtx tc = tile_ctx<CONN>(b, tlist[e / C::NPIX]);
             const int i = (int)(e % C::NPIX);
-            const int x = x0 + i % C::TX, y = y0 + (i / C::TX) % C::TY, z = z0 + i / (C::TX * C::TY);
-            if (x >= geo.W || y >= geo.H || z >= geo.D) continue;
-            const int p = (z * geo.H + y) * geo.W + x;
+            const int x = tc.x0 + i % C::TX, y = tc.y0 + (i / C::TX) % C::TY, z = tc.z0 + i / (C::TX * C::TY);
+            if (x >= tc.geo.W || y >= tc.geo.H || z >= tc.geo.D) continue;
+            const int p = tc.base + (z * tc.geo.H + y) * tc.geo.W + x;
             const int l0 = __ldcg(par + p);
             int l = l0;
             for (int k = 0; k < RR; k++) {
@@ -557,8 +635,8 @@ __global__ void __launch_bounds__(NTHR) k_jump2(Geo geo, TileGeo tg, int32_t *pa
                 ch = 1;
             }
         }
-        const unsigned b = __ballot_sync(0xffffffffu, ch);
-        if (lane == 0 && b) atomicAdd(&status->changed[r % 3], 1);
+        const unsigned bl = __ballot_sync(0xffffffffu, ch);
+        if (lane == 0 && bl) atomicAdd(&status->changed[r % 3], 1);
         __threadfence();
         if (!grid_barrier(status, timeout_ns)) return;
         if (*(volatile int *)&status->changed[r % 3] == 0) {
@@ -576,21 +654,20 @@ __global__ void __launch_bounds__(NTHR) k_jump2(Geo geo, TileGeo tg, int32_t *pa
         bool isr = false;
         int p = 0;
         if (e < total) {
-            int x0, y0, z0;
-            tile_origin<CONN>(tg, tlist[e / C::NPIX], x0, y0, z0);
+            const TileCtx tc = tile_ctx<CONN>(b, tlist[e / C::NPIX]);
             const int i = (int)(e % C::NPIX);
-            const int x = x0 + i % C::TX, y = y0 + (i / C::TX) % C::TY, z = z0 + i / (C::TX * C::TY);
-            if (x < geo.W && y < geo.H && z < geo.D) {
-                p = (z * geo.H + y) * geo.W + x;
+            const int x = tc.x0 + i % C::TX, y = tc.y0 + (i / C::TX) % C::TY, z = tc.z0 + i / (C::TX * C::TY);
+            if (x < tc.geo.W && y < tc.geo.H && z < tc.geo.D) {
+                p = tc.base + (z * tc.geo.H + y) * tc.geo.W + x;
                 isr = dist[p] >= INF_D && __ldcg(par + p) == p;
             }
         }
-        const unsigned b = __ballot_sync(0xffffffffu, isr);
-        if (!b) continue;
-        int base = 0;
-        if (lane == 0) base = atomicAdd(counters + CNT_ROOTS, __popc(b));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (isr) roots[base + __popc(b & ((1u << lane) - 1u))] = p;
+        const unsigned bl = __ballot_sync(0xffffffffu, isr);
+        if (!bl) continue;
+        int rb = 0;
+        if (lane == 0) rb = atomicAdd(counters + CNT_ROOTS, __popc(bl));
+        rb = __shfl_sync(0xffffffffu, rb, 0);
+        if (isr) roots[rb + __popc(bl & ((1u << lane) - 1u))] = p;
     }
 }
 
@@ -643,11 +720,10 @@ template <typename T, int CONN> struct LabelBox {
 
 template <typename T, int CONN, bool TMA>
 __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ CUtensorMap tmp,
-                                                        const __grid_constant__ CUtensorMap tmg,
-                                                        const T *__restrict__ g, Geo geo, TileGeo tg, int32_t *par,
-                                                        int32_t *mi, int do_rag, unsigned long long *keys,
-                                                        uint32_t *vals, int32_t *slots, int32_t *ecount,
-                                                        unsigned long long gmask, DevStatus *status)
+                                                        const __grid_constant__ CUtensorMap tmg, const Batch b,
+                                                        int32_t *par, int32_t *mi, int do_rag,
+                                                        unsigned long long *keys, uint32_t *vals, int32_t *slots,
+                                                        int32_t *ecount, unsigned long long gmask, DevStatus *status)
 {
     using C = TC<CONN>;
     using B = LabelBox<T, CONN>;
@@ -658,8 +734,10 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
     int *pb = (int *)(smem + B::OFF_P);
     T *gb = (T *)(smem + B::OFF_G);
     const int tid = threadIdx.x, lane = tid & 31;
-    int x0, y0, z0;
-    tile_origin<CONN>(tg, blockIdx.x, x0, y0, z0);
+    const TileCtx tc = tile_ctx<CONN>(b, blockIdx.x);   // TMA: a single image (b.one)
+    const Geo &geo = tc.geo;
+    const T *g = (const T *)tc.grad;
+    const int x0 = tc.x0, y0 = tc.y0, z0 = tc.z0, base = tc.base;
     if (TMA) {
         if (tid == 0) {
             mbar_init(&bar, 1);
@@ -696,7 +774,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
                     r[k] = pb[(bz * C::BY + by) * B::RWP + bx + B::AP - C::BXL];
                 } else {
                     const int q = (z * geo.H + y) * geo.W + x;
-                    r[k] = par[q];
+                    r[k] = par[base + q];
                     if (do_rag) gb[(bz * C::BY + by) * B::RWG + bx + B::AG - C::BXL] = g[q];
                 }
             }
@@ -735,7 +813,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
         const int bp = (lz * C::BY + ly) * B::RWP + lx + B::AP;
         const int bg = (lz * C::BY + ly) * B::RWG + lx + B::AG;
         const int r = in ? pb[bp] : -1;
-        const int p = in ? (z * geo.H + y) * geo.W + x : 0;
+        const int p = in ? base + (z * geo.H + y) * geo.W + x : 0;
         if (in) par[p] = r;
         // smallest pixel index of each basin: lanes are consecutive x of one
         // row, so the first lane of every run of equal roots holds the run's
@@ -827,6 +905,85 @@ static __global__ void __launch_bounds__(NTHR) k_rank_clear(const int32_t *count
         if (rootm[j] >= 0) bitmap[rootm[j] >> 5] = 0u;
 }
 
+// Canonical id of a root; ids outside [0, K0) can only come from an earlier
+// device error and are written as -1 instead of being used as an index.
+__device__ __forceinline__ int safe_id(const int32_t *__restrict__ idmap, int r, int K0)
+{
+    const int c = idmap[r];
+    return (unsigned)c < (unsigned)K0 ? c : -1;
+}
+
+__device__ __forceinline__ int level_id(const int32_t *__restrict__ gm, int c) { return c >= 0 ? gm[c] : -1; }
+
+// rbase[i] = number of basins (of the whole batch) whose smallest pixel index
+// lies below image i's first pixel, i.e. the global id of image i's first
+// basin; rbase[n] = total.  Image i's canonical ids are global ids - rbase[i].
+static __global__ void __launch_bounds__(NTHR) k_rank_bases(const Batch b, const unsigned *__restrict__ bitmap,
+                                                            const int32_t *__restrict__ gpre, const int32_t *counters,
+                                                            int32_t *rbase)
+{
+    for (int i = blockIdx.x * NTHR + threadIdx.x; i <= b.n; i += gridDim.x * NTHR) {
+        if (i == b.n) {
+            rbase[i] = counters[CNT_ROOTS];
+            continue;
+        }
+        const int m = img_desc(b, i).base;
+        const int w = m >> 5, gi = w >> 5;
+        int rank = gpre[gi];
+        for (int u = gi * 32; u < w; u++) rank += __popc(bitmap[u]);
+        rank += __popc(bitmap[w] & ((1u << (m & 31)) - 1u));
+        rbase[i] = rank;
+    }
+}
+
+// Batched level write: pixel g of the batch belongs to image i; its level-0
+// id is its basin's global id minus rbase[i], its level-k id the global
+// level-k id minus that of image i's first basin (regions never span images,
+// and global ids are ordered image by image).
+static __global__ void __launch_bounds__(NTHR) k_write_batch(const Batch b, const int32_t *__restrict__ par,
+                                                             const int32_t *__restrict__ idmap,
+                                                             const int32_t *__restrict__ gmap, size_t kstride, int NL,
+                                                             const int32_t *__restrict__ rbase,
+                                                             const int32_t *__restrict__ k0_ptr)
+{
+    const int K0 = *k0_ptr;
+    int cur = -1, lo = 0, hi = -1;   // cached image of the previous pixel
+    ImgDesc d{};
+    int rb = 0;
+    for (int g = blockIdx.x * NTHR + threadIdx.x; g < b.npix; g += gridDim.x * NTHR) {
+        if (g < lo || g > hi) {
+            cur = img_of_pixel(b, g);
+            d = img_desc(b, cur);
+            lo = d.base;
+            hi = d.base + d.N - 1;
+            rb = rbase[cur];
+        }
+        const int p = g - d.base;
+        const int c = safe_id(idmap, par[g], K0);
+        d.out[p] = c >= 0 ? c - rb : -1;
+        for (int k = 1; k < NL; k++) {
+            const int32_t *gm = gmap + (size_t)(k - 1) * kstride;
+            d.out[(size_t)k * d.N + p] = c >= 0 ? gm[c] - gm[rb] : -1;
+        }
+    }
+}
+
+// Per-image region counts of every level (batched calls).
+static __global__ void __launch_bounds__(NTHR) k_counts_batch(const Batch b, const int32_t *__restrict__ gmap,
+                                                              size_t kstride, int NL, const int32_t *__restrict__ rbase)
+{
+    for (int i = blockIdx.x * NTHR + threadIdx.x; i < b.n; i += gridDim.x * NTHR) {
+        const ImgDesc d = img_desc(b, i);
+        if (!d.counts) continue;
+        const int first = rbase[i], last = rbase[i + 1] - 1;
+        d.counts[0] = last - first + 1;
+        for (int k = 1; k < NL; k++) {
+            const int32_t *gm = gmap + (size_t)(k - 1) * kstride;
+            d.counts[k] = last >= first ? gm[last] - gm[first] + 1 : 0;
+        }
+    }
+}
+
 // Step II distances as ws_plateau_distance reports them: 0 for state-0
 // pixels, the distance for reached plateau pixels, -1 otherwise.
 static __global__ void __launch_bounds__(NTHR) k_dist_out2(Geo geo, TileGeo tg, const int32_t *__restrict__ par,
@@ -849,16 +1006,6 @@ static __global__ void __launch_bounds__(NTHR) k_dist_out2(Geo geo, TileGeo tg, 
 // ---------------------------------------------------------------------------
 // k_write: one pass writing the canonical level-0 id and every waterfall level
 // ---------------------------------------------------------------------------
-
-// Canonical id of a root; ids outside [0, K0) can only come from an earlier
-// device error and are written as -1 instead of being used as an index.
-__device__ __forceinline__ int safe_id(const int32_t *__restrict__ idmap, int r, int K0)
-{
-    const int c = idmap[r];
-    return (unsigned)c < (unsigned)K0 ? c : -1;
-}
-
-__device__ __forceinline__ int level_id(const int32_t *__restrict__ gm, int c) { return c >= 0 ? gm[c] : -1; }
 
 static __global__ void __launch_bounds__(NTHR) k_write_vec(int N, const int32_t *__restrict__ par,
                                                            const int32_t *__restrict__ idmap,
