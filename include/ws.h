@@ -217,7 +217,7 @@ typedef struct {
  * over all of them, so small images do not leave the GPU idle.  Every image's
  * result is exactly what ws_segment returns for it alone.
  *   items         n descriptors (host memory, read during the call)
- *   dtype, connectivity, NL   shared by all images
+ *   dtype, connectivity, NL   shared by all images; NL <= 64
  * The images' pixels must total below 2^31.
  */
 ws_status ws_segment_batch(ws_context *ctx, int n, const ws_item *items, ws_dtype dtype, int connectivity, int NL,

@@ -292,6 +292,7 @@ ws_status ws_context_create(ws_context **out, int device, size_t budget)
     if (st == WS_OK) st = dalloc(c, &c->w.bsum, 4096 * 4);
     if (st == WS_OK) st = dalloc(c, &c->w.kcount, 4);
     if (st == WS_OK) st = dalloc(c, &c->w.counters, 16);
+    if (st == WS_OK) st = dalloc(c, &c->w.lcount, kMaxLevels * 4);
     if (st == WS_OK) {
         e = cudaMemset(c->status, 0, sizeof(DevStatus));
         if (e == cudaSuccess) e = cudaMemset(c->w.ecount, 0, 4);
@@ -315,7 +316,7 @@ void ws_context_destroy(ws_context *c)
     void *ptrs[] = {w.par,   w.aux,    w.dist,   w.plat,   w.act,    w.tlist,  w.roots,  w.rootm,
                     w.counters, w.bitmap, w.gcnt, w.csum,   w.keys,   w.vals,   w.slots,  w.ecount,
                     w.gmap,  w.newmin, w.uf,     w.rank,   w.bsum,   w.kcount, w.grad_stage, w.levels_stage,
-                    w.counts_stage, w.descs, w.rbase};
+                    w.counts_stage, w.descs, w.rbase, w.lcount};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &r : c->prof.pending) {
@@ -540,7 +541,7 @@ static ws_status prep_batch(ws_context *c, int n, const ws_item *items, ws_dtype
     if (!c) return WS_ERR_INVALID;
     c->err.clear();
     if (n < 1 || !items) return set_error(c, WS_ERR_INVALID, "empty batch");
-    if (NL < 1) return set_error(c, WS_ERR_INVALID, "NL must be >= 1");
+    if (NL < 1 || NL > kMaxLevels) return set_error(c, WS_ERR_INVALID, "NL must be in 1..64 for a batch");
     geos.resize((size_t)n);
     for (int i = 0; i < n; i++) {
         ws_status st = make_geo(c, &items[i].shape, &geos[i]);

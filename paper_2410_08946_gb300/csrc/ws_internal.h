@@ -59,6 +59,7 @@ struct Workspace {
     int32_t *rank = nullptr;        // [kmax]
     int32_t *bsum = nullptr;        // per-block sums for device-wide scans [4096]
     int32_t *kcount = nullptr;      // K0 of the last watershed [1]
+    int32_t *lcount = nullptr;      // region count per level of the last batch [kMaxLevels]
     // host-copy staging for ws_segment_host
     size_t host_n = 0, grad_n = 0;
     uint8_t *grad_stage = nullptr;  // device copy of a host gradient
@@ -121,6 +122,9 @@ struct PhaseScope {
     PhaseScope(ws_context *c_, int ph_, cudaStream_t s_);
     ~PhaseScope();
 };
+
+// Largest NL of a batched call (per-level totals are kept in a fixed array).
+constexpr int kMaxLevels = 64;
 
 // Bytes reserved per image descriptor of a batch (>= sizeof(ImgDesc)).
 constexpr size_t kDescBytes = 128;

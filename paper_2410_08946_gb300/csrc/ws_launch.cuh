@@ -363,12 +363,13 @@ template <typename T, int CONN> static ws_status run_segment_batch(ws_context *c
     b.ntiles = (int)ntiles;
     b.npix = (int)npix;
     if ((st = run_core<T, CONN>(c, b, NL > 1, s)) != WS_OK) return st;
-    if (NL > 1 && (st = run_levels(c, NL, w.aux, w.counters + CNT_ROOTS, nullptr, s)) != WS_OK) return st;
+    // w.lcount[k] = region count of level k over the whole batch
+    if (NL > 1 && (st = run_levels(c, NL, w.aux, w.counters + CNT_ROOTS, w.lcount, s)) != WS_OK) return st;
     {
         PhaseScope ps(c, PH_LEVEL_WRITE, s);
         k_write_batch<<<pixel_grid(c, b.npix), NTHR, 0, s>>>(b, w.par, w.aux, w.gmap, w.kmax, NL, w.rbase,
                                                              w.counters + CNT_ROOTS);
-        k_counts_batch<<<(n + NTHR - 1) / NTHR, NTHR, 0, s>>>(b, w.gmap, w.kmax, NL, w.rbase);
+        k_counts_batch<<<(n + NTHR - 1) / NTHR, NTHR, 0, s>>>(b, w.gmap, w.kmax, NL, w.rbase, w.lcount);
         c->launches += 2;
     }
     if (NL > 1) return run_cleanup(c, s);

@@ -968,18 +968,22 @@ static __global__ void __launch_bounds__(NTHR) k_write_batch(const Batch b, cons
     }
 }
 
-// Per-image region counts of every level (batched calls).
+// Per-image region counts of every level (batched calls).  Level-k ids are
+// contiguous per image and ordered image by image; image i's smallest level-k
+// id is that of its first basin, so its count is the next image's smallest
+// id (or the level's total, ktot[k]) minus its own.
 static __global__ void __launch_bounds__(NTHR) k_counts_batch(const Batch b, const int32_t *__restrict__ gmap,
-                                                              size_t kstride, int NL, const int32_t *__restrict__ rbase)
+                                                              size_t kstride, int NL, const int32_t *__restrict__ rbase,
+                                                              const int32_t *__restrict__ ktot)
 {
     for (int i = blockIdx.x * NTHR + threadIdx.x; i < b.n; i += gridDim.x * NTHR) {
         const ImgDesc d = img_desc(b, i);
         if (!d.counts) continue;
-        const int first = rbase[i], last = rbase[i + 1] - 1;
-        d.counts[0] = last - first + 1;
+        d.counts[0] = rbase[i + 1] - rbase[i];
         for (int k = 1; k < NL; k++) {
             const int32_t *gm = gmap + (size_t)(k - 1) * kstride;
-            d.counts[k] = last >= first ? gm[last] - gm[first] + 1 : 0;
+            const int next = i + 1 < b.n ? gm[rbase[i + 1]] : ktot[k];
+            d.counts[k] = next - gm[rbase[i]];
         }
     }
 }
