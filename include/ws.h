@@ -240,6 +240,60 @@ ws_status ws_graph_launch(ws_graph *g, ws_stream_t stream);
 void ws_graph_destroy(ws_graph *g);
 
 /* ------------------------------------------------------------------------ */
+/* serving: a request loop with continuous batching                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct ws_server ws_server;
+
+/* One partitioning request (the hierarchy of Alg. 4 for one image). */
+typedef struct {
+    const void *grad;     /* gradient samples [N]: host memory if on_host, else device memory */
+    int32_t on_host;      /* 1: grad and the outputs are host memory (copied by the server) */
+    int32_t connectivity; /* 4 / 8 (2D) or 6 (3D) */
+    ws_dtype dtype;
+    int32_t NL;           /* levels, counting level 0 */
+    ws_shape shape;
+    int32_t *levels;      /* int32 [NL*N] output (host or device, as grad) */
+    int32_t *counts;      /* int32 [NL] output (may be NULL) */
+} ws_request;
+
+/*
+ * Starts a server on `device`: a scheduler thread and n_lanes lanes, each with
+ * its own context, stream and resident staging buffers.  Requests wait in a
+ * queue; whenever a lane is free the scheduler takes the queued requests that
+ * share the oldest one's dtype, connectivity, dimensionality and NL (up to
+ * max_batch of them, within the lane's share of the memory budget) and runs
+ * them as one batch (ws_segment_batch), so requests that arrive while others
+ * are running are admitted as soon as a lane frees up and their work overlaps
+ * on the device.  budget_bytes is split evenly between the lanes: a lane
+ * admits requests while the sum of their estimated device footprints
+ * (workspace, and staging of host buffers) fits its share, and its context's
+ * workspace is capped at that share; 0 = no bound.  Host buffers should be
+ * pinned (page-locked) so that their copies overlap other lanes' work.
+ */
+ws_status ws_server_create(ws_server **out, int device, size_t budget_bytes, int n_lanes, int max_batch);
+
+/* Queues a request (its descriptor is copied; its buffers must stay valid
+ * until ws_poll reports it finished).  Returns WS_ERR_OOM if the request
+ * alone cannot fit a lane's share of the budget. */
+ws_status ws_submit(ws_server *srv, const ws_request *req, uint64_t *ticket);
+
+/* Waits up to timeout_us microseconds (0: do not wait, < 0: no limit) for a
+ * request: WS_OK when its outputs are complete (host outputs included),
+ * WS_ERR_NOT_READY if not yet, WS_ERR_CANCELLED, or the error that failed its
+ * batch.  Once a final status has been returned the ticket is forgotten
+ * (polling it again returns WS_ERR_INVALID). */
+ws_status ws_poll(ws_server *srv, uint64_t ticket, int64_t timeout_us);
+
+/* Cancels a request that is still queued (WS_OK); one already running
+ * finishes normally (WS_ERR_NOT_READY is returned). */
+ws_status ws_cancel(ws_server *srv, uint64_t ticket);
+
+/* Stops the scheduler: queued requests are cancelled, running batches finish,
+ * then every resource is released. */
+void ws_server_destroy(ws_server *srv);
+
+/* ------------------------------------------------------------------------ */
 /* step-level entry points (for parity checks of individual steps)           */
 /* ------------------------------------------------------------------------ */
 

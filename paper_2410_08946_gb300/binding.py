@@ -38,6 +38,12 @@ class ws_item(ctypes.Structure):
                 ("counts_d", ctypes.c_void_p)]
 
 
+class ws_request(ctypes.Structure):
+    _fields_ = [("grad", ctypes.c_void_p), ("on_host", ctypes.c_int32), ("connectivity", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("NL", ctypes.c_int32), ("shape", ws_shape),
+                ("levels", ctypes.c_void_p), ("counts", ctypes.c_void_p)]
+
+
 class ws_tuning(ctypes.Structure):
     _fields_ = [("plateau_round_cap", ctypes.c_int32), ("jump_round_cap", ctypes.c_int32),
                 ("jumps_per_round", ctypes.c_int32), ("barrier_timeout_ms", ctypes.c_int32),
@@ -89,6 +95,11 @@ def load(path: str = LIB_PATH):
             "ws_graph_create": ([P, I, ctypes.POINTER(ws_item), I, I, I, P, ctypes.POINTER(P)], I),
             "ws_graph_launch": ([P, P], I),
             "ws_graph_destroy": ([P], None),
+            "ws_server_create": ([ctypes.POINTER(P), I, S, I, I], I),
+            "ws_submit": ([P, ctypes.POINTER(ws_request), ctypes.POINTER(ctypes.c_uint64)], I),
+            "ws_poll": ([P, ctypes.c_uint64, ctypes.c_int64], I),
+            "ws_cancel": ([P, ctypes.c_uint64], I),
+            "ws_server_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -316,6 +327,74 @@ class BatchGraph:
         if self.handle:
             self.ctx.lib.ws_graph_destroy(self.handle)
             self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A libws request loop (ws_server_*): continuous batching over lanes."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, lanes: int = 4, max_batch: int = 64):
+        self.lib = load()
+        self.handle = ctypes.c_void_p()
+        st = self.lib.ws_server_create(ctypes.byref(self.handle), int(device), int(budget_bytes), int(lanes),
+                                       int(max_batch))
+        if st != WS_OK:
+            raise WsError(st, "ws_server_create failed")
+        self._keep = {}
+
+    def submit(self, grad, conn: int, NL: int, levels=None, counts=None) -> int:
+        """Queues one image (CPU tensor: host request, CUDA tensor: device request).
+        Returns the ticket; outputs are kept alive until the ticket is polled."""
+        import torch
+        on_host = not grad.is_cuda
+        if levels is None:
+            levels = torch.empty((NL,) + tuple(grad.shape), dtype=torch.int32, device=grad.device,
+                                 pin_memory=on_host)
+        if counts is None:
+            counts = torch.empty(NL, dtype=torch.int32, device=grad.device, pin_memory=on_host)
+        r = ws_request()
+        r.grad = ctypes.c_void_p(grad.data_ptr())
+        r.on_host = 1 if on_host else 0
+        r.connectivity = int(conn)
+        r.dtype = _dtype_code(grad)
+        r.NL = int(NL)
+        r.shape = _shape_of(grad.shape)
+        r.levels = ctypes.c_void_p(levels.data_ptr())
+        r.counts = ctypes.c_void_p(counts.data_ptr())
+        t = ctypes.c_uint64()
+        st = self.lib.ws_submit(self.handle, ctypes.byref(r), ctypes.byref(t))
+        if st != WS_OK:
+            raise WsError(st, "ws_submit failed")
+        self._keep[t.value] = (grad, levels, counts)
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = -1):
+        """Returns (status, levels, counts); outputs are meaningful when status == WS_OK."""
+        st = self.lib.ws_poll(self.handle, ctypes.c_uint64(ticket), int(timeout_us))
+        if st == WS_ERR_NOT_READY:
+            return st, None, None
+        _, levels, counts = self._keep.pop(ticket, (None, None, None))
+        return st, levels, counts
+
+    def cancel(self, ticket: int) -> int:
+        return self.lib.ws_cancel(self.handle, ctypes.c_uint64(ticket))
+
+    def close(self):
+        if self.handle:
+            self.lib.ws_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
     def __del__(self):
         try:
