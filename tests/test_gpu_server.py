@@ -64,7 +64,7 @@ def test_server_mix_matches_alone(ctx, pool, on_host):
             t = t.pin_memory() if on_host else t.cuda()
             tickets.append(srv.submit(t, conn, NL))
         for (arr, conn, NL), tk in zip(reqs, tickets):
-            st, lv, cnt = srv.poll(tk)
+            st, lv, cnt = srv.poll(tk, 120_000_000)
             assert st == binding.WS_OK
             ref_l, ref_c = _reference(ctx, arr, conn, NL)
             assert torch.equal(lv.cpu(), ref_l)
@@ -76,7 +76,7 @@ def test_server_against_oracle(ctx, pool):
     arr = np.ascontiguousarray(pool[0][:200, :300])
     with binding.Server(0, lanes=2) as srv:
         tk = srv.submit(torch.from_numpy(arr).pin_memory(), 8, 5)
-        st, lv, cnt = srv.poll(tk)
+        st, lv, cnt = srv.poll(tk, 120_000_000)
     assert st == binding.WS_OK
     levels, counts = oracle.segment(arr, 8, 5)
     assert np.array_equal(lv.numpy(), levels) and cnt.tolist() == counts.tolist()
@@ -89,7 +89,7 @@ def test_server_cancel_and_budget(ctx, pool):
         tickets = [srv.submit(torch.from_numpy(a).pin_memory(), c, nl) for a, c, nl in reqs]
         cancelled = [tk for tk in tickets[20:] if srv.cancel(tk) == binding.WS_OK]
         for (arr, conn, NL), tk in zip(reqs, tickets):
-            st, lv, cnt = srv.poll(tk)
+            st, lv, cnt = srv.poll(tk, 120_000_000)
             if tk in cancelled:
                 assert st in (binding.WS_ERR_CANCELLED, binding.WS_OK)
             else:
