@@ -188,6 +188,151 @@ def run_reference(args):
     return 0
 
 
+def _pool_2d(seed):
+    """4096^2 uint8 blob gradient (32 blobs per 256^2, the small-image density):
+    the images of the batch and of the request stream are crops of it."""
+    import oracle  # noqa: F401  (the gradient of the pool is computed on the GPU below)
+    from paper_2410_08946_gb300 import synth
+    return synth.blob_image(4096, 4096, 8192, seed)
+
+
+def run_batch(ctx, binding, torch, n=512, NL=6, conn=4, reps=3):
+    """Config 3: n 2D uint8 images, sides log-uniform in [64, 2048], as one
+    CUDA-graph replay of the batched pipeline vs n per-image ws_segment calls."""
+    from paper_2410_08946_gb300 import synth
+    img = torch.from_numpy(_pool_2d(SEED + 1)).cuda()
+    pool = ctx.gradient(img)
+    shapes = synth.batch_shapes(n, 64, 2048, seed=SEED + 3)
+    offs = synth.integers(SEED + 3, 41, 2 * n, 0, 4096 - 2048)
+    grads = [pool[int(offs[2 * i]):int(offs[2 * i]) + h, int(offs[2 * i + 1]):int(offs[2 * i + 1]) + w].contiguous()
+             for i, (h, w) in enumerate(shapes)]
+    npx = sum(g.numel() for g in grads)
+    graph = ctx.graph(grads, conn, NL)
+    ctx.check()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        graph.launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        graph.launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = e0.elapsed_time(e1) / reps
+    outs = [(torch.empty((NL,) + tuple(g.shape), dtype=torch.int32, device="cuda"),
+             torch.empty(NL, dtype=torch.int32, device="cuda")) for g in grads]
+    for g, (lv, c) in zip(grads, outs):
+        ctx.segment(g, conn, NL, lv, c)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        for g, (lv, c) in zip(grads, outs):
+            ctx.segment(g, conn, NL, lv, c)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_single = e0.elapsed_time(e1) / reps
+    ctx.check()
+    same = all(torch.equal(a, b[0]) for a, b in zip(graph.levels, outs))
+    graph.close()
+    return {"workload": f"{n} 2D uint8 crops of a 4096^2 blob gradient, sides log-uniform [64, 2048], "
+                        f"{npx} px, 4-connectivity, NL={NL}",
+            "batched_graph_ms": ms_graph, "batched_gvox_s": npx / ms_graph / 1e6,
+            "per_image_ms": ms_single, "per_image_gvox_s": npx / ms_single / 1e6,
+            "speedup": ms_single / ms_graph, "identical": bool(same)}
+
+
+def run_serve(ctx, binding, torch, seconds=10.0, rate=200.0, NL=4, budget=40 << 30, lanes=4):
+    """Config 4: Poisson arrivals (rate/s for `seconds`), 80% 2D uint8 (sides
+    log-uniform [256, 4096]) and 20% 3D uint16 (sides [64, 256]), device-resident
+    requests, served by the continuous-batching loop vs one ws_segment per
+    request on one stream.  Latency = arrival -> labels complete on the device."""
+    import numpy as np
+    from paper_2410_08946_gb300 import synth
+    img = torch.from_numpy(_pool_2d(SEED + 4)).cuda()
+    pool2 = ctx.gradient(img)
+    pool3 = torch.from_numpy(synth.distance_volume(256, 256, 256, sample_seeds(256), seed=SEED + 4)).cuda()
+    reqs = synth.request_stream(rate, seconds, seed=SEED + 4)
+    inputs = []
+    for i, r in enumerate(reqs):
+        if r["kind"] == "2d":
+            h, w = r["shape"]
+            y, x = (i * 7919) % (4097 - h), (i * 104729) % (4097 - w)
+            inputs.append((pool2[y:y + h, x:x + w].contiguous(), 4))
+        else:
+            d, h, w = r["shape"]
+            inputs.append((pool3[:d, :h, :w].contiguous(), 6))
+    npx = sum(g.numel() for g, _ in inputs)
+    times = [r["t"] for r in reqs]
+
+    def pct(v, q):
+        return float(np.percentile(np.array(v) * 1e3, q))
+
+    # served: submit at arrival times, poll completions
+    srv = binding.Server(0, budget_bytes=budget, lanes=lanes, max_batch=64)
+    for g, conn in inputs[:8]:                     # warm the lanes' workspaces
+        srv.poll(srv.submit(g, conn, NL), 120_000_000)
+    torch.cuda.synchronize()
+    lat, pending = [], []
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(inputs) or pending:
+        now = time.perf_counter() - t0
+        while i < len(inputs) and times[i] <= now:
+            pending.append((srv.submit(inputs[i][0], inputs[i][1], NL), times[i]))
+            i += 1
+        still = []
+        for tk, ta in pending:
+            st, lv, c = srv.poll(tk, 0)
+            if st == binding.WS_ERR_NOT_READY:
+                still.append((tk, ta))
+            else:
+                lat.append(time.perf_counter() - t0 - ta)
+        pending = still
+        if i < len(inputs) and not pending:
+            time.sleep(max(0.0, min(0.001, times[i] - (time.perf_counter() - t0))))
+    wall_served = time.perf_counter() - t0
+    # saturation: the first n_sat requests queued at once
+    n_sat = min(len(inputs), 400)
+    sat_px = sum(g.numel() for g, _ in inputs[:n_sat])
+    t1 = time.perf_counter()
+    tks = [srv.submit(g, conn, NL) for g, conn in inputs[:n_sat]]
+    for tk in tks:
+        srv.poll(tk, 600_000_000)
+    sat_served = time.perf_counter() - t1
+    srv.close()
+    # per-image: one ws_segment per request, in arrival order, one stream
+    lat1 = []
+    buf = torch.empty(NL * max(g.numel() for g, _ in inputs), dtype=torch.int32, device="cuda")
+    cnt = torch.empty(NL, dtype=torch.int32, device="cuda")
+
+    def single(g, conn):
+        ctx.segment(g, conn, NL, buf[:NL * g.numel()].view((NL,) + tuple(g.shape)), cnt)
+
+    t0 = time.perf_counter()
+    for (g, conn), ta in zip(inputs, times):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        single(g, conn)
+        torch.cuda.current_stream().synchronize()
+        lat1.append(time.perf_counter() - t0 - ta)
+    t1 = time.perf_counter()
+    for g, conn in inputs[:n_sat]:
+        single(g, conn)
+    torch.cuda.synchronize()
+    sat_single = time.perf_counter() - t1
+    ctx.check()
+    return {"workload": f"Poisson {rate:g} req/s for {seconds:g} s ({len(inputs)} requests, {npx} px): 80% 2D uint8 "
+                        f"256..4096, 20% 3D uint16 64..256, NL={NL}, device-resident, budget {budget >> 30} GB, "
+                        f"{lanes} lanes",
+            "served_p50_ms": pct(lat, 50), "served_p99_ms": pct(lat, 99),
+            "per_image_p50_ms": pct(lat1, 50), "per_image_p99_ms": pct(lat1, 99),
+            "served_gvox_s_saturated": sat_px / sat_served / 1e9,
+            "per_image_gvox_s_saturated": sat_px / sat_single / 1e9, "saturation_requests": n_sat,
+            "offered_gvox_s": npx / seconds / 1e9, "served_wall_s": wall_served}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -199,6 +344,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-image batch measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -315,6 +463,12 @@ def main():
         line["e2e"] = {"value": N * world / e2e_s / 1e9, "unit": "Gvox/s", "ms_per_step": e2e_s * 1e3,
                        "h2d_bytes_per_step": int(N * 2), "d2h_bytes_per_step": int(NL * N * 4 + NL * 4)}
         del grad_h, levels_h
+    if world == 1 and not args.no_batch:
+        del levels_d
+        torch.cuda.empty_cache()
+        line["batch"] = run_batch(ctx, binding, torch)
+    if world == 1 and not args.no_serve:
+        line["serve"] = run_serve(ctx, binding, torch, seconds=args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
