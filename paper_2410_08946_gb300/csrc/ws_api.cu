@@ -68,44 +68,82 @@ template <typename P> static void dfree(ws_context *c, P **p, size_t bytes)
     }
 }
 
+// Capacity to allocate when a workspace array must grow from `have` to at
+// least `need`: 1.5x the old capacity (so that a stream of growing requests
+// reallocates rarely; cudaFree synchronises the device), or exactly `need`.
+static size_t grown(size_t need, size_t have, bool exact)
+{
+    if (exact || have == 0) return need;
+    const size_t g = have + have / 2;
+    return g > need ? g : need;
+}
+
+static ws_status alloc_pixels(ws_context *c, size_t N)
+{
+    Workspace &w = c->w;
+    ws_status st;
+    // sizes first, so that free_pixels releases exactly what a partial failure allocated
+    w.N = N;
+    w.rmax = N / 2 + 2;
+    w.nwords = (N + 31) / 32;
+    w.ngroups = (w.nwords + 31) / 32;
+    w.nchunks = (w.ngroups + 2047) / 2048;
+    if ((st = dalloc(c, &w.par, N * 4)) || (st = dalloc(c, &w.aux, N * 4)) || (st = dalloc(c, &w.dist, N * 4)) ||
+        (st = dalloc(c, &w.roots, w.rmax * 4)) || (st = dalloc(c, &w.rootm, w.rmax * 4)) ||
+        (st = dalloc(c, &w.bitmap, w.nwords * 4)) || (st = dalloc(c, &w.gcnt, (w.ngroups + 1) * 4)) ||
+        (st = dalloc(c, &w.csum, (w.nchunks + 1) * 4)))
+        return st;
+    cudaError_t e = cudaMemset(w.bitmap, 0, w.nwords * 4);
+    if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
+    return WS_OK;
+}
+
+static void free_pixels(ws_context *c)
+{
+    Workspace &w = c->w;
+    dfree(c, &w.par, w.N * 4);
+    dfree(c, &w.aux, w.N * 4);
+    dfree(c, &w.dist, w.N * 4);
+    dfree(c, &w.roots, w.rmax * 4);
+    dfree(c, &w.rootm, w.rmax * 4);
+    dfree(c, &w.bitmap, w.nwords * 4);
+    dfree(c, &w.gcnt, (w.ngroups + 1) * 4);
+    dfree(c, &w.csum, (w.nchunks + 1) * 4);
+    w.N = w.rmax = w.nwords = w.ngroups = w.nchunks = 0;
+}
+
 ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles)
 {
     Workspace &w = c->w;
     ws_status st = WS_OK;
     if (N > w.N) {
-        dfree(c, &w.par, w.N * 4);
-        dfree(c, &w.aux, w.N * 4);
-        dfree(c, &w.dist, w.N * 4);
-        dfree(c, &w.roots, w.rmax * 4);
-        dfree(c, &w.rootm, w.rmax * 4);
-        dfree(c, &w.bitmap, w.nwords * 4);
-        dfree(c, &w.gcnt, (w.ngroups + 1) * 4);
-        dfree(c, &w.csum, (w.nchunks + 1) * 4);
-        w.N = 0;
-        const size_t rmax = N / 2 + 2, nwords = (N + 31) / 32, ngroups = (nwords + 31) / 32;
-        const size_t nchunks = (ngroups + 2047) / 2048;
-        if ((st = dalloc(c, &w.par, N * 4)) || (st = dalloc(c, &w.aux, N * 4)) || (st = dalloc(c, &w.dist, N * 4)) ||
-            (st = dalloc(c, &w.roots, rmax * 4)) || (st = dalloc(c, &w.rootm, rmax * 4)) ||
-            (st = dalloc(c, &w.bitmap, nwords * 4)) || (st = dalloc(c, &w.gcnt, (ngroups + 1) * 4)) ||
-            (st = dalloc(c, &w.csum, (nchunks + 1) * 4)))
-            return st;
-        cudaError_t e = cudaMemset(w.bitmap, 0, nwords * 4);
-        if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
-        w.rmax = rmax;
-        w.nwords = nwords;
-        w.ngroups = ngroups;
-        w.nchunks = nchunks;
-        w.N = N;
+        const size_t have = w.N;
+        free_pixels(c);
+        if ((st = alloc_pixels(c, grown(N, have, false))) != WS_OK) {
+            free_pixels(c);
+            if ((st = alloc_pixels(c, N)) != WS_OK) return st;
+        }
     }
     if (ntiles > w.ntiles) {
+        const size_t have = w.ntiles;
+        for (int exact = 0; exact < 2; exact++) {
+            dfree(c, &w.plat, w.ntiles);
+            dfree(c, &w.act, w.ntiles * 2);
+            dfree(c, &w.tlist, w.ntiles * 4);
+            w.ntiles = 0;
+            const size_t n = grown(ntiles, have, exact);
+            if ((st = dalloc(c, &w.plat, n)) || (st = dalloc(c, &w.act, n * 2)) || (st = dalloc(c, &w.tlist, n * 4))) {
+                w.ntiles = n;  // so that the frees above release what was allocated
+                continue;
+            }
+            w.ntiles = n;
+            return WS_OK;
+        }
         dfree(c, &w.plat, w.ntiles);
         dfree(c, &w.act, w.ntiles * 2);
         dfree(c, &w.tlist, w.ntiles * 4);
         w.ntiles = 0;
-        if ((st = dalloc(c, &w.plat, ntiles)) || (st = dalloc(c, &w.act, ntiles * 2)) ||
-            (st = dalloc(c, &w.tlist, ntiles * 4)))
-            return st;
-        w.ntiles = ntiles;
+        return st;
     }
     return WS_OK;
 }
@@ -118,10 +156,13 @@ ws_status ensure_edges(ws_context *c, size_t cap)
     dfree(c, &w.keys, w.edge_cap * 8);
     dfree(c, &w.vals, w.edge_cap * 4);
     dfree(c, &w.slots, w.edge_cap * 4);
+    dfree(c, (uint8_t **)&w.ea, w.edge_cap * 12);
+    dfree(c, (uint8_t **)&w.eb, w.edge_cap * 12);
     w.edge_cap = 0;
     ws_status st;
     if ((st = dalloc(c, &w.keys, cap * 8)) || (st = dalloc(c, &w.vals, cap * 4)) ||
-        (st = dalloc(c, &w.slots, cap * 4)))
+        (st = dalloc(c, &w.slots, cap * 4)) || (st = dalloc(c, (uint8_t **)&w.ea, cap * 12)) ||
+        (st = dalloc(c, (uint8_t **)&w.eb, cap * 12)))
         return st;
     cudaError_t e = cudaMemset(w.keys, 0xff, cap * 8);
     if (e == cudaSuccess) e = cudaMemset(w.vals, 0xff, cap * 4);
@@ -293,6 +334,7 @@ ws_status ws_context_create(ws_context **out, int device, size_t budget)
     if (st == WS_OK) st = dalloc(c, &c->w.kcount, 4);
     if (st == WS_OK) st = dalloc(c, &c->w.counters, 16);
     if (st == WS_OK) st = dalloc(c, &c->w.lcount, kMaxLevels * 4);
+    if (st == WS_OK) st = dalloc(c, &c->w.ecnt, kMaxLevels * 4);
     if (st == WS_OK) {
         e = cudaMemset(c->status, 0, sizeof(DevStatus));
         if (e == cudaSuccess) e = cudaMemset(c->w.ecount, 0, 4);
@@ -316,7 +358,7 @@ void ws_context_destroy(ws_context *c)
     void *ptrs[] = {w.par,   w.aux,    w.dist,   w.plat,   w.act,    w.tlist,  w.roots,  w.rootm,
                     w.counters, w.bitmap, w.gcnt, w.csum,   w.keys,   w.vals,   w.slots,  w.ecount,
                     w.gmap,  w.newmin, w.uf,     w.rank,   w.bsum,   w.kcount, w.grad_stage, w.levels_stage,
-                    w.counts_stage, w.descs, w.rbase, w.lcount};
+                    w.counts_stage, w.descs, w.rbase, w.lcount, w.ea, w.eb, w.ecnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &r : c->prof.pending) {

@@ -50,6 +50,8 @@ struct Workspace {
     uint32_t *vals = nullptr;       // pass value (min height), empty = ~0
     int32_t *slots = nullptr;       // used slots, in insertion order [edge_cap]
     int32_t *ecount = nullptr;      // number of used slots             [1]
+    void *ea = nullptr, *eb = nullptr;  // region-graph edge lists (a, b, pass), 12 B each [edge_cap]
+    int32_t *ecnt = nullptr;        // edges of each level             [kMaxLevels]
     // region graph arrays (level-0 region count K0 <= kmax)
     size_t kmax = 0;
     int levels_cap = 0;             // NL-1 the gmap array can hold

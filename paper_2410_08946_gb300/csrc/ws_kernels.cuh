@@ -29,7 +29,7 @@
 //                    (newmin, Union over kept edges, canonical ids);
 //                    cooperative launch
 //   k_level_write    levels[k][p] = map_k[L0[p]] for all k in one pass
-//   k_hash_clear     returns the used table slots to empty
+//   k_edges_compact  region table -> dense edge list (and the table emptied)
 #pragma once
 
 #include <cooperative_groups.h>
@@ -362,20 +362,88 @@ static __device__ __forceinline__ int block_sum(int v, int *red)
     return s;
 }
 
-static __global__ void __launch_bounds__(NTHR) k_levels(const unsigned long long *__restrict__ keys,
-                                                 const uint32_t *__restrict__ vals,
-                                                 const int32_t *__restrict__ slots, const int32_t *ecount,
-                                                 const int32_t *__restrict__ idmap,
-                                                 const int32_t *k0_ptr, int NL, int32_t *gmap, size_t kstride,
-                                                 uint32_t *newmin, int32_t *uf, int32_t *rank, int32_t *bsum,
-                                                 int32_t *counts, DevStatus *status,
-                                                 unsigned long long timeout_ns)
+// One edge of the region graph: regions a < b and their pass value.
+struct Edge {
+    int a, b;
+    unsigned h;
+};
+
+// Edge lists are rewritten between levels by other CTAs: read them from L2.
+__device__ __forceinline__ Edge ld_edge(const Edge *p)
+{
+    const int *q = reinterpret_cast<const int *>(p);
+    Edge e;
+    e.a = __ldcg(q);
+    e.b = __ldcg(q + 1);
+    e.h = (unsigned)__ldcg(q + 2);
+    return e;
+}
+
+// Region table -> dense edge list in canonical level-0 ids (idmap maps the
+// table's keys, root pixels, to ids; nullptr: keys are ids already).  Every
+// used slot is returned to empty on the way, and the slot count is reset.
+static __global__ void __launch_bounds__(NTHR) k_edges_compact(unsigned long long *keys, uint32_t *vals,
+                                                               const int32_t *__restrict__ slots, int32_t *ecount,
+                                                               const int32_t *__restrict__ idmap,
+                                                               const int32_t *__restrict__ k0_ptr, Edge *edges,
+                                                               int32_t *lcnt, DevStatus *status)
+{
+    const int E = *ecount;
+    const int K0 = *k0_ptr;
+    for (int e = blockIdx.x * NTHR + threadIdx.x; e < E; e += gridDim.x * NTHR) {
+        const int s = slots[e];
+        const unsigned long long key = keys[s];
+        int a = (int)(key >> 32), b = (int)(key & 0xffffffffu);
+        if (idmap) {
+            a = idmap[a];
+            b = idmap[b];
+        }
+        Edge ed;
+        if ((unsigned)a < (unsigned)K0 && (unsigned)b < (unsigned)K0) {
+            ed.a = a < b ? a : b;
+            ed.b = a < b ? b : a;
+            ed.h = vals[s];
+        } else {  // only after an earlier device error: a self-loop is ignored
+            ed.a = ed.b = 0;
+            ed.h = 0;
+        }
+        edges[e] = ed;
+        keys[s] = EMPTY_KEY;
+        vals[s] = 0xffffffffu;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) status->edges = E;
+    (void)lcnt;
+}
+
+static __global__ void k_edges_reset(int32_t *ecount, int32_t *lcnt, int nl)
+{
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        if (threadIdx.x == 0) {
+            lcnt[0] = *ecount;  // edges of level 0
+            *ecount = 0;
+        }
+        for (int k = 1 + threadIdx.x; k < nl; k += 32) lcnt[k] = 0;
+    }
+}
+
+// NL-1 levels of lowest-pass merging on the region graph (cooperative).
+// Level k works on an edge list in level-k ids (ecnt[k] edges, in ebuf[k&1]):
+// newmin(A) = min pass of A's edges; Union across every edge that is the
+// lowest pass of one endpoint; level-(k+1) ids = ranks of the Union roots
+// (the smallest level-k id of each new region, so ids stay ordered by each
+// region's smallest pixel); the edges that stay between two different new
+// regions are relabelled into ebuf[(k+1)&1].  Multi-edges are kept: a
+// region's lowest pass over several parallel edges is their minimum either way.
+static __global__ void __launch_bounds__(NTHR) k_levels(Edge *e0, Edge *e1, int32_t *ecnt,
+                                                        const int32_t *k0_ptr, int NL, int32_t *gmap, size_t kstride,
+                                                        uint32_t *newmin, int32_t *uf, int32_t *rank, int32_t *bsum,
+                                                        int32_t *counts, DevStatus *status,
+                                                        unsigned long long timeout_ns)
 {
     __shared__ int red[NTHR / 32];
     __shared__ int carry;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int gsz = gridDim.x * NTHR;
-    const int E = *ecount;
     const int K0 = *k0_ptr;
     if (K0 < 1 || (size_t)K0 > kstride) {
         if (blockIdx.x == 0 && tid == 0) record_error(status, DEV_BAD_LABELS, 8);
@@ -386,6 +454,9 @@ static __global__ void __launch_bounds__(NTHR) k_levels(const unsigned long long
     for (int k = 0; k + 1 < NL; k++) {
         const int32_t *gm = k == 0 ? nullptr : gmap + (size_t)(k - 1) * kstride;
         int32_t *gout = gmap + (size_t)k * kstride;
+        const Edge *cur = (k & 1) ? e1 : e0;
+        Edge *nxt = (k & 1) ? e0 : e1;
+        const int E = *(volatile int32_t *)(ecnt + k);
         // A: reset
         for (int a = blockIdx.x * NTHR + tid; a < Kk; a += gsz) {
             newmin[a] = 0xffffffffu;
@@ -394,52 +465,32 @@ static __global__ void __launch_bounds__(NTHR) k_levels(const unsigned long long
         if (!grid_barrier(status, timeout_ns)) return;
         // B: newmin(A) = lowest pass of A
         for (int e = blockIdx.x * NTHR + tid; e < E; e += gsz) {
-            int s = slots[e];
-            unsigned long long key = keys[s];
-            int a0 = (int)(key >> 32), b0 = (int)(key & 0xffffffffu);
-            if (idmap) {
-                a0 = idmap[a0];
-                b0 = idmap[b0];
-            }
-            if ((unsigned)a0 >= (unsigned)K0 || (unsigned)b0 >= (unsigned)K0) continue;  // only after a device error
-            unsigned h = vals[s];
-            int A = gm ? __ldcg(gm + a0) : a0, B = gm ? __ldcg(gm + b0) : b0;
-            if (A != B) {
-                atomicMin(newmin + A, h);
-                atomicMin(newmin + B, h);
+            const Edge ed = ld_edge(cur + e);
+            if (ed.a != ed.b) {
+                atomicMin(newmin + ed.a, ed.h);
+                atomicMin(newmin + ed.b, ed.h);
             }
         }
         if (!grid_barrier(status, timeout_ns)) return;
         // C: Union across every edge that is the lowest pass of one endpoint
         for (int e = blockIdx.x * NTHR + tid; e < E; e += gsz) {
-            int s = slots[e];
-            unsigned long long key = keys[s];
-            int a0 = (int)(key >> 32), b0 = (int)(key & 0xffffffffu);
-            if (idmap) {
-                a0 = idmap[a0];
-                b0 = idmap[b0];
-            }
-            if ((unsigned)a0 >= (unsigned)K0 || (unsigned)b0 >= (unsigned)K0) continue;  // only after a device error
-            unsigned h = vals[s];
-            int A = gm ? __ldcg(gm + a0) : a0, B = gm ? __ldcg(gm + b0) : b0;
-            if (A != B && (h == __ldcg(newmin + A) || h == __ldcg(newmin + B))) uf_union(uf, A, B, status);
+            const Edge ed = ld_edge(cur + e);
+            if (ed.a != ed.b && (ed.h == __ldcg(newmin + ed.a) || ed.h == __ldcg(newmin + ed.b)))
+                uf_union(uf, ed.a, ed.b, status);
         }
         if (!grid_barrier(status, timeout_ns)) return;
-        // D: flatten; count roots per contiguous chunk (order-preserving scan)
+        // D: count roots per contiguous chunk (order-preserving scan)
         const int chunk = (Kk + gridDim.x - 1) / gridDim.x;
         const int c0 = blockIdx.x * chunk, c1 = min(Kk, c0 + chunk);
         int cnt = 0;
-        for (int a = c0 + tid; a < c1; a += NTHR) {
-            int r = uf_find(uf, a);
-            cnt += (r == a);
-        }
+        for (int a = c0 + tid; a < c1; a += NTHR) cnt += uf_find(uf, a) == a;
         int tot = block_sum(cnt, red);
         if (tid == 0) bsum[blockIdx.x] = tot;
         if (!grid_barrier(status, timeout_ns)) return;
-        // E: ranks of the roots (roots = smallest level-k id of each new region)
+        // E: ranks of the roots
         int off = 0, all = 0;
         for (int b = tid; b < (int)gridDim.x; b += NTHR) {
-            int v = *(volatile int *)(bsum + b);
+            const int v = *(volatile int *)(bsum + b);
             all += v;
             if (b < (int)blockIdx.x) off += v;
         }
@@ -448,16 +499,16 @@ static __global__ void __launch_bounds__(NTHR) k_levels(const unsigned long long
         if (tid == 0) carry = off;
         __syncthreads();
         for (int a0 = c0; a0 < c1; a0 += NTHR) {
-            int a = a0 + tid;
+            const int a = a0 + tid;
             int isr = 0;
             if (a < c1) isr = uf_find(uf, a) == a;
-            unsigned b = __ballot_sync(0xffffffffu, isr);
+            const unsigned bl = __ballot_sync(0xffffffffu, isr);
             __syncthreads();
-            if (lane == 0) red[wid] = __popc(b);
+            if (lane == 0) red[wid] = __popc(bl);
             __syncthreads();
             int o = carry;
             for (int w = 0; w < wid; w++) o += red[w];
-            if (isr) rank[a] = o + __popc(b & ((1u << lane) - 1u));
+            if (isr) rank[a] = o + __popc(bl & ((1u << lane) - 1u));
             __syncthreads();
             if (tid == 0) {
                 int s = 0;
@@ -468,10 +519,34 @@ static __global__ void __launch_bounds__(NTHR) k_levels(const unsigned long long
         }
         if (blockIdx.x == 0 && tid == 0 && counts) counts[k + 1] = all;
         if (!grid_barrier(status, timeout_ns)) return;
-        // F: compose the level-0 -> level-(k+1) map
+        // F: compose the level-0 -> level-(k+1) map; contract the edge list
         for (int c = blockIdx.x * NTHR + tid; c < K0; c += gsz) {
-            int A = gm ? __ldcg(gm + c) : c;
+            const int A = gm ? __ldcg(gm + c) : c;
             gout[c] = __ldcg(rank + uf_find(uf, A));
+        }
+        if (k + 2 < NL) {
+            for (int e0i = blockIdx.x * NTHR; e0i < E; e0i += gsz) {
+                const int e = e0i + tid;
+                bool keep = false;
+                Edge ne{0, 0, 0};
+                if (e < E) {
+                    const Edge ed = ld_edge(cur + e);
+                    if (ed.a != ed.b) {
+                        const int A = __ldcg(rank + uf_find(uf, ed.a)), B = __ldcg(rank + uf_find(uf, ed.b));
+                        if (A != B) {
+                            keep = true;
+                            ne.a = A < B ? A : B;
+                            ne.b = A < B ? B : A;
+                            ne.h = ed.h;
+                        }
+                    }
+                }
+                const unsigned bl = __ballot_sync(0xffffffffu, keep);
+                int base = 0;
+                if (lane == 0 && bl) base = atomicAdd(ecnt + k + 1, __popc(bl));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (keep) nxt[base + __popc(bl & ((1u << lane) - 1u))] = ne;
+            }
         }
         Kk = all;
         if (!grid_barrier(status, timeout_ns)) return;
@@ -486,25 +561,6 @@ static __global__ void __launch_bounds__(NTHR) k_level_write(int N, const int32_
         int c = L0[p];
         bool ok = c >= 0 && (size_t)c < kstride;
         for (int k = 0; k < nlev; k++) __stcs(out + (size_t)k * N + p, ok ? gmap[(size_t)k * kstride + c] : -1);
-    }
-}
-
-static __global__ void __launch_bounds__(NTHR) k_hash_clear(unsigned long long *keys, uint32_t *vals,
-                                                     const int32_t *slots, int32_t *ecount)
-{
-    const int E = *ecount;
-    for (int e = blockIdx.x * NTHR + threadIdx.x; e < E; e += gridDim.x * NTHR) {
-        int s = slots[e];
-        keys[s] = EMPTY_KEY;
-        vals[s] = 0xffffffffu;
-    }
-}
-
-static __global__ void k_reset_count(int32_t *ecount, DevStatus *status)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        status->edges = *ecount;
-        *ecount = 0;
     }
 }
 

@@ -265,33 +265,30 @@ static inline ws_status run_write(ws_context *c, const Geo &geo, int NL, int32_t
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "write launch");
 }
 
-// Region-graph merging for levels 1..NL-1 over the filled region table;
-// idmap maps table keys to canonical level-0 ids (nullptr: keys are ids).
+// Region-graph merging for levels 1..NL-1 over the filled region table:
+// the table becomes a dense edge list in canonical level-0 ids (idmap maps
+// its keys to ids; nullptr: the keys are ids), the table is emptied for the
+// next call, then the cooperative k_levels contracts the list level by level.
 static inline ws_status run_levels(ws_context *c, int NL, const int32_t *idmap, const int32_t *k0_ptr,
                                    int32_t *counts, cudaStream_t s)
 {
     Workspace &w = c->w;
     cudaError_t e = reset_barrier(c, s);
     if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
+    {
+        PhaseScope ps(c, PH_CLEANUP, s);
+        k_edges_compact<<<c->num_sms * 8, NTHR, 0, s>>>(w.keys, w.vals, w.slots, w.ecount, idmap, k0_ptr,
+                                                        (Edge *)w.ea, w.ecnt, c->status);
+        k_edges_reset<<<1, 32, 0, s>>>(w.ecount, w.ecnt, NL);
+        c->launches += 2;
+    }
     PhaseScope ps(c, PH_LEVELS, s);
     int grid = coop_grid(c, k_levels, NTHR, 0, c->num_sms * 4);
     if (grid > 4096) grid = 4096;
-    e = launch_coop(k_levels, grid, NTHR, 0, s, (const unsigned long long *)w.keys, (const uint32_t *)w.vals,
-                    (const int32_t *)w.slots, (const int32_t *)w.ecount, idmap, k0_ptr, NL, w.gmap, w.kmax,
+    e = launch_coop(k_levels, grid, NTHR, 0, s, (Edge *)w.ea, (Edge *)w.eb, w.ecnt, k0_ptr, NL, w.gmap, w.kmax,
                     w.newmin, w.uf, w.rank, w.bsum, counts, c->status, tune_timeout_ns(c));
     c->launches += 1;
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "levels launch");
-}
-
-static inline ws_status run_cleanup(ws_context *c, cudaStream_t s)
-{
-    Workspace &w = c->w;
-    PhaseScope ps(c, PH_CLEANUP, s);
-    k_hash_clear<<<c->num_sms * 4, NTHR, 0, s>>>(w.keys, w.vals, w.slots, w.ecount);
-    k_reset_count<<<1, 32, 0, s>>>(w.ecount, c->status);
-    c->launches += 2;
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "cleanup launch");
 }
 
 template <typename T, int CONN> static ws_status run_watershed(ws_context *c, const void *grad, const Geo &geo,
@@ -324,9 +321,7 @@ template <typename T, int CONN> static ws_status run_segment(ws_context *c, cons
         k_copy_int<<<1, 32, 0, s>>>(w.counters + CNT_ROOTS, counts);
         c->launches += 1;
     }
-    if ((st = run_write(c, geo, NL, levels, s)) != WS_OK) return st;
-    if (NL > 1) return run_cleanup(c, s);
-    return WS_OK;
+    return run_write(c, geo, NL, levels, s);
 }
 
 // A batch of images (same dtype and connectivity) in one launch per phase:
@@ -372,7 +367,6 @@ template <typename T, int CONN> static ws_status run_segment_batch(ws_context *c
         k_counts_batch<<<(n + NTHR - 1) / NTHR, NTHR, 0, s>>>(b, w.gmap, w.kmax, NL, w.rbase, w.lcount);
         c->launches += 2;
     }
-    if (NL > 1) return run_cleanup(c, s);
     e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "batch launch");
 }
@@ -432,7 +426,8 @@ template <typename T, int CONN> static ws_status run_waterfall(ws_context *c, co
         k_level_write<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo.N, labels0, w.gmap, w.kmax, NL - 1, levels);
         c->launches += 1;
     }
-    return run_cleanup(c, s);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "waterfall launch");
 }
 
 template <int CONN> static void descs_host(int n, const Geo *geos, const ws_item *items, void *out)
