@@ -235,11 +235,17 @@ def run_batch(ctx, binding, torch, n=512, NL=6, conn=4, reps=3):
     ctx.check()
     same = all(torch.equal(a, b[0]) for a, b in zip(graph.levels, outs))
     graph.close()
+    ctx.phase_times()
+    ctx.set_profiling(True)
+    ctx.segment_batch(grads, conn, NL, [o[0] for o in outs], [o[1] for o in outs])
+    ctx.check()
+    phases = {k: round(v[0], 4) for k, v in ctx.phase_times().items() if v[1]}
+    ctx.set_profiling(False)
     return {"workload": f"{n} 2D uint8 crops of a 4096^2 blob gradient, sides log-uniform [64, 2048], "
                         f"{npx} px, 4-connectivity, NL={NL}",
             "batched_graph_ms": ms_graph, "batched_gvox_s": npx / ms_graph / 1e6,
             "per_image_ms": ms_single, "per_image_gvox_s": npx / ms_single / 1e6,
-            "speedup": ms_single / ms_graph, "identical": bool(same)}
+            "speedup": ms_single / ms_graph, "identical": bool(same), "phases_ms_eager": phases}
 
 
 def run_serve(ctx, binding, torch, seconds=10.0, rate=200.0, NL=4, budget=40 << 30, lanes=4):

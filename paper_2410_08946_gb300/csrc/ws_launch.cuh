@@ -181,8 +181,10 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
         if (e != cudaSuccess) return set_cuda_error(c, e, "jump launch");
     }
     if (do_rag) {
+        // distinct adjacent basin pairs: about 3 K0 <= 1.5 N for a fragmented 2D
+        // image; slots for a load factor <= 1/2 (capped at 2^28 slots)
         const int halfn = Nb<CONN>::n / 2;
-        size_t want = (size_t)b.npix * halfn / 8;
+        size_t want = (size_t)b.npix * halfn / 2;
         if (c->tun.edge_capacity > 0) want = (size_t)c->tun.edge_capacity;
         size_t cap = 1 << 16;
         while (cap < want && cap < ((size_t)1 << 28)) cap <<= 1;
