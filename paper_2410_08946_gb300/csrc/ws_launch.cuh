@@ -197,7 +197,18 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
         const bool tma = !b.d && make_tmap_3d(&tmp, w.par, 4, b.one.W, b.one.H, b.one.D, B::RWP, C::BY, C::BZ) &&
                          make_tmap_3d(&tmg, b.one.grad, sizeof(T), b.one.W, b.one.H, b.one.D, B::RWG, C::BY, C::BZ);
         const unsigned long long gmask = w.edge_cap ? w.edge_cap - 1 : 0;
-        if (tma) {
+        if constexpr (CONN == 6) {
+            // k_label6 is the 3D specialisation (same box, same results)
+            using B6 = Label6Box<T>;
+            if (!tma) {
+                memset(&tmp, 0, sizeof tmp);
+                memset(&tmg, 0, sizeof tmg);
+            }
+            auto kern = tma ? k_label6<T, true> : k_label6<T, false>;
+            if ((e = allow_smem(kern, B6::SMEM)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
+            kern<<<b.ntiles, C::NT, B6::SMEM, s>>>(tmp, tmg, b, w.par, w.aux, do_rag ? 1 : 0, w.keys, w.vals, w.slots,
+                                                   w.ecount, gmask, c->status);
+        } else if (tma) {
             if ((e = allow_smem(k_label<T, CONN, true>, B::SMEM)) != cudaSuccess)
                 return set_cuda_error(c, e, "smem attribute");
             k_label<T, CONN, true><<<b.ntiles, C::NT, B::SMEM, s>>>(tmp, tmg, b, w.par, w.aux, do_rag ? 1 : 0, w.keys,

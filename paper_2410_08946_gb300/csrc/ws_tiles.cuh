@@ -713,10 +713,31 @@ template <typename T, int CONN> struct LabelBox {
     static constexpr int RWG = C::TX + 2 * AG;          // grad box: x from x0 - AG
     static constexpr int PBYTES = RWP * C::BY * C::BZ * 4;
     static constexpr int GBYTES = RWG * C::BY * C::BZ * (int)sizeof(T);
-    static constexpr int OFF_P = C::HASH * 12;          // multiple of 128
+    static constexpr int DSLOTS = 4096;                 // distinct path ends per tile (dedupe table)
+    static constexpr int RBYTES = DSLOTS * 8 > C::HASH * 12 ? DSLOTS * 8 : C::HASH * 12;
+    static constexpr int OFF_P = (RBYTES + 127) & ~127; // region R (dedupe, then edge hash) first
     static constexpr int OFF_G = OFF_P + ((PBYTES + 127) & ~127);
     static constexpr int SMEM = OFF_G + ((GBYTES + 127) & ~127);
 };
+
+// Slot of `key` in the CTA's table of distinct path ends (inserted if new);
+// -1 when the table is crowded.
+__device__ __forceinline__ int dedupe_slot(int *dk, int key, int nslots)
+{
+    volatile int *vk = dk;
+    unsigned s = ((unsigned)key * 0x9E3779B1u) >> 20;   // 12 bits: nslots == 4096
+    s &= (unsigned)(nslots - 1);
+    for (int probe = 0; probe < 64; probe++) {
+        const int k = vk[s];
+        if (k == key) return (int)s;
+        if (k == -1) {
+            const int old = atomicCAS(dk + s, -1, key);
+            if (old == -1 || old == key) return (int)s;
+        }
+        s = (s + 1) & (unsigned)(nslots - 1);
+    }
+    return -1;
+}
 
 template <typename T, int CONN, bool TMA>
 __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ CUtensorMap tmp,
@@ -729,8 +750,10 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
     using B = LabelBox<T, CONN>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
-    unsigned long long *hk = (unsigned long long *)smem;
+    unsigned long long *hk = (unsigned long long *)smem;   // edge hash (after the root phase)
     unsigned *hv = (unsigned *)(hk + C::HASH);
+    int *dk = (int *)smem;                                  // distinct path ends (root phase)
+    int *dr = dk + B::DSLOTS;                               // their roots
     int *pb = (int *)(smem + B::OFF_P);
     T *gb = (T *)(smem + B::OFF_G);
     const int tid = threadIdx.x, lane = tid & 31;
@@ -747,62 +770,92 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
             if (do_rag) tma_load_3d(gb, &tmg, x0 - B::AG, y0, z0, &bar);
         }
     }
+    for (int i = tid; i < B::DSLOTS; i += C::NT) dk[i] = -1;
+    // Roots of the tile and of its forward halo.  Many pixels of a tile share
+    // the end of their in-tile path (parallel paths leave the tile through the
+    // same face pixels), so the ends are first deduplicated in shared memory,
+    // each distinct end is chased to its root once (in lock step, LPD chases
+    // in flight per thread), and the pixels take the root of their end.
+    {
+        // box entries: -1 outside the image, -2 - slot for a deduplicated end,
+        // the end itself (>= 0) when the table had no room (chased directly)
+        constexpr int LPB = (C::BS + C::NT - 1) / C::NT;
+        constexpr int LPD = B::DSLOTS / C::NT;
+        __syncthreads();  // the dedupe table is cleared (and the barrier initialised)
+        if (TMA) {
+            const bool ok = mbar_wait(&bar, 0, status);
+            if (__syncthreads_or(!ok)) return;
+        }
+#pragma unroll 4
+        for (int k = 0; k < LPB; k++) {
+            const int i = tid + k * C::NT;
+            if (i >= C::BS) break;
+            const int bx = i % C::BX, by = (i / C::BX) % C::BY, bz = i / (C::BX * C::BY);
+            const int x = x0 - C::BXL + bx, y = y0 + by, z = z0 + bz;
+            const int pos = (bz * C::BY + by) * B::RWP + bx + B::AP - C::BXL;
+            int r = -1;
+            if (x >= 0 && x < geo.W && y < geo.H && z < geo.D) {
+                if (TMA) {
+                    r = pb[pos];
+                } else {
+                    const int q = (z * geo.H + y) * geo.W + x;
+                    r = par[base + q];
+                    if (do_rag) gb[(bz * C::BY + by) * B::RWG + bx + B::AG - C::BXL] = g[q];
+                }
+                const int sl = dedupe_slot(dk, r, B::DSLOTS);
+                if (sl >= 0) r = -2 - sl;
+            }
+            pb[pos] = r;
+        }
+        __syncthreads();
+        // chase the distinct ends to their roots, LPD chases in flight per thread
+        {
+            int e[LPD];
+            unsigned live = 0;
+#pragma unroll
+            for (int m = 0; m < LPD; m++) {
+                e[m] = dk[tid + m * C::NT];
+                live |= (e[m] >= 0 ? 1u : 0u) << m;
+            }
+            for (int hop = 0; live && hop < (1 << 22); hop++) {
+                int u[LPD];
+#pragma unroll
+                for (int m = 0; m < LPD; m++) u[m] = (live >> m) & 1u ? par[e[m]] : e[m];
+#pragma unroll
+                for (int m = 0; m < LPD; m++) {
+                    if (u[m] == e[m]) live &= ~(1u << m);
+                    e[m] = u[m];
+                }
+            }
+            if (live) record_error(status, DEV_NONCONVERGED, 9);
+#pragma unroll
+            for (int m = 0; m < LPD; m++) dr[tid + m * C::NT] = e[m];
+        }
+        __syncthreads();
+        // every box entry takes its root
+#pragma unroll 4
+        for (int k = 0; k < LPB; k++) {
+            const int i = tid + k * C::NT;
+            if (i >= C::BS) break;
+            const int bx = i % C::BX, by = (i / C::BX) % C::BY, bz = i / (C::BX * C::BY);
+            const int pos = (bz * C::BY + by) * B::RWP + bx + B::AP - C::BXL;
+            int r = pb[pos];
+            if (r < -1) {
+                r = dr[-2 - r];
+            } else if (r >= 0) {  // crowded table: chase this end alone
+                int guard = 0;
+                for (int u = par[r]; u != r && guard < (1 << 22); u = par[r], guard++) r = u;
+                if (guard >= (1 << 22)) record_error(status, DEV_NONCONVERGED, 9);
+            }
+            pb[pos] = r;
+        }
+    }
+    __syncthreads();   // the dedupe table is dead: region R becomes the edge hash
     if (do_rag)
         for (int i = tid; i < C::HASH; i += C::NT) {
             hk[i] = EMPTY_KEY;
             hv[i] = 0xffffffffu;
         }
-    // roots of the tile and of its forward halo: all path ends of this thread
-    // are read first, then chased to their roots in lock step, so the thread
-    // keeps LPB independent gathers in flight per hop
-    {
-        constexpr int LPB = (C::BS + C::NT - 1) / C::NT;
-        int r[LPB];
-        if (TMA) {
-            __syncthreads();  // the barrier is initialised before anyone polls it
-            const bool ok = mbar_wait(&bar, 0, status);
-            if (__syncthreads_or(!ok)) return;
-        }
-#pragma unroll
-        for (int k = 0; k < LPB; k++) {
-            const int i = tid + k * C::NT;
-            const int bx = i % C::BX, by = (i / C::BX) % C::BY, bz = i / (C::BX * C::BY);
-            const int x = x0 - C::BXL + bx, y = y0 + by, z = z0 + bz;
-            r[k] = -1;
-            if (i < C::BS && x >= 0 && x < geo.W && y < geo.H && z < geo.D) {
-                if (TMA) {
-                    r[k] = pb[(bz * C::BY + by) * B::RWP + bx + B::AP - C::BXL];
-                } else {
-                    const int q = (z * geo.H + y) * geo.W + x;
-                    r[k] = par[base + q];
-                    if (do_rag) gb[(bz * C::BY + by) * B::RWG + bx + B::AG - C::BXL] = g[q];
-                }
-            }
-        }
-        unsigned live = 0;
-#pragma unroll
-        for (int k = 0; k < LPB; k++) live |= (r[k] >= 0 ? 1u : 0u) << k;
-        for (int hop = 0; live && hop < (1 << 22); hop++) {
-            int u[LPB];
-#pragma unroll
-            for (int k = 0; k < LPB; k++) u[k] = (live >> k) & 1u ? par[r[k]] : r[k];
-#pragma unroll
-            for (int k = 0; k < LPB; k++) {
-                if (u[k] == r[k]) live &= ~(1u << k);
-                r[k] = u[k];
-            }
-        }
-        if (live) record_error(status, DEV_NONCONVERGED, 9);
-        __syncthreads();   // every thread has read its path ends from the box
-#pragma unroll
-        for (int k = 0; k < LPB; k++) {
-            const int i = tid + k * C::NT;
-            if (i < C::BS) {
-                const int bx = i % C::BX, by = (i / C::BX) % C::BY, bz = i / (C::BX * C::BY);
-                pb[(bz * C::BY + by) * B::RWP + bx + B::AP - C::BXL] = r[k];
-            }
-        }
-    }
     __syncthreads();
 #pragma unroll 1
     for (int k = 0; k < C::PER; k++) {
@@ -837,6 +890,268 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
     if (!do_rag) return;
     __syncthreads();
     for (int i = tid; i < C::HASH; i += C::NT)
+        if (hk[i] != EMPTY_KEY) edge_insert(hk[i], hv[i], keys, vals, slots, ecount, gmask, status);
+}
+
+// ---------------------------------------------------------------------------
+// k_label6: k_label for 3D 6-connectivity, one z column of the tile per thread
+// ---------------------------------------------------------------------------
+//
+// Same box and same results as k_label<T, 6>, with the per-pixel work cut
+// down for the dense 3D case:
+//   - thread (lx, ly) walks the column z = 0..TZ-1 of the tile, so box
+//     positions advance by a constant and no per-pixel index is decoded;
+//   - box entries hold the code of their path end (its slot in the tile's
+//     table of distinct ends, which the chase turns into roots);
+//   - the smallest pixel index per basin is taken at the start of every run
+//     of equal codes along the column, into a per-tile table of roots, and
+//     reaches the global array once per root and tile;
+//   - the +x neighbour's root comes from the next lane, the +z neighbour's
+//     from the next step of the column; pass values of a basin pair are
+//     folded into a one-entry register cache while the same pair repeats
+//     (boundary surfaces cross a column as runs of one pair), and only a
+//     change of pair reaches the shared edge hash.
+
+template <typename T> struct Label6Box {
+    using L = LabelBox<T, 6>;
+    static constexpr int DSLOTS = 4096;   // distinct path ends per tile
+    static constexpr int RT = 256;        // distinct roots per tile (smallest-index table)
+    static constexpr int EH = 512;        // shared edge-hash slots
+    static constexpr int OFF_DK = 0;
+    static constexpr int OFF_RK = OFF_DK + DSLOTS * 4;
+    static constexpr int OFF_RM = OFF_RK + RT * 4;
+    static constexpr int OFF_HK = OFF_RM + RT * 4;
+    static constexpr int OFF_HV = OFF_HK + EH * 8;
+    static constexpr int OFF_P = (OFF_HV + EH * 4 + 127) & ~127;
+    static constexpr int OFF_G = OFF_P + ((L::PBYTES + 127) & ~127);
+    static constexpr int SMEM = OFF_G + ((L::GBYTES + 127) & ~127);
+};
+
+// Root of path end e by plain pointer chasing (ends the table had no room for).
+static __device__ __noinline__ int chase_root(const int32_t *par, int e, int npix, DevStatus *status)
+{
+    for (int hop = 0; hop < (1 << 22); hop++) {
+        const int u = par[e];
+        if (u == e) return e;
+        if ((unsigned)u >= (unsigned)npix) break;
+        e = u;
+    }
+    record_error(status, DEV_NONCONVERGED, 9);
+    return -1;
+}
+
+// Smallest pixel index p of root r, into the tile's root table (rk, rm);
+// a crowded table sends p straight to the global array.
+static __device__ __noinline__ void root_min(int *rk, int *rm, int nslots, int r, int p, int32_t *mi)
+{
+    volatile int *vk = rk;
+    unsigned s = ((unsigned)r * 0x9E3779B1u) >> 24;
+    s &= (unsigned)(nslots - 1);
+    for (int probe = 0; probe < 32; probe++) {
+        int k = vk[s];
+        if (k == -1) {
+            k = atomicCAS(rk + s, -1, r);
+            if (k == -1) k = r;
+        }
+        if (k == r) {
+            atomicMin(rm + s, p);
+            return;
+        }
+        s = (s + 1) & (unsigned)(nslots - 1);
+    }
+    atomicMin(mi + r, p);
+}
+
+template <typename T, bool TMA>
+__global__ void __launch_bounds__(TT<6>::NT, 2) k_label6(const __grid_constant__ CUtensorMap tmp,
+                                                         const __grid_constant__ CUtensorMap tmg, const Batch b,
+                                                         int32_t *par, int32_t *mi, int do_rag,
+                                                         unsigned long long *keys, uint32_t *vals, int32_t *slots,
+                                                         int32_t *ecount, unsigned long long gmask, DevStatus *status)
+{
+    using C = TC<6>;
+    using L = LabelBox<T, 6>;
+    using B = Label6Box<T>;
+    static_assert(C::NT == C::TX * C::TY && C::TX == 32, "one column per thread, one row per warp");
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    int *dk = (int *)(smem + B::OFF_DK);   // distinct ends, then their roots
+    int *rk = (int *)(smem + B::OFF_RK);
+    int *rm = (int *)(smem + B::OFF_RM);
+    unsigned long long *hk = (unsigned long long *)(smem + B::OFF_HK);
+    unsigned *hv = (unsigned *)(smem + B::OFF_HV);
+    int *pb = (int *)(smem + B::OFF_P);
+    T *gb = (T *)(smem + B::OFF_G);
+    const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
+    const TileCtx tc = tile_ctx<6>(b, blockIdx.x);   // TMA: a single image (b.one)
+    const Geo &geo = tc.geo;
+    const T *g = (const T *)tc.grad;
+    const int x0 = tc.x0, y0 = tc.y0, z0 = tc.z0, base = tc.base;
+    const int npix = b.npix;
+    constexpr int SZ = C::BY * L::RWP;   // box step of one z
+    constexpr int GZ = C::BY * L::RWG;
+    if (TMA && tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        mbar_arrive_expect_tx(&bar, L::PBYTES + (do_rag ? L::GBYTES : 0));
+        tma_load_3d(pb, &tmp, x0 - L::AP, y0, z0, &bar);
+        if (do_rag) tma_load_3d(gb, &tmg, x0 - L::AG, y0, z0, &bar);
+    }
+    for (int i = tid; i < B::DSLOTS; i += C::NT) dk[i] = -1;
+    if (tid < B::RT) {
+        rk[tid] = -1;
+        rm[tid] = 0x7fffffff;
+    }
+    if (do_rag)
+        for (int i = tid; i < B::EH; i += C::NT) {
+            hk[i] = EMPTY_KEY;
+            hv[i] = 0xffffffffu;
+        }
+    __syncthreads();   // tables cleared (and the barrier initialised)
+    if (TMA) {
+        const bool ok = mbar_wait(&bar, 0, status);
+        if (__syncthreads_or(!ok)) return;
+    }
+
+    // Box entry -> code: -1 outside the image, the end's slot (>= 0), or
+    // -2 - end when the table of ends had no room.
+    const int x = x0 + lane, y = y0 + ly;
+    const bool col_in = x < geo.W && y < geo.H;
+    auto encode = [&](int pos, int gpos, bool in, int q, int &pe, int &pc) {
+        int c = -1;
+        if (in) {
+            int e;
+            if (TMA) {
+                e = pb[pos];
+            } else {
+                e = par[base + q];
+                if (do_rag) gb[gpos] = g[q];
+            }
+            if ((unsigned)e >= (unsigned)npix) {
+                record_error(status, DEV_NONCONVERGED, 11);
+            } else if (e == pe) {
+                c = pc;
+            } else {
+                const int s = dedupe_slot(dk, e, B::DSLOTS);
+                c = s >= 0 ? s : -2 - e;
+                pe = e;
+                pc = c;
+            }
+        }
+        pb[pos] = c;
+    };
+    const int pcol = ly * L::RWP + lane + L::AP;   // box position of (lane, ly, z = 0)
+    const int gcol = ly * L::RWG + lane + L::AG;
+    {
+        int pe = -1, pc = -1;
+#pragma unroll 1
+        for (int k = 0; k <= C::TZ; k++)   // the column and its +z face entry
+            encode(pcol + k * SZ, gcol + k * GZ, col_in && z0 + k < geo.D, ((z0 + k) * geo.H + y) * geo.W + x, pe,
+                   pc);
+        // +y face: (lane, TY, z = ly)
+        pe = -1;
+        encode((ly * C::BY + C::TY) * L::RWP + lane + L::AP, (ly * C::BY + C::TY) * L::RWG + lane + L::AG,
+               x < geo.W && y0 + C::TY < geo.H && z0 + ly < geo.D, ((z0 + ly) * geo.H + y0 + C::TY) * geo.W + x, pe,
+               pc);
+        // +x face: (TX, tid % TY, tid / TY) for the first TY * TZ threads
+        if (tid < C::TY * C::TZ) {
+            const int fy = tid % C::TY, fz = tid / C::TY;
+            pe = -1;
+            encode((fz * C::BY + fy) * L::RWP + C::TX + L::AP, (fz * C::BY + fy) * L::RWG + C::TX + L::AG,
+                   x0 + C::TX < geo.W && y0 + fy < geo.H && z0 + fz < geo.D,
+                   ((z0 + fz) * geo.H + y0 + fy) * geo.W + x0 + C::TX, pe, pc);
+        }
+    }
+    __syncthreads();
+    // chase the distinct ends to their roots, LPD chases in flight per thread
+    {
+        constexpr int LPD = B::DSLOTS / C::NT;
+        int e[LPD];
+        unsigned live = 0;
+#pragma unroll
+        for (int m = 0; m < LPD; m++) {
+            e[m] = dk[tid + m * C::NT];
+            live |= (e[m] >= 0 ? 1u : 0u) << m;
+        }
+        for (int hop = 0; live && hop < (1 << 22); hop++) {
+            int u[LPD];
+#pragma unroll
+            for (int m = 0; m < LPD; m++) u[m] = (live >> m) & 1u ? par[e[m]] : e[m];
+#pragma unroll
+            for (int m = 0; m < LPD; m++) {
+                if (u[m] == e[m]) {
+                    live &= ~(1u << m);
+                } else if ((unsigned)u[m] >= (unsigned)npix) {
+                    live &= ~(1u << m);
+                    e[m] = -1;
+                    record_error(status, DEV_NONCONVERGED, 11);
+                } else {
+                    e[m] = u[m];
+                }
+            }
+        }
+        if (live) record_error(status, DEV_NONCONVERGED, 9);
+#pragma unroll
+        for (int m = 0; m < LPD; m++) dk[tid + m * C::NT] = e[m];
+    }
+    __syncthreads();
+
+    auto root_of = [&](int c) -> int {
+        if (c >= 0) return dk[c];
+        if (c == -1) return -1;
+        return chase_root(par, -2 - c, npix, status);
+    };
+    // the column: roots, smallest indices, pass values of +x, +y, +z pairs
+    unsigned ca = 0xffffffffu, cb = 0u, ch = 0xffffffffu;   // register edge cache
+    int pc = -1;
+    int rz = root_of(pb[pcol]);
+    int p = base + (z0 * geo.H + y) * geo.W + x;
+#pragma unroll 1
+    for (int k = 0; k < C::TZ && z0 + k < geo.D; k++, p += geo.HW) {   // trip count uniform in the CTA
+        const int pos = pcol + k * SZ;
+        const int c = pb[pos];
+        const int r = rz;
+        rz = root_of(pb[pos + SZ]);
+        if (r >= 0) {
+            par[p] = r;
+            if (c != pc) {
+                pc = c;
+                root_min(rk, rm, B::RT, r, p, mi);
+            }
+        }
+        if (!do_rag) continue;
+        int rx = __shfl_down_sync(0xffffffffu, r, 1);
+        if (lane == 31) rx = root_of(pb[pos + 1]);
+        const int ry = root_of(pb[pos + L::RWP]);
+        const bool ex = rx >= 0 && rx != r, ey = ry >= 0 && ry != r, ez = rz >= 0 && rz != r;
+        if (r >= 0 && (ex | ey | ez)) {
+            const int gpos = gcol + k * GZ;
+            const unsigned gp = gb[gpos];
+#pragma unroll
+            for (int n = 0; n < 3; n++) {
+                const bool en = n == 0 ? ex : (n == 1 ? ey : ez);
+                if (!en) continue;
+                const int rn = n == 0 ? rx : (n == 1 ? ry : rz);
+                const unsigned gq = gb[gpos + (n == 0 ? 1 : (n == 1 ? L::RWG : GZ))];
+                const unsigned h = gp > gq ? gp : gq;
+                const unsigned lo = (unsigned)(r < rn ? r : rn), hi = (unsigned)(r < rn ? rn : r);
+                if (lo == ca && hi == cb) {
+                    ch = h < ch ? h : ch;
+                } else {
+                    if (ca != 0xffffffffu)
+                        smem_edge_insert(ca, cb, ch, hk, hv, B::EH, keys, vals, slots, ecount, gmask, status);
+                    ca = lo;
+                    cb = hi;
+                    ch = h;
+                }
+            }
+        }
+    }
+    if (do_rag && ca != 0xffffffffu) smem_edge_insert(ca, cb, ch, hk, hv, B::EH, keys, vals, slots, ecount, gmask, status);
+    __syncthreads();
+    if (tid < B::RT && rk[tid] >= 0) atomicMin(mi + rk[tid], rm[tid]);
+    if (!do_rag) return;
+    for (int i = tid; i < B::EH; i += C::NT)
         if (hk[i] != EMPTY_KEY) edge_insert(hk[i], hv[i], keys, vals, slots, ecount, gmask, status);
 }
 
