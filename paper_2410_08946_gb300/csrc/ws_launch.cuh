@@ -125,7 +125,22 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
         CUtensorMap tm;
         const bool tma = !b.d && make_tmap_3d(&tm, b.one.grad, sizeof(T), b.one.W, b.one.H, b.one.D, B::RW, C::HY,
                                               C::HZ);
-        if (tma) {
+        if constexpr (CONN == 6) {
+            // k_init6 is the 3D specialisation (same results)
+            if (tma) {
+                if ((e = allow_smem(k_init6<T, true>, B::SMEM_TMA)) != cudaSuccess)
+                    return set_cuda_error(c, e, "smem attribute");
+                const int grid = coop_grid(c, k_init6<T, true>, C::NT, B::SMEM_TMA, b.ntiles);
+                k_init6<T, true><<<grid, C::NT, B::SMEM_TMA, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act, w.tlist,
+                                                                  w.roots, w.counters, c->status);
+            } else {
+                memset(&tm, 0, sizeof tm);
+                if ((e = allow_smem(k_init6<T, false>, B::SMEM_PLAIN)) != cudaSuccess)
+                    return set_cuda_error(c, e, "smem attribute");
+                k_init6<T, false><<<b.ntiles, C::NT, B::SMEM_PLAIN, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act,
+                                                                         w.tlist, w.roots, w.counters, c->status);
+            }
+        } else if (tma) {
             if ((e = allow_smem(k_init<T, CONN, true>, B::SMEM_TMA)) != cudaSuccess)
                 return set_cuda_error(c, e, "smem attribute");
             const int grid = coop_grid(c, k_init<T, CONN, true>, C::NT, B::SMEM_TMA, b.ntiles);

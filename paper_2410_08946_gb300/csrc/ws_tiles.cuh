@@ -421,6 +421,225 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
 }
 
 // ---------------------------------------------------------------------------
+// k_init6: k_init for 3D 6-connectivity, one z column of the tile per thread
+// ---------------------------------------------------------------------------
+//
+// Same results as k_init<T, 6>.  The dense 3D case is written without
+// divergent branches in the per-pixel work: step I tracks the lowest
+// neighbour (and its local and global offsets) with selects, the pointer
+// doubling keeps a thread's own entries in registers and moves them with
+// predicated shared-memory loads and stores (every load of a round issued
+// before any store, two hops per round), and the pixel states travel packed
+// two bits per pixel.
+
+// v = c >= 0 ? nx[c] : c, nx at shared address sbase (no branch)
+__device__ __forceinline__ int gather_if(int c, unsigned sbase)
+{
+    int v;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ge.s32 p, %1, 0;\n\tmov.b32 %0, %1;\n\t@p ld.volatile.shared.b32 %0, [%2];\n\t}"
+        : "=r"(v)
+        : "r"(c), "r"(sbase + 4u * (unsigned)c)
+        : "memory");
+    return v;
+}
+
+// if (c >= 0) shared[addr] = v (no branch)
+__device__ __forceinline__ void store_if(int c, unsigned addr, int v)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ge.s32 p, %0, 0;\n\t@p st.volatile.shared.b32 [%1], %2;\n\t}" ::"r"(c),
+                 "r"(addr), "r"(v)
+                 : "memory");
+}
+
+template <typename T, bool TMA>
+__global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ CUtensorMap tm, const Batch b,
+                                                        int32_t *__restrict__ par, int32_t *__restrict__ mi,
+                                                        int32_t *__restrict__ dist, uint8_t *__restrict__ plat,
+                                                        uint8_t *__restrict__ act, int32_t *__restrict__ tlist,
+                                                        int32_t *__restrict__ roots, int32_t *counters,
+                                                        DevStatus *status)
+{
+    using C = TC<6>;
+    using B = InitBox<T, 6>;
+    static_assert(C::NT == C::TX * C::TY && C::TX == 32 && C::PER == C::TZ, "one z column per thread");
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[2];
+    int *nx = (int *)(smem + (TMA ? 2 : 1) * B::STAGE);
+    const unsigned sbase = smem_u32(nx);
+    const int tid = threadIdx.x, lane = tid & 31, lx = lane, ly = tid >> 5;
+    const int G = gridDim.x;
+    constexpr int SZ = C::HY * B::RW;              // box step of one z
+    const int h0 = (ly + 1) * B::RW + lx + B::A;   // box index of (lx, ly, z = -1)
+
+    if (TMA) {  // a single image (b.one); two tiles in flight per CTA
+        if (tid == 0) {
+            mbar_init(&bars[0], 1);
+            mbar_init(&bars[1], 1);
+            mbar_fence_init();
+            const int t0 = blockIdx.x;
+            if (t0 < b.ntiles) init_issue<T, 6, TMA>(&tm, (T *)smem, &bars[0], b, t0);
+            if (t0 + G < b.ntiles) init_issue<T, 6, TMA>(&tm, (T *)(smem + B::STAGE), &bars[1], b, t0 + G);
+        }
+        __syncthreads();
+    }
+
+    int j = 0;
+    for (int t = blockIdx.x; t < b.ntiles; t += G, j++) {
+        const int s = TMA ? (j & 1) : 0;
+        T *gs = (T *)(smem + s * B::STAGE);
+        const TileCtx tc = tile_ctx<6>(b, t);
+        const Geo &geo = tc.geo;
+        const int x0 = tc.x0, y0 = tc.y0, z0 = tc.z0, base = tc.base;
+        if (TMA) {
+            const bool ok = mbar_wait(&bars[s], (unsigned)((j >> 1) & 1), status);
+            if (__syncthreads_or(!ok)) return;
+        } else {
+            const T *g = (const T *)tc.grad;
+            constexpr int LPT = (B::ELEMS + C::NT - 1) / C::NT;
+            constexpr int LB = 6;
+#pragma unroll
+            for (int k0 = 0; k0 < LPT; k0 += LB) {
+                unsigned v[LB];
+#pragma unroll
+                for (int kk = 0; kk < LB; kk++) {
+                    const int i = tid + (k0 + kk) * C::NT;
+                    const int hx = i % B::RW, hy = (i / B::RW) % C::HY, hz = i / (B::RW * C::HY);
+                    const int xx = x0 - B::A + hx, yy = y0 - 1 + hy, zz = z0 - 1 + hz;
+                    v[kk] = 0;
+                    if (k0 + kk < LPT && i < B::ELEMS && xx >= 0 && xx < geo.W && yy >= 0 && yy < geo.H &&
+                        zz >= 0 && zz < geo.D)
+                        v[kk] = __ldg(g + (zz * geo.H + yy) * geo.W + xx);
+                }
+#pragma unroll
+                for (int kk = 0; kk < LB; kk++) {
+                    const int i = tid + (k0 + kk) * C::NT;
+                    if (k0 + kk < LPT && i < B::ELEMS) gs[i] = (T)v[kk];
+                }
+            }
+            __syncthreads();
+        }
+
+        // step I (Eq. 1) on the column: lowest neighbour, ties to the later
+        // one in ascending index order (z-1, y-1, x-1, x+1, y+1, z+1)
+        const int x = x0 + lx, y = y0 + ly;
+        const int W = geo.W, HW = geo.HW;
+        const bool interior = x0 >= 1 && x0 + C::TX < geo.W && y0 >= 1 && y0 + C::TY < geo.H && z0 >= 1 &&
+                              z0 + C::TZ < geo.D;
+        const bool col_in = x < geo.W && y < geo.H;
+        const bool vxm = interior || x > 0, vxp = interior || x + 1 < geo.W;
+        const bool vym = interior || y > 0, vyp = interior || y + 1 < geo.H;
+        int cur[C::TZ];    // this thread's entries of nx
+        unsigned stb = 0;  // their states, two bits each
+        int plateau = 0;
+        {
+            unsigned cz[C::TZ + 2];
+#pragma unroll
+            for (int k = 0; k < C::TZ + 2; k++) cz[k] = gs[h0 + k * SZ];
+            int p = base + (z0 * geo.H + y) * geo.W + x;
+#pragma unroll
+            for (int k = 0; k < C::TZ; k++, p += HW) {
+                const int z = z0 + k;
+                const int h = h0 + (k + 1) * SZ;
+                const unsigned gp = cz[k + 1];
+                unsigned m = 0xffffffffu;
+                int lo = 0, go = 0;
+                bool tin = false, has = false;
+                auto take = [&](bool valid, unsigned v, int l, int gofs, bool ti) {
+                    const bool tk = valid && v <= m;
+                    m = tk ? v : m;
+                    lo = tk ? l : lo;
+                    go = tk ? gofs : go;
+                    tin = tk ? ti : tin;
+                    has = has || tk;
+                };
+                take(interior || z > 0, cz[k], -C::TX * C::TY, -HW, k > 0);
+                take(vym, gs[h - B::RW], -C::TX, -W, ly > 0);
+                take(vxm, gs[h - 1], -1, -1, lx > 0);
+                take(vxp, gs[h + 1], 1, 1, lx < C::TX - 1);
+                take(vyp, gs[h + B::RW], C::TX, W, ly < C::TY - 1);
+                take(interior || z + 1 < geo.D, cz[k + 2], C::TX * C::TY, HW, k < C::TZ - 1);
+                const bool in = col_in && z < geo.D;
+                const bool st0 = has && m < gp, st1 = !has || m > gp;
+                const int code = !in ? STOUT : (st0 ? ST0 : (st1 ? ST1 : STP));
+                const int i = tid + k * C::NT;
+                const int c = !in ? enc_final(0) : (st0 ? (tin ? i + lo : enc_final(p + go)) : enc_final(p));
+                plateau |= code == STP;
+                stb |= (unsigned)code << (2 * k);
+                nx[i] = c;
+            }
+        }
+        __syncthreads();  // the gradient box of stage s is no longer read; nx is complete
+        if (TMA && tid == 0 && t + 2 * G < b.ntiles) init_issue<T, 6, TMA>(&tm, gs, &bars[s], b, t + 2 * G);
+#pragma unroll
+        for (int k = 0; k < C::TZ; k++) cur[k] = nx[tid + k * C::NT];
+
+        // step III inside the tile: pointer doubling, two hops a round.  A
+        // value read while its owner is updating it is the old or the new
+        // pointer of a pixel further down the same path, or the path's end.
+        for (int round = 0; round < 32; round++) {
+            int more = 0;
+#pragma unroll
+            for (int h = 0; h < C::TZ; h += 8) {  // eight entries in flight
+                int nxt[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++) nxt[k] = gather_if(cur[h + k], sbase);
+#pragma unroll
+                for (int k = 0; k < 8; k++) nxt[k] = gather_if(nxt[k], sbase);
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    store_if(cur[h + k], sbase + 4u * (unsigned)(tid + (h + k) * C::NT), nxt[k]);
+                    more |= nxt[k] >= 0;
+                    cur[h + k] = nxt[k];
+                }
+            }
+            if (!__syncthreads_or(more)) break;
+        }
+
+        {
+            int p = base + (z0 * geo.H + y) * geo.W + x;
+#pragma unroll
+            for (int k = 0; k < C::TZ; k++, p += HW) {
+                const unsigned sk = (stb >> (2 * k)) & 3u;
+                if (sk == (unsigned)STOUT) continue;
+                const int e = cur[k];
+                par[p] = e < 0 ? dec_final(e) : p;  // e >= 0 cannot survive 32 rounds
+                if (sk != (unsigned)ST0) mi[p] = 0x7fffffff;
+            }
+        }
+        // list the strict minima (roots known now)
+#pragma unroll
+        for (int k = 0; k < C::TZ; k++) {
+            const bool isr = ((stb >> (2 * k)) & 3u) == (unsigned)ST1;
+            const unsigned bb = __ballot_sync(0xffffffffu, isr);
+            if (!bb) continue;
+            int rb = 0;
+            if (lane == 0) rb = atomicAdd(counters + CNT_ROOTS, __popc(bb));
+            rb = __shfl_sync(0xffffffffu, rb, 0);
+            if (isr) roots[rb + __popc(bb & ((1u << lane) - 1u))] = base + ((z0 + k) * geo.H + y) * geo.W + x;
+        }
+        if (__syncthreads_or(plateau)) {
+            int p = base + (z0 * geo.H + y) * geo.W + x;
+#pragma unroll
+            for (int k = 0; k < C::TZ; k++, p += HW) {
+                const unsigned sk = (stb >> (2 * k)) & 3u;
+                if (sk == (unsigned)STOUT) continue;
+                dist[p] = sk == (unsigned)ST0 ? 0 : (sk == (unsigned)ST1 ? -2 : INF_D);
+            }
+            if (tid == 0) {
+                plat[t] = 1;
+                act[t] = 1;
+                tlist[atomicAdd(counters + CNT_TILES, 1)] = t;
+            }
+        } else if (tid == 0) {
+            plat[t] = 0;
+        }
+        // (the __syncthreads_or above also orders this tile's nx reads before
+        // the next tile's nx writes)
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_plateau2: step II distances on plateau tiles (cooperative)
 // ---------------------------------------------------------------------------
 
