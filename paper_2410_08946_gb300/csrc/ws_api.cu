@@ -229,7 +229,35 @@ PhaseScope::~PhaseScope()
 
 static const char *const PHASE_NAMES[NPHASE] = {"step1",       "plateau", "resolve_union", "jump",
                                                 "compact",     "rag",     "levels",        "level_write",
-                                                "cleanup",     "gradient", "copy"};
+                                                "cleanup",     "gradient", "copy",          "chase"};
+
+ws_status ensure_ends(ws_context *c, size_t N, size_t ntiles)
+{
+    Workspace &w = c->w;
+    ws_status st;
+    if (N > w.ncode) {
+        const size_t have = w.ncode;
+        dfree(c, &w.code, w.ncode * 2);
+        dfree(c, &w.ends, w.ncode * 4);
+        w.ncode = grown(N, have, false);
+        if ((st = dalloc(c, &w.code, w.ncode * 2)) || (st = dalloc(c, &w.ends, w.ncode * 4))) {
+            dfree(c, &w.code, w.ncode * 2);
+            dfree(c, &w.ends, w.ncode * 4);
+            w.ncode = 0;
+            return st;
+        }
+    }
+    if (ntiles > w.ntends) {
+        const size_t have = w.ntends;
+        dfree(c, &w.tends, w.ntends * 8);
+        w.ntends = grown(ntiles, have, false);
+        if ((st = dalloc(c, &w.tends, w.ntends * 8))) {
+            w.ntends = 0;
+            return st;
+        }
+    }
+    return WS_OK;
+}
 
 ws_status ensure_batch(ws_context *c, size_t n)
 {
@@ -358,7 +386,7 @@ void ws_context_destroy(ws_context *c)
     void *ptrs[] = {w.par,   w.aux,    w.dist,   w.plat,   w.act,    w.tlist,  w.roots,  w.rootm,
                     w.counters, w.bitmap, w.gcnt, w.csum,   w.keys,   w.vals,   w.slots,  w.ecount,
                     w.gmap,  w.newmin, w.uf,     w.rank,   w.bsum,   w.kcount, w.grad_stage, w.levels_stage,
-                    w.counts_stage, w.descs, w.rbase, w.lcount, w.ea, w.eb, w.ecnt};
+                    w.counts_stage, w.descs, w.rbase, w.lcount, w.ea, w.eb, w.ecnt, w.code, w.ends, w.tends};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &r : c->prof.pending) {

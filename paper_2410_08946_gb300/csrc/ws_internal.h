@@ -36,7 +36,13 @@ struct Workspace {
     size_t rmax = 0;
     int32_t *roots = nullptr; // list of basin roots                         [rmax]
     int32_t *rootm = nullptr; // smallest pixel index of each listed root    [rmax]
-    int32_t *counters = nullptr;  // plateau tiles, roots, ...               [4]
+    int32_t *counters = nullptr;  // plateau tiles, roots, path ends, ...    [4]
+    // 3D path ends: per pixel the slot of its in-tile path end, per tile the
+    // span of its slots in `ends` (the end pixel, then its root)
+    size_t ncode = 0, ntends = 0;
+    uint16_t *code = nullptr;     // [ncode]
+    int32_t *ends = nullptr;      // [ncode]
+    int2 *tends = nullptr;        // (first slot, slot count) per tile  [ntends]
     size_t nwords = 0, ngroups = 0, nchunks = 0;
     uint32_t *bitmap = nullptr;   // one bit per pixel index (kept zero)     [nwords]
     int32_t *gcnt = nullptr;      // popcount per 32-word group, then prefix [ngroups]
@@ -82,6 +88,7 @@ enum Phase {
     PH_CLEANUP,       // edge table reset
     PH_GRADIENT,      // blur + Sobel
     PH_COPY,          // host <-> device copies of ws_segment_host
+    PH_CHASE,         // roots of the 3D tiles' path ends
     NPHASE
 };
 
@@ -142,6 +149,7 @@ ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles);
 ws_status ensure_edges(ws_context *c, size_t cap);
 ws_status ensure_regions(ws_context *c, size_t kmax, int levels);
 ws_status ensure_batch(ws_context *c, size_t n);
+ws_status ensure_ends(ws_context *c, size_t N, size_t ntiles);
 ws_status set_error_msg(ws_context *c, ws_status st, const char *msg);
 ws_status set_cuda_error(ws_context *c, cudaError_t e, const char *what);
 

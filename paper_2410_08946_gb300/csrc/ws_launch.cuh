@@ -115,6 +115,7 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
     Workspace &w = c->w;
     ws_status st = ensure_pixels(c, b.npix, b.ntiles);
     if (st != WS_OK) return st;
+    if (CONN == 6 && (st = ensure_ends(c, b.npix, b.ntiles)) != WS_OK) return st;
     cudaError_t e = cudaMemsetAsync(w.act, 0, 2 * (size_t)b.ntiles, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 16, s);
     if (e == cudaSuccess) e = reset_barrier(c, s);
@@ -132,13 +133,15 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
                     return set_cuda_error(c, e, "smem attribute");
                 const int grid = coop_grid(c, k_init6<T, true>, C::NT, B::SMEM_TMA, b.ntiles);
                 k_init6<T, true><<<grid, C::NT, B::SMEM_TMA, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act, w.tlist,
-                                                                  w.roots, w.counters, c->status);
+                                                                  w.roots, w.code, w.ends, w.tends, w.counters,
+                                                                  c->status);
             } else {
                 memset(&tm, 0, sizeof tm);
                 if ((e = allow_smem(k_init6<T, false>, B::SMEM_PLAIN)) != cudaSuccess)
                     return set_cuda_error(c, e, "smem attribute");
                 k_init6<T, false><<<b.ntiles, C::NT, B::SMEM_PLAIN, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act,
-                                                                         w.tlist, w.roots, w.counters, c->status);
+                                                                         w.tlist, w.roots, w.code, w.ends, w.tends,
+                                                                         w.counters, c->status);
             }
         } else if (tma) {
             if ((e = allow_smem(k_init<T, CONN, true>, B::SMEM_TMA)) != cudaSuccess)
@@ -205,6 +208,11 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
         while (cap < want && cap < ((size_t)1 << 28)) cap <<= 1;
         if ((st = ensure_edges(c, cap)) != WS_OK) return st;
     }
+    if constexpr (CONN == 6) {  // 3D: roots of the tiles' path ends
+        PhaseScope pc(c, PH_CHASE, s);
+        k_chase<<<c->num_sms * 8, NTHR, 0, s>>>(b, w.ends, w.tends, w.code, w.counters, w.par, c->status);
+        c->launches += 1;
+    }
     {
         PhaseScope ps(c, PH_RAG, s);
         using B = LabelBox<T, CONN>;
@@ -213,16 +221,21 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
                          make_tmap_3d(&tmg, b.one.grad, sizeof(T), b.one.W, b.one.H, b.one.D, B::RWG, C::BY, C::BZ);
         const unsigned long long gmask = w.edge_cap ? w.edge_cap - 1 : 0;
         if constexpr (CONN == 6) {
-            // k_label6 is the 3D specialisation (same box, same results)
-            using B6 = Label6Box<T>;
-            if (!tma) {
-                memset(&tmp, 0, sizeof tmp);
+            // 3D: the per-pixel pass over slot codes (roots known from k_chase)
+            using B6 = Rag6Box<T>;
+            CUtensorMap tmc;
+            const bool tma6 = !b.d &&
+                              make_tmap_3d(&tmc, w.code, 2, b.one.W, b.one.H, b.one.D, B6::CW, B6::BY, B6::BZ) &&
+                              make_tmap_3d(&tmg, b.one.grad, sizeof(T), b.one.W, b.one.H, b.one.D, B6::GW, B6::BY,
+                                           B6::BZ);
+            if (!tma6) {
+                memset(&tmc, 0, sizeof tmc);
                 memset(&tmg, 0, sizeof tmg);
             }
-            auto kern = tma ? k_label6<T, true> : k_label6<T, false>;
+            auto kern = tma6 ? k_rag6<T, true> : k_rag6<T, false>;
             if ((e = allow_smem(kern, B6::SMEM)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
-            kern<<<b.ntiles, C::NT, B6::SMEM, s>>>(tmp, tmg, b, w.par, w.aux, do_rag ? 1 : 0, w.keys, w.vals, w.slots,
-                                                   w.ecount, gmask, c->status);
+            kern<<<b.ntiles, C::NT, B6::SMEM, s>>>(tmc, tmg, b, w.code, w.ends, w.tends, w.par, w.aux, do_rag ? 1 : 0,
+                                                   w.keys, w.vals, w.slots, w.ecount, gmask, c->status);
         } else if (tma) {
             if ((e = allow_smem(k_label<T, CONN, true>, B::SMEM)) != cudaSuccess)
                 return set_cuda_error(c, e, "smem attribute");

@@ -45,7 +45,10 @@ constexpr size_t OFF_TLIST = OFF_ACT + a256(kMaxTiles * 2);
 constexpr size_t OFF_COUNTERS = OFF_TLIST + a256(kMaxTiles * 4);
 constexpr size_t OFF_STATUS = OFF_COUNTERS + 256;
 constexpr size_t OFF_KCOUNT = OFF_STATUS + a256(sizeof(DevStatus));
-constexpr size_t kScratchBytes = OFF_KCOUNT + 256;
+constexpr size_t OFF_CODE = OFF_KCOUNT + 256;                  // 3D path: slot code per pixel
+constexpr size_t OFF_ENDS = OFF_CODE + a256(kMaxPixels * 2);   // 3D path: path ends, then roots
+constexpr size_t OFF_TENDS = OFF_ENDS + a256(kMaxPixels * 4);  // 3D path: slot span per tile
+constexpr size_t kScratchBytes = OFF_TENDS + a256(kMaxTiles * 8);
 
 }  // namespace
 
@@ -115,6 +118,11 @@ ws_status setup(int dev, ws_context **out)
         w.tlist = reinterpret_cast<int32_t *>(base + OFF_TLIST);
         w.counters = reinterpret_cast<int32_t *>(base + OFF_COUNTERS);
         w.kcount = reinterpret_cast<int32_t *>(base + OFF_KCOUNT);
+        w.ncode = kMaxPixels;
+        w.code = reinterpret_cast<uint16_t *>(base + OFF_CODE);
+        w.ends = reinterpret_cast<int32_t *>(base + OFF_ENDS);
+        w.ntends = kMaxTiles;
+        w.tends = reinterpret_cast<int2 *>(base + OFF_TENDS);
         sl.ready = true;
     }
     *out = &sl.ctx;

@@ -21,6 +21,16 @@
 //               tile-to-tile hops left), smallest pixel index per basin, and
 //               Alg. 5 step V on pixel pairs (pass values, deduplicated in a
 //               shared-memory hash before the global region table)
+//
+// 3D volumes (6-connectivity) take a variant of this pipeline with one z
+// column of the tile per thread:
+//   k_init6     as k_init, and numbers the tile's in-tile path ends (slots):
+//               per pixel the 16-bit slot of its end, per tile the list of
+//               its end pixels; par holds the arrow of Eq. 1
+//   k_chase     the root of every listed end, following par out of the
+//               tile and the slot codes through the next tiles
+//   k_rag6      per tile: roots by slot lookup, smallest index per basin,
+//               and Alg. 5 step V from per-warp lists of boundary pixels
 //   k_rank_*    canonical ids: rank of every basin's smallest pixel index
 //               among all of them, by a bitmap over pixel indices
 //   k_write     per pixel: canonical id of its root and its id on every
@@ -78,7 +88,7 @@ template <int CONN> inline TileGeo tiles_for(const Geo &g)
 }
 
 // counters[] slots in the workspace
-enum { CNT_TILES = 0, CNT_ROOTS = 1, CNT_K0 = 2, CNT_NGROUPS = 3 };
+enum { CNT_TILES = 0, CNT_ROOTS = 1, CNT_ENDS = 2 };
 
 __device__ __forceinline__ int enc_final(int g) { return -1 - g; }
 __device__ __forceinline__ int dec_final(int e) { return -1 - e; }
@@ -424,13 +434,19 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
 // k_init6: k_init for 3D 6-connectivity, one z column of the tile per thread
 // ---------------------------------------------------------------------------
 //
-// Same results as k_init<T, 6>.  The dense 3D case is written without
-// divergent branches in the per-pixel work: step I tracks the lowest
-// neighbour (and its local and global offsets) with selects, the pointer
-// doubling keeps a thread's own entries in registers and moves them with
-// predicated shared-memory loads and stores (every load of a round issued
-// before any store, two hops per round), and the pixel states travel packed
-// two bits per pixel.
+// Step I (Eq. 1) and step III inside the tile, for the 3D path (k_init6,
+// k_chase, k_rag6):
+//   - par[p] is the arrow of Eq. 1 (the lowest neighbour), or p itself for a
+//     strict minimum or a plateau pixel (resolved later by step II / IV);
+//   - a pixel whose arrow leaves the tile, a minimum and a plateau pixel end
+//     their in-tile paths; the ends of tile t get slots 0..n-1, ends[first +
+//     slot] is the end pixel and tends[t] = (first, n);
+//   - pointer doubling (two hops a round, a thread's column of pointers in
+//     registers, predicated shared-memory gathers, every load of a round
+//     issued before any store) takes every pixel to its end: code[p] is the
+//     slot of p's end.
+// The per-pixel work has no divergent branches: step I tracks the lowest
+// neighbour and its offsets with selects.
 
 // v = c >= 0 ? nx[c] : c, nx at shared address sbase (no branch)
 __device__ __forceinline__ int gather_if(int c, unsigned sbase)
@@ -457,14 +473,18 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
                                                         int32_t *__restrict__ par, int32_t *__restrict__ mi,
                                                         int32_t *__restrict__ dist, uint8_t *__restrict__ plat,
                                                         uint8_t *__restrict__ act, int32_t *__restrict__ tlist,
-                                                        int32_t *__restrict__ roots, int32_t *counters,
-                                                        DevStatus *status)
+                                                        int32_t *__restrict__ roots, uint16_t *__restrict__ code,
+                                                        int32_t *__restrict__ ends, int2 *__restrict__ tends,
+                                                        int32_t *counters, DevStatus *status)
 {
     using C = TC<6>;
     using B = InitBox<T, 6>;
     static_assert(C::NT == C::TX * C::TY && C::TX == 32 && C::PER == C::TZ, "one z column per thread");
+    constexpr int NW = C::NT / 32;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[2];
+    __shared__ int wbase[NW];
+    __shared__ int s_first;
     int *nx = (int *)(smem + (TMA ? 2 : 1) * B::STAGE);
     const unsigned sbase = smem_u32(nx);
     const int tid = threadIdx.x, lane = tid & 31, lx = lane, ly = tid >> 5;
@@ -529,17 +549,17 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
         const bool col_in = x < geo.W && y < geo.H;
         const bool vxm = interior || x > 0, vxp = interior || x + 1 < geo.W;
         const bool vym = interior || y > 0, vyp = interior || y + 1 < geo.H;
-        int cur[C::TZ];    // this thread's entries of nx
-        unsigned stb = 0;  // their states, two bits each
+        const int p0 = base + (z0 * geo.H + y) * geo.W + x;   // global index of (lx, ly, z = 0)
+        unsigned stb = 0;   // pixel states, two bits each
+        unsigned endb = 0;  // bit k: pixel k of the column ends its in-tile path
         int plateau = 0;
         {
             unsigned cz[C::TZ + 2];
 #pragma unroll
             for (int k = 0; k < C::TZ + 2; k++) cz[k] = gs[h0 + k * SZ];
-            int p = base + (z0 * geo.H + y) * geo.W + x;
 #pragma unroll
-            for (int k = 0; k < C::TZ; k++, p += HW) {
-                const int z = z0 + k;
+            for (int k = 0; k < C::TZ; k++) {
+                const int z = z0 + k, p = p0 + k * HW;
                 const int h = h0 + (k + 1) * SZ;
                 const unsigned gp = cz[k + 1];
                 unsigned m = 0xffffffffu;
@@ -561,22 +581,54 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
                 take(interior || z + 1 < geo.D, cz[k + 2], C::TX * C::TY, HW, k < C::TZ - 1);
                 const bool in = col_in && z < geo.D;
                 const bool st0 = has && m < gp, st1 = !has || m > gp;
-                const int code = !in ? STOUT : (st0 ? ST0 : (st1 ? ST1 : STP));
+                const int state = !in ? STOUT : (st0 ? ST0 : (st1 ? ST1 : STP));
                 const int i = tid + k * C::NT;
-                const int c = !in ? enc_final(0) : (st0 ? (tin ? i + lo : enc_final(p + go)) : enc_final(p));
-                plateau |= code == STP;
-                stb |= (unsigned)code << (2 * k);
-                nx[i] = c;
+                const bool follow = in && st0 && tin;   // the arrow stays in the tile
+                nx[i] = follow ? i + lo : -1;           // ends are numbered below
+                if (in) par[p] = st0 ? p + go : p;
+                plateau |= state == STP;
+                stb |= (unsigned)state << (2 * k);
+                endb |= (unsigned)(in && !follow) << k;
             }
         }
-        __syncthreads();  // the gradient box of stage s is no longer read; nx is complete
-        if (TMA && tid == 0 && t + 2 * G < b.ntiles) init_issue<T, 6, TMA>(&tm, gs, &bars[s], b, t + 2 * G);
+        // number the ends: warp counts, block prefix, one span of the global
+        // end list per tile (its offset is needed only at the end)
+        {
+            int wc = 0;
 #pragma unroll
-        for (int k = 0; k < C::TZ; k++) cur[k] = nx[tid + k * C::NT];
+            for (int k = 0; k < C::TZ; k++) wc += __popc(__ballot_sync(0xffffffffu, (endb >> k) & 1u));
+            if (lane == 0) wbase[ly] = wc;
+        }
+        __syncthreads();  // the gradient box of stage s is no longer read
+        if (TMA && tid == 0 && t + 2 * G < b.ntiles) init_issue<T, 6, TMA>(&tm, gs, &bars[s], b, t + 2 * G);
+        int first = 0, nend = 0;
+        if (tid == 0) {
+            for (int w = 0; w < NW; w++) {
+                const int c = wbase[w];
+                wbase[w] = nend;
+                nend += c;
+            }
+            first = atomicAdd(counters + CNT_ENDS, nend);
+        }
+        __syncthreads();
+        {
+            int run = wbase[ly];
+#pragma unroll
+            for (int k = 0; k < C::TZ; k++) {
+                const bool e = (endb >> k) & 1u;
+                const unsigned bb = __ballot_sync(0xffffffffu, e);
+                if (e) nx[tid + k * C::NT] = -1 - (run + __popc(bb & ((1u << lane) - 1u)));
+                run += __popc(bb);
+            }
+        }
+        __syncthreads();
 
         // step III inside the tile: pointer doubling, two hops a round.  A
         // value read while its owner is updating it is the old or the new
         // pointer of a pixel further down the same path, or the path's end.
+        int cur[C::TZ];
+#pragma unroll
+        for (int k = 0; k < C::TZ; k++) cur[k] = nx[tid + k * C::NT];
         for (int round = 0; round < 32; round++) {
             int more = 0;
 #pragma unroll
@@ -595,15 +647,20 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             }
             if (!__syncthreads_or(more)) break;
         }
-
+        if (tid == 0) {
+            s_first = first;
+            tends[t] = make_int2(first, nend);
+        }
+        __syncthreads();
         {
-            int p = base + (z0 * geo.H + y) * geo.W + x;
+            const int fst = s_first;
 #pragma unroll
-            for (int k = 0; k < C::TZ; k++, p += HW) {
+            for (int k = 0; k < C::TZ; k++) {
                 const unsigned sk = (stb >> (2 * k)) & 3u;
                 if (sk == (unsigned)STOUT) continue;
-                const int e = cur[k];
-                par[p] = e < 0 ? dec_final(e) : p;  // e >= 0 cannot survive 32 rounds
+                const int p = p0 + k * HW, slot = -1 - cur[k];   // cur[k] < 0 after 32 rounds
+                code[p] = (uint16_t)slot;
+                if ((endb >> k) & 1u) ends[fst + slot] = p;
                 if (sk != (unsigned)ST0) mi[p] = 0x7fffffff;
             }
         }
@@ -616,15 +673,14 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             int rb = 0;
             if (lane == 0) rb = atomicAdd(counters + CNT_ROOTS, __popc(bb));
             rb = __shfl_sync(0xffffffffu, rb, 0);
-            if (isr) roots[rb + __popc(bb & ((1u << lane) - 1u))] = base + ((z0 + k) * geo.H + y) * geo.W + x;
+            if (isr) roots[rb + __popc(bb & ((1u << lane) - 1u))] = p0 + k * HW;
         }
         if (__syncthreads_or(plateau)) {
-            int p = base + (z0 * geo.H + y) * geo.W + x;
 #pragma unroll
-            for (int k = 0; k < C::TZ; k++, p += HW) {
+            for (int k = 0; k < C::TZ; k++) {
                 const unsigned sk = (stb >> (2 * k)) & 3u;
                 if (sk == (unsigned)STOUT) continue;
-                dist[p] = sk == (unsigned)ST0 ? 0 : (sk == (unsigned)ST1 ? -2 : INF_D);
+                dist[p0 + k * HW] = sk == (unsigned)ST0 ? 0 : (sk == (unsigned)ST1 ? -2 : INF_D);
             }
             if (tid == 0) {
                 plat[t] = 1;
@@ -634,8 +690,8 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
         } else if (tid == 0) {
             plat[t] = 0;
         }
-        // (the __syncthreads_or above also orders this tile's nx reads before
-        // the next tile's nx writes)
+        // (the __syncthreads_or above also orders this tile's nx, wbase and
+        // s_first reads before the next tile's writes)
     }
 }
 
@@ -1113,51 +1169,8 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
 }
 
 // ---------------------------------------------------------------------------
-// k_label6: k_label for 3D 6-connectivity, one z column of the tile per thread
+// per-tile smallest-index table (3D path)
 // ---------------------------------------------------------------------------
-//
-// Same box and same results as k_label<T, 6>, with the per-pixel work cut
-// down for the dense 3D case:
-//   - thread (lx, ly) walks the column z = 0..TZ-1 of the tile, so box
-//     positions advance by a constant and no per-pixel index is decoded;
-//   - box entries hold the code of their path end (its slot in the tile's
-//     table of distinct ends, which the chase turns into roots);
-//   - the smallest pixel index per basin is taken at the start of every run
-//     of equal codes along the column, into a per-tile table of roots, and
-//     reaches the global array once per root and tile;
-//   - the +x neighbour's root comes from the next lane, the +z neighbour's
-//     from the next step of the column; pass values of a basin pair are
-//     folded into a one-entry register cache while the same pair repeats
-//     (boundary surfaces cross a column as runs of one pair), and only a
-//     change of pair reaches the shared edge hash.
-
-template <typename T> struct Label6Box {
-    using L = LabelBox<T, 6>;
-    static constexpr int DSLOTS = 4096;   // distinct path ends per tile
-    static constexpr int RT = 256;        // distinct roots per tile (smallest-index table)
-    static constexpr int EH = 512;        // shared edge-hash slots
-    static constexpr int OFF_DK = 0;
-    static constexpr int OFF_RK = OFF_DK + DSLOTS * 4;
-    static constexpr int OFF_RM = OFF_RK + RT * 4;
-    static constexpr int OFF_HK = OFF_RM + RT * 4;
-    static constexpr int OFF_HV = OFF_HK + EH * 8;
-    static constexpr int OFF_P = (OFF_HV + EH * 4 + 127) & ~127;
-    static constexpr int OFF_G = OFF_P + ((L::PBYTES + 127) & ~127);
-    static constexpr int SMEM = OFF_G + ((L::GBYTES + 127) & ~127);
-};
-
-// Root of path end e by plain pointer chasing (ends the table had no room for).
-static __device__ __noinline__ int chase_root(const int32_t *par, int e, int npix, DevStatus *status)
-{
-    for (int hop = 0; hop < (1 << 22); hop++) {
-        const int u = par[e];
-        if (u == e) return e;
-        if ((unsigned)u >= (unsigned)npix) break;
-        e = u;
-    }
-    record_error(status, DEV_NONCONVERGED, 9);
-    return -1;
-}
 
 // Smallest pixel index p of root r, into the tile's root table (rk, rm);
 // a crowded table sends p straight to the global array.
@@ -1181,42 +1194,156 @@ static __device__ __noinline__ void root_min(int *rk, int *rm, int nslots, int r
     atomicMin(mi + r, p);
 }
 
+// ---------------------------------------------------------------------------
+// k_chase, k_rag6: roots and region adjacency of the 3D path
+// ---------------------------------------------------------------------------
+
+// Global tile of pixel g (3D tiling of its image).
+__device__ __forceinline__ int tile_of_pixel(const Batch &b, int g)
+{
+    const ImgDesc d = img_desc(b, img_of_pixel(b, g));
+    const int q = g - d.base;
+    const int z = q / d.HW, r = q - z * d.HW, y = r / d.W, x = r - y * d.W;
+    return d.tile0 + ((z / TT<6>::TZ) * d.nty + y / TT<6>::TY) * d.ntx + x / TT<6>::TX;
+}
+
+// Root of every listed in-tile path end, in place, and the end pixel's par
+// set to it.  From an end e, par[e] is the next pixel q of the path (in a
+// neighbouring tile, or given by step II / IV), and q's own in-tile end is
+// ends[first of q's tile + code[q]] (or, once chased, already its root);
+// repeat until a root (par[r] == r).
+static __global__ void __launch_bounds__(NTHR) k_chase(const Batch b, int32_t *ends, const int2 *__restrict__ tends,
+                                                       const uint16_t *__restrict__ code, const int32_t *counters,
+                                                       int32_t *par, DevStatus *status)
+{
+    const int n = counters[CNT_ENDS];
+    const int npix = b.npix;
+    for (int j = blockIdx.x * NTHR + threadIdx.x; j < n; j += gridDim.x * NTHR) {
+        const int e0 = ends[j];
+        int e = e0;
+        bool ok = (unsigned)e0 < (unsigned)npix;
+        for (int hop = 0; ok; hop++) {
+            const int q = par[e];
+            if (q == e) break;
+            if ((unsigned)q >= (unsigned)npix || hop >= (1 << 22)) {
+                ok = false;
+                break;
+            }
+            const int2 te = __ldg(tends + tile_of_pixel(b, q));
+            const int s = __ldg(code + q);
+            if (s >= te.y) {
+                ok = false;
+                break;
+            }
+            e = ends[te.x + s];
+            if ((unsigned)e >= (unsigned)npix) ok = false;
+        }
+        if (!ok) {  // only after an earlier device error
+            record_error(status, DEV_NONCONVERGED, 12);
+            ends[j] = 0;
+            continue;
+        }
+        ends[j] = e;
+        if (e != e0) par[e0] = e;
+    }
+}
+
+// Shared-memory layout of k_rag6: the tile's slot -> root table, the roots
+// of the +x, +y, +z face pixels of the neighbouring tiles, the root table
+// for smallest indices, the edge hash, the per-warp boundary lists, then the
+// slot-code box and the
+// gradient box of the tile and its forward faces (x from x0, rows padded to
+// 16-byte multiples).
+template <typename T> struct Rag6Box {
+    using C = TC<6>;
+    static constexpr int BY = C::TY + 1, BZ = C::TZ + 1;
+    static constexpr int CW = C::TX + 8;                                  // uint16 code row: x0 .. x0 + 39
+    static constexpr int GW = sizeof(T) == 1 ? C::TX + 16 : C::TX + 8;    // gradient row
+    static constexpr int CBYTES = CW * BY * BZ * 2;
+    static constexpr int GBYTES = GW * BY * BZ * (int)sizeof(T);
+    static constexpr int TR = C::NPIX;                                    // slots of one tile
+    static constexpr int HX = C::TY * C::TZ, HY = C::TX * C::TZ, HZ = C::TX * C::TY;
+    static constexpr int RT = 256, EH = 512;
+    static constexpr int OFF_TR = 0;
+    static constexpr int OFF_H = OFF_TR + TR * 4;
+    static constexpr int OFF_RK = OFF_H + (HX + HY + HZ) * 4;
+    static constexpr int OFF_RM = OFF_RK + RT * 4;
+    static constexpr int OFF_HK = OFF_RM + RT * 4;
+    static constexpr int OFF_HV = OFF_HK + EH * 8;
+    static constexpr int BL = 128;                  // boundary list entries per warp
+    static constexpr int OFF_BL = OFF_HV + EH * 4;  // (root, where) per entry
+    static constexpr int OFF_C = (OFF_BL + (C::NT / 32) * BL * 8 + 127) & ~127;
+    static constexpr int OFF_G = OFF_C + ((CBYTES + 127) & ~127);
+    static constexpr int SMEM = OFF_G + ((GBYTES + 127) & ~127);
+    static_assert(OFF_HK % 8 == 0, "edge keys are 8-byte words");
+};
+
+// root of slot c of tile tn (a pixel of a neighbouring tile), -1 if invalid
+__device__ __forceinline__ int halo_root(bool valid, int c, int tn, const int2 *tends, const int32_t *ends,
+                                         DevStatus *status)
+{
+    if (!valid) return -1;
+    const int2 e = __ldg(tends + tn);
+    if (c >= e.y) {  // only after an earlier device error
+        record_error(status, DEV_NONCONVERGED, 13);
+        return -1;
+    }
+    return __ldg(ends + e.x + c);
+}
+
+// Per 3D tile, one z column per thread: the root of every pixel (through its
+// slot code and the tile's table) into par, the smallest pixel index per
+// basin, and with do_rag Alg. 5 step V on the +x, +y, +z pixel pairs: the
+// pass value max(G(p), G(q)) of every pair of different basins.
+//   - Smallest index: only a pixel with no pixel of its basin at -x, -y or
+//     -z inside the tile can hold the tile's smallest index of that basin;
+//     those few candidates go through the per-tile root table.
+//   - Pass values: the pixel loop only detects the pixels with a boundary
+//     in +x, +y or +z and appends (root, position, directions) to its warp's
+//     list (ballot-compacted stores, no divergent work); the lists are then
+//     worked through densely (every lane busy): pass values and the shared
+//     edge hash, which dedupes the pairs before the global region table.
 template <typename T, bool TMA>
-__global__ void __launch_bounds__(TT<6>::NT, 2) k_label6(const __grid_constant__ CUtensorMap tmp,
-                                                         const __grid_constant__ CUtensorMap tmg, const Batch b,
-                                                         int32_t *par, int32_t *mi, int do_rag,
-                                                         unsigned long long *keys, uint32_t *vals, int32_t *slots,
-                                                         int32_t *ecount, unsigned long long gmask, DevStatus *status)
+__global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ CUtensorMap tmc,
+                                                       const __grid_constant__ CUtensorMap tmg, const Batch b,
+                                                       const uint16_t *__restrict__ code,
+                                                       const int32_t *__restrict__ ends,
+                                                       const int2 *__restrict__ tends, int32_t *par, int32_t *mi,
+                                                       int do_rag, unsigned long long *keys, uint32_t *vals,
+                                                       int32_t *slots, int32_t *ecount, unsigned long long gmask,
+                                                       DevStatus *status)
 {
     using C = TC<6>;
-    using L = LabelBox<T, 6>;
-    using B = Label6Box<T>;
-    static_assert(C::NT == C::TX * C::TY && C::TX == 32, "one column per thread, one row per warp");
+    using B = Rag6Box<T>;
+    static_assert(C::NT == C::TX * C::TY && C::TX == 32 && C::TY <= 16 && C::TZ <= 16, "column layout");
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
-    int *dk = (int *)(smem + B::OFF_DK);   // distinct ends, then their roots
+    int *tr = (int *)(smem + B::OFF_TR);
+    int *hx = (int *)(smem + B::OFF_H), *hy = hx + B::HX, *hz = hy + B::HY;
     int *rk = (int *)(smem + B::OFF_RK);
     int *rm = (int *)(smem + B::OFF_RM);
     unsigned long long *hk = (unsigned long long *)(smem + B::OFF_HK);
     unsigned *hv = (unsigned *)(smem + B::OFF_HV);
-    int *pb = (int *)(smem + B::OFF_P);
+    int2 *bl = (int2 *)(smem + B::OFF_BL);
+    uint16_t *cb = (uint16_t *)(smem + B::OFF_C);
     T *gb = (T *)(smem + B::OFF_G);
     const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
-    const TileCtx tc = tile_ctx<6>(b, blockIdx.x);   // TMA: a single image (b.one)
+    const int t = blockIdx.x;
+    const TileCtx tc = tile_ctx<6>(b, t);
     const Geo &geo = tc.geo;
-    const T *g = (const T *)tc.grad;
     const int x0 = tc.x0, y0 = tc.y0, z0 = tc.z0, base = tc.base;
-    const int npix = b.npix;
-    constexpr int SZ = C::BY * L::RWP;   // box step of one z
-    constexpr int GZ = C::BY * L::RWG;
+    constexpr int SZ = B::BY * B::CW, GZ = B::BY * B::GW;
     if (TMA && tid == 0) {
         mbar_init(&bar, 1);
         mbar_fence_init();
-        mbar_arrive_expect_tx(&bar, L::PBYTES + (do_rag ? L::GBYTES : 0));
-        tma_load_3d(pb, &tmp, x0 - L::AP, y0, z0, &bar);
-        if (do_rag) tma_load_3d(gb, &tmg, x0 - L::AG, y0, z0, &bar);
+        mbar_arrive_expect_tx(&bar, B::CBYTES + (do_rag ? B::GBYTES : 0));
+        tma_load_3d(cb, &tmc, x0, y0, z0, &bar);
+        if (do_rag) tma_load_3d(gb, &tmg, x0, y0, z0, &bar);
     }
-    for (int i = tid; i < B::DSLOTS; i += C::NT) dk[i] = -1;
+    {
+        const int2 te = __ldg(tends + t);
+        for (int i = tid; i < te.y; i += C::NT) tr[i] = __ldg(ends + te.x + i);
+    }
     if (tid < B::RT) {
         rk[tid] = -1;
         rm[tid] = 0x7fffffff;
@@ -1226,147 +1353,115 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_label6(const __grid_constant__
             hk[i] = EMPTY_KEY;
             hv[i] = 0xffffffffu;
         }
-    __syncthreads();   // tables cleared (and the barrier initialised)
+    if (!TMA) {
+        const T *g = (const T *)tc.grad;
+        for (int i = tid; i < B::CW * B::BY * B::BZ; i += C::NT) {
+            const int bx = i % B::CW, by = (i / B::CW) % B::BY, bz = i / (B::CW * B::BY);
+            const int xx = x0 + bx, yy = y0 + by, zz = z0 + bz;
+            const bool in = xx < geo.W && yy < geo.H && zz < geo.D;
+            const int q = (zz * geo.H + yy) * geo.W + xx;
+            cb[i] = in ? code[base + q] : (uint16_t)0;
+            if (do_rag && bx < B::GW) gb[(bz * B::BY + by) * B::GW + bx] = in ? g[q] : (T)0;
+        }
+        constexpr int XW = B::GW > B::CW ? B::GW - B::CW : 1;   // gradient columns beyond the code box
+        if (do_rag && B::GW > B::CW)
+            for (int i = tid; i < XW * B::BY * B::BZ; i += C::NT) {
+                const int bx = B::CW + i % XW, by = (i / XW) % B::BY, bz = i / (XW * B::BY);
+                const int xx = x0 + bx, yy = y0 + by, zz = z0 + bz;
+                const bool in = xx < geo.W && yy < geo.H && zz < geo.D;
+                gb[(bz * B::BY + by) * B::GW + bx] = in ? g[(zz * geo.H + yy) * geo.W + xx] : (T)0;
+            }
+    }
+    __syncthreads();   // tables filled (and the barrier initialised)
     if (TMA) {
         const bool ok = mbar_wait(&bar, 0, status);
         if (__syncthreads_or(!ok)) return;
     }
 
-    // Box entry -> code: -1 outside the image, the end's slot (>= 0), or
-    // -2 - end when the table of ends had no room.
     const int x = x0 + lane, y = y0 + ly;
     const bool col_in = x < geo.W && y < geo.H;
-    auto encode = [&](int pos, int gpos, bool in, int q, int &pe, int &pc) {
-        int c = -1;
-        if (in) {
-            int e;
-            if (TMA) {
-                e = pb[pos];
-            } else {
-                e = par[base + q];
-                if (do_rag) gb[gpos] = g[q];
-            }
-            if ((unsigned)e >= (unsigned)npix) {
-                record_error(status, DEV_NONCONVERGED, 11);
-            } else if (e == pe) {
-                c = pc;
-            } else {
-                const int s = dedupe_slot(dk, e, B::DSLOTS);
-                c = s >= 0 ? s : -2 - e;
-                pe = e;
-                pc = c;
-            }
-        }
-        pb[pos] = c;
-    };
-    const int pcol = ly * L::RWP + lane + L::AP;   // box position of (lane, ly, z = 0)
-    const int gcol = ly * L::RWG + lane + L::AG;
-    {
-        int pe = -1, pc = -1;
-#pragma unroll 1
-        for (int k = 0; k <= C::TZ; k++)   // the column and its +z face entry
-            encode(pcol + k * SZ, gcol + k * GZ, col_in && z0 + k < geo.D, ((z0 + k) * geo.H + y) * geo.W + x, pe,
-                   pc);
-        // +y face: (lane, TY, z = ly)
-        pe = -1;
-        encode((ly * C::BY + C::TY) * L::RWP + lane + L::AP, (ly * C::BY + C::TY) * L::RWG + lane + L::AG,
-               x < geo.W && y0 + C::TY < geo.H && z0 + ly < geo.D, ((z0 + ly) * geo.H + y0 + C::TY) * geo.W + x, pe,
-               pc);
-        // +x face: (TX, tid % TY, tid / TY) for the first TY * TZ threads
-        if (tid < C::TY * C::TZ) {
+    if (do_rag) {
+        // roots of the forward face pixels, which belong to neighbouring tiles
+        const int ntx = tc.tg.ntx, nty = tc.tg.nty;
+        hz[tid] = halo_root(col_in && z0 + C::TZ < geo.D, cb[(C::TZ * B::BY + ly) * B::CW + lane], t + ntx * nty,
+                            tends, ends, status);
+        hy[tid] = halo_root(x < geo.W && y0 + C::TY < geo.H && z0 + ly < geo.D,
+                            cb[(ly * B::BY + C::TY) * B::CW + lane], t + ntx, tends, ends, status);
+        if (tid < B::HX) {
             const int fy = tid % C::TY, fz = tid / C::TY;
-            pe = -1;
-            encode((fz * C::BY + fy) * L::RWP + C::TX + L::AP, (fz * C::BY + fy) * L::RWG + C::TX + L::AG,
-                   x0 + C::TX < geo.W && y0 + fy < geo.H && z0 + fz < geo.D,
-                   ((z0 + fz) * geo.H + y0 + fy) * geo.W + x0 + C::TX, pe, pc);
+            hx[tid] = halo_root(x0 + C::TX < geo.W && y0 + fy < geo.H && z0 + fz < geo.D,
+                                cb[(fz * B::BY + fy) * B::CW + C::TX], t + 1, tends, ends, status);
         }
+        __syncthreads();
     }
-    __syncthreads();
-    // chase the distinct ends to their roots, LPD chases in flight per thread
-    {
-        constexpr int LPD = B::DSLOTS / C::NT;
-        int e[LPD];
-        unsigned live = 0;
+
+    auto root_at = [&](bool valid, int c) -> int { return valid ? tr[c & (B::TR - 1)] : -1; };
+    const bool vy = y + 1 < geo.H;
+    // +x / +y / +z neighbour root of pixel (lx, wy, k) of the tile
+    auto nb_root = [&](int dir, int lx, int wy, int k) -> int {
+        const int pos = (k * B::BY + wy) * B::CW + lx;
+        if (dir == 0) return lx + 1 < C::TX ? root_at(x0 + lx + 1 < geo.W, cb[pos + 1]) : hx[wy + C::TY * k];
+        if (dir == 1) return wy + 1 < C::TY ? root_at(y0 + wy + 1 < geo.H, cb[pos + B::CW]) : hy[lx + C::TX * k];
+        return k + 1 < C::TZ ? root_at(z0 + k + 1 < geo.D, cb[pos + SZ]) : hz[wy * C::TX + lx];
+    };
+    // pass values of a warp's listed boundary pixels, every lane busy
+    int2 *wl = bl + ly * B::BL;
+    auto drain = [&](int n) {
+        for (int e = lane; e < n; e += 32) {
+            const int r = wl[e].x, w = wl[e].y;
+            const int lx = w & 31, k = (w >> 5) & 31, fl = w >> 10;
+            const int gpos = (k * B::BY + ly) * B::GW + lx;
+            const unsigned gp = gb[gpos];
 #pragma unroll
-        for (int m = 0; m < LPD; m++) {
-            e[m] = dk[tid + m * C::NT];
-            live |= (e[m] >= 0 ? 1u : 0u) << m;
-        }
-        for (int hop = 0; live && hop < (1 << 22); hop++) {
-            int u[LPD];
-#pragma unroll
-            for (int m = 0; m < LPD; m++) u[m] = (live >> m) & 1u ? par[e[m]] : e[m];
-#pragma unroll
-            for (int m = 0; m < LPD; m++) {
-                if (u[m] == e[m]) {
-                    live &= ~(1u << m);
-                } else if ((unsigned)u[m] >= (unsigned)npix) {
-                    live &= ~(1u << m);
-                    e[m] = -1;
-                    record_error(status, DEV_NONCONVERGED, 11);
-                } else {
-                    e[m] = u[m];
-                }
+            for (int dir = 0; dir < 3; dir++) {
+                if (!((fl >> dir) & 1)) continue;
+                const int rn = nb_root(dir, lx, ly, k);
+                const unsigned gq = gb[gpos + (dir == 0 ? 1 : (dir == 1 ? B::GW : GZ))];
+                const unsigned h = gp > gq ? gp : gq;
+                smem_edge_insert((unsigned)(r < rn ? r : rn), (unsigned)(r < rn ? rn : r), h, hk, hv, B::EH, keys,
+                                 vals, slots, ecount, gmask, status);
             }
         }
-        if (live) record_error(status, DEV_NONCONVERGED, 9);
-#pragma unroll
-        for (int m = 0; m < LPD; m++) dk[tid + m * C::NT] = e[m];
-    }
-    __syncthreads();
-
-    auto root_of = [&](int c) -> int {
-        if (c >= 0) return dk[c];
-        if (c == -1) return -1;
-        return chase_root(par, -2 - c, npix, status);
     };
-    // the column: roots, smallest indices, pass values of +x, +y, +z pairs
-    unsigned ca = 0xffffffffu, cb = 0u, ch = 0xffffffffu;   // register edge cache
-    int pc = -1;
-    int rz = root_of(pb[pcol]);
+    int nl = 0;    // entries in this warp's list
+    int pr = -1;   // root of (x, y, z - 1)
+    const int pcol = ly * B::CW + lane;
     int p = base + (z0 * geo.H + y) * geo.W + x;
+    int rz = root_at(col_in && z0 < geo.D, cb[pcol]);
 #pragma unroll 1
     for (int k = 0; k < C::TZ && z0 + k < geo.D; k++, p += geo.HW) {   // trip count uniform in the CTA
         const int pos = pcol + k * SZ;
-        const int c = pb[pos];
         const int r = rz;
-        rz = root_of(pb[pos + SZ]);
+        if (k + 1 < C::TZ) rz = root_at(col_in && z0 + k + 1 < geo.D, cb[pos + SZ]);
+        else rz = do_rag ? hz[tid] : -1;
+        // smallest index: a candidate has no pixel of its basin at -x, -y, -z in the tile
+        const int rxm = __shfl_up_sync(0xffffffffu, r, 1);
+        const int rym = ly > 0 ? root_at(col_in, cb[pos - B::CW]) : -1;
         if (r >= 0) {
             par[p] = r;
-            if (c != pc) {
-                pc = c;
-                root_min(rk, rm, B::RT, r, p, mi);
-            }
+            if (r != pr && r != rym && (lane == 0 || r != rxm)) root_min(rk, rm, B::RT, r, p, mi);
         }
+        pr = r;
         if (!do_rag) continue;
         int rx = __shfl_down_sync(0xffffffffu, r, 1);
-        if (lane == 31) rx = root_of(pb[pos + 1]);
-        const int ry = root_of(pb[pos + L::RWP]);
-        const bool ex = rx >= 0 && rx != r, ey = ry >= 0 && ry != r, ez = rz >= 0 && rz != r;
-        if (r >= 0 && (ex | ey | ez)) {
-            const int gpos = gcol + k * GZ;
-            const unsigned gp = gb[gpos];
-#pragma unroll
-            for (int n = 0; n < 3; n++) {
-                const bool en = n == 0 ? ex : (n == 1 ? ey : ez);
-                if (!en) continue;
-                const int rn = n == 0 ? rx : (n == 1 ? ry : rz);
-                const unsigned gq = gb[gpos + (n == 0 ? 1 : (n == 1 ? L::RWG : GZ))];
-                const unsigned h = gp > gq ? gp : gq;
-                const unsigned lo = (unsigned)(r < rn ? r : rn), hi = (unsigned)(r < rn ? rn : r);
-                if (lo == ca && hi == cb) {
-                    ch = h < ch ? h : ch;
-                } else {
-                    if (ca != 0xffffffffu)
-                        smem_edge_insert(ca, cb, ch, hk, hv, B::EH, keys, vals, slots, ecount, gmask, status);
-                    ca = lo;
-                    cb = hi;
-                    ch = h;
-                }
-            }
+        if (lane == 31) rx = hx[ly + C::TY * k];
+        const int ry = ly + 1 < C::TY ? root_at(vy, cb[pos + B::CW]) : hy[lane + C::TX * k];
+        const int fl = r < 0 ? 0
+                             : (rx >= 0 && rx != r ? 1 : 0) | (ry >= 0 && ry != r ? 2 : 0) | (rz >= 0 && rz != r ? 4 : 0);
+        const unsigned m = __ballot_sync(0xffffffffu, fl != 0);
+        if (fl) wl[nl + __popc(m & ((1u << lane) - 1u))] = make_int2(r, (fl << 10) | (k << 5) | lane);
+        nl += __popc(m);
+        if (nl > B::BL - 32) {   // warp-uniform: the list is nearly full
+            __syncwarp();
+            drain(nl);
+            __syncwarp();
+            nl = 0;
         }
     }
-    if (do_rag && ca != 0xffffffffu) smem_edge_insert(ca, cb, ch, hk, hv, B::EH, keys, vals, slots, ecount, gmask, status);
+    if (do_rag) {
+        __syncwarp();
+        drain(nl);
+    }
     __syncthreads();
     if (tid < B::RT && rk[tid] >= 0) atomicMin(mi + rk[tid], rm[tid]);
     if (!do_rag) return;
