@@ -127,21 +127,22 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
         const bool tma = !b.d && make_tmap_3d(&tm, b.one.grad, sizeof(T), b.one.W, b.one.H, b.one.D, B::RW, C::HY,
                                               C::HZ);
         if constexpr (CONN == 6) {
-            // k_init6 is the 3D specialisation (same results)
+            // k_init6 is the 3D specialisation (it also numbers the path ends)
+            using B6 = Init6Box<T>;
             if (tma) {
-                if ((e = allow_smem(k_init6<T, true>, B::SMEM_TMA)) != cudaSuccess)
+                if ((e = allow_smem(k_init6<T, true>, B6::SMEM_TMA)) != cudaSuccess)
                     return set_cuda_error(c, e, "smem attribute");
-                const int grid = coop_grid(c, k_init6<T, true>, C::NT, B::SMEM_TMA, b.ntiles);
-                k_init6<T, true><<<grid, C::NT, B::SMEM_TMA, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act, w.tlist,
-                                                                  w.roots, w.code, w.ends, w.tends, w.counters,
-                                                                  c->status);
+                const int grid = coop_grid(c, k_init6<T, true>, C::NT, B6::SMEM_TMA, b.ntiles);
+                k_init6<T, true><<<grid, C::NT, B6::SMEM_TMA, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act,
+                                                                   w.tlist, w.roots, w.code, w.ends, w.tends,
+                                                                   w.counters, c->status);
             } else {
                 memset(&tm, 0, sizeof tm);
-                if ((e = allow_smem(k_init6<T, false>, B::SMEM_PLAIN)) != cudaSuccess)
+                if ((e = allow_smem(k_init6<T, false>, B6::SMEM_PLAIN)) != cudaSuccess)
                     return set_cuda_error(c, e, "smem attribute");
-                k_init6<T, false><<<b.ntiles, C::NT, B::SMEM_PLAIN, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act,
-                                                                         w.tlist, w.roots, w.code, w.ends, w.tends,
-                                                                         w.counters, c->status);
+                k_init6<T, false><<<b.ntiles, C::NT, B6::SMEM_PLAIN, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act,
+                                                                          w.tlist, w.roots, w.code, w.ends, w.tends,
+                                                                          w.counters, c->status);
             }
         } else if (tma) {
             if ((e = allow_smem(k_init<T, CONN, true>, B::SMEM_TMA)) != cudaSuccess)

@@ -441,31 +441,75 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
 //   - a pixel whose arrow leaves the tile, a minimum and a plateau pixel end
 //     their in-tile paths; the ends of tile t get slots 0..n-1, ends[first +
 //     slot] is the end pixel and tends[t] = (first, n);
-//   - pointer doubling (two hops a round, a thread's column of pointers in
-//     registers, predicated shared-memory gathers, every load of a round
-//     issued before any store) takes every pixel to its end: code[p] is the
-//     slot of p's end.
-// The per-pixel work has no divergent branches: step I tracks the lowest
-// neighbour and its offsets with selects.
+//   - pointer doubling (ends point at themselves; two hops a round, a
+//     thread's column of pointers in registers, every load of a round issued
+//     before any store) takes every pixel to its end: code[p] is the slot of
+//     p's end.
+// Step I picks the lowest neighbour with one integer minimum over packed
+// keys (value << 3 | 7 - n, so that ties go to the later neighbour n in
+// ascending index order) and has no divergent branches.
 
-// v = c >= 0 ? nx[c] : c, nx at shared address sbase (no branch)
-__device__ __forceinline__ int gather_if(int c, unsigned sbase)
-{
-    int v;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ge.s32 p, %1, 0;\n\tmov.b32 %0, %1;\n\t@p ld.volatile.shared.b32 %0, [%2];\n\t}"
-        : "=r"(v)
-        : "r"(c), "r"(sbase + 4u * (unsigned)c)
-        : "memory");
-    return v;
-}
+__device__ __forceinline__ unsigned umin2(unsigned a, unsigned b) { return a < b ? a : b; }
 
-// if (c >= 0) shared[addr] = v (no branch)
-__device__ __forceinline__ void store_if(int c, unsigned addr, int v)
+template <typename T> struct Init6Box {
+    using B = InitBox<T, 6>;
+    static constexpr int NPIX = TC<6>::NPIX;
+    static constexpr int SMEM_TMA = 2 * B::STAGE + NPIX * 4 + NPIX * 2;   // two stages, pointers, slots
+    static constexpr int SMEM_PLAIN = B::STAGE + NPIX * 4 + NPIX * 2;
+};
+
+// Step I on the thread's column (z = 0..TZ-1): in-tile pointers into nx
+// (ends point at themselves), the arrow into par, states into stb (two bits
+// per pixel), ends into endb.  CHECK = false for a tile whose halo lies
+// inside the image.
+template <typename T, bool CHECK>
+__device__ __forceinline__ void init6_step1(const T *gs, int *nx, int32_t *par, const int *lo_tab, const int *go_tab,
+                                            int tid, int lx, int ly, int h0, int p0, int x, int y, int z0,
+                                            const Geo &geo, unsigned &stb, unsigned &endb, int &plateau)
 {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ge.s32 p, %0, 0;\n\t@p st.volatile.shared.b32 [%1], %2;\n\t}" ::"r"(c),
-                 "r"(addr), "r"(v)
-                 : "memory");
+    using C = TC<6>;
+    using B = InitBox<T, 6>;
+    constexpr int SZ = C::HY * B::RW;
+    const bool col_in = x < geo.W && y < geo.H;
+    const bool vxm = x > 0, vxp = x + 1 < geo.W, vym = y > 0, vyp = y + 1 < geo.H;
+    // bit n: neighbour n of a pixel of this column lies in the tile (z bits per k below)
+    const unsigned tcol = (ly > 0 ? 2u : 0u) | (lx > 0 ? 4u : 0u) | (lx < C::TX - 1 ? 8u : 0u) |
+                          (ly < C::TY - 1 ? 16u : 0u);
+    unsigned cz[C::TZ + 2];
+#pragma unroll
+    for (int k = 0; k < C::TZ + 2; k++) cz[k] = gs[h0 + k * SZ];
+#pragma unroll
+    for (int k = 0; k < C::TZ; k++) {
+        const int z = z0 + k, p = p0 + k * geo.HW;
+        const int h = h0 + (k + 1) * SZ;
+        const unsigned gp = cz[k + 1];
+        unsigned k0 = cz[k] * 8u + 7u, k1 = (unsigned)gs[h - B::RW] * 8u + 6u, k2 = (unsigned)gs[h - 1] * 8u + 5u;
+        unsigned k3 = (unsigned)gs[h + 1] * 8u + 4u, k4 = (unsigned)gs[h + B::RW] * 8u + 3u, k5 = cz[k + 2] * 8u + 2u;
+        if (CHECK) {
+            k0 = z > 0 ? k0 : 0xffffffffu;
+            k1 = vym ? k1 : 0xffffffffu;
+            k2 = vxm ? k2 : 0xffffffffu;
+            k3 = vxp ? k3 : 0xffffffffu;
+            k4 = vyp ? k4 : 0xffffffffu;
+            k5 = z + 1 < geo.D ? k5 : 0xffffffffu;
+        }
+        const unsigned m = umin2(umin2(umin2(k0, k1), umin2(k2, k3)), umin2(k4, k5));
+        const bool has = !CHECK || m != 0xffffffffu;
+        const unsigned vmin = m >> 3;
+        const int n = 7 - (int)(m & 7u);
+        const bool in = !CHECK || (col_in && z < geo.D);
+        const bool st0 = has && vmin < gp, st1 = !has || vmin > gp;
+        const int state = !in ? STOUT : (st0 ? ST0 : (st1 ? ST1 : STP));
+        const unsigned tin = (tcol | (k > 0 ? 1u : 0u) | (k < C::TZ - 1 ? 32u : 0u)) >> (n & 7);
+        const int i = tid + k * C::NT;
+        const bool follow = in && st0 && (tin & 1u);   // the arrow stays in the tile
+        const int nn = has ? n : 0;
+        nx[i] = follow ? i + lo_tab[nn] : i;
+        if (in) par[p] = st0 ? p + go_tab[nn] : p;
+        plateau |= state == STP;
+        stb |= (unsigned)state << (2 * k);
+        endb |= (unsigned)(in && !follow) << k;
+    }
 }
 
 template <typename T, bool TMA>
@@ -479,18 +523,23 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
 {
     using C = TC<6>;
     using B = InitBox<T, 6>;
-    static_assert(C::NT == C::TX * C::TY && C::TX == 32 && C::PER == C::TZ, "one z column per thread");
+    static_assert(C::NT == C::TX * C::TY && C::TX == 32 && C::PER == C::TZ && C::NT / 32 <= 32, "column layout");
     constexpr int NW = C::NT / 32;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[2];
     __shared__ int wbase[NW];
     __shared__ int s_first;
+    __shared__ int lo_tab[6], go_tab[6];
     int *nx = (int *)(smem + (TMA ? 2 : 1) * B::STAGE);
-    const unsigned sbase = smem_u32(nx);
+    uint16_t *slotof = (uint16_t *)(nx + C::NPIX);
     const int tid = threadIdx.x, lane = tid & 31, lx = lane, ly = tid >> 5;
     const int G = gridDim.x;
     constexpr int SZ = C::HY * B::RW;              // box step of one z
     const int h0 = (ly + 1) * B::RW + lx + B::A;   // box index of (lx, ly, z = -1)
+    if (tid < 6) {  // local offsets of the neighbours, ascending index order
+        const int l[6] = {-C::TX * C::TY, -C::TX, -1, 1, C::TX, C::TX * C::TY};
+        lo_tab[tid] = l[tid];
+    }
 
     if (TMA) {  // a single image (b.one); two tiles in flight per CTA
         if (tid == 0) {
@@ -501,8 +550,8 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             if (t0 < b.ntiles) init_issue<T, 6, TMA>(&tm, (T *)smem, &bars[0], b, t0);
             if (t0 + G < b.ntiles) init_issue<T, 6, TMA>(&tm, (T *)(smem + B::STAGE), &bars[1], b, t0 + G);
         }
-        __syncthreads();
     }
+    __syncthreads();
 
     int j = 0;
     for (int t = blockIdx.x; t < b.ntiles; t += G, j++) {
@@ -511,6 +560,10 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
         const TileCtx tc = tile_ctx<6>(b, t);
         const Geo &geo = tc.geo;
         const int x0 = tc.x0, y0 = tc.y0, z0 = tc.z0, base = tc.base;
+        if (tid < 6) {  // global offsets (the image may change from tile to tile in a batch)
+            const int gofs[6] = {-geo.HW, -geo.W, -1, 1, geo.W, geo.HW};
+            go_tab[tid] = gofs[tid];
+        }
         if (TMA) {
             const bool ok = mbar_wait(&bars[s], (unsigned)((j >> 1) & 1), status);
             if (__syncthreads_or(!ok)) return;
@@ -540,58 +593,22 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             __syncthreads();
         }
 
-        // step I (Eq. 1) on the column: lowest neighbour, ties to the later
-        // one in ascending index order (z-1, y-1, x-1, x+1, y+1, z+1)
+        // step I (Eq. 1) on the column
         const int x = x0 + lx, y = y0 + ly;
-        const int W = geo.W, HW = geo.HW;
+        const int HW = geo.HW;
         const bool interior = x0 >= 1 && x0 + C::TX < geo.W && y0 >= 1 && y0 + C::TY < geo.H && z0 >= 1 &&
                               z0 + C::TZ < geo.D;
-        const bool col_in = x < geo.W && y < geo.H;
-        const bool vxm = interior || x > 0, vxp = interior || x + 1 < geo.W;
-        const bool vym = interior || y > 0, vyp = interior || y + 1 < geo.H;
         const int p0 = base + (z0 * geo.H + y) * geo.W + x;   // global index of (lx, ly, z = 0)
         unsigned stb = 0;   // pixel states, two bits each
         unsigned endb = 0;  // bit k: pixel k of the column ends its in-tile path
         int plateau = 0;
-        {
-            unsigned cz[C::TZ + 2];
-#pragma unroll
-            for (int k = 0; k < C::TZ + 2; k++) cz[k] = gs[h0 + k * SZ];
-#pragma unroll
-            for (int k = 0; k < C::TZ; k++) {
-                const int z = z0 + k, p = p0 + k * HW;
-                const int h = h0 + (k + 1) * SZ;
-                const unsigned gp = cz[k + 1];
-                unsigned m = 0xffffffffu;
-                int lo = 0, go = 0;
-                bool tin = false, has = false;
-                auto take = [&](bool valid, unsigned v, int l, int gofs, bool ti) {
-                    const bool tk = valid && v <= m;
-                    m = tk ? v : m;
-                    lo = tk ? l : lo;
-                    go = tk ? gofs : go;
-                    tin = tk ? ti : tin;
-                    has = has || tk;
-                };
-                take(interior || z > 0, cz[k], -C::TX * C::TY, -HW, k > 0);
-                take(vym, gs[h - B::RW], -C::TX, -W, ly > 0);
-                take(vxm, gs[h - 1], -1, -1, lx > 0);
-                take(vxp, gs[h + 1], 1, 1, lx < C::TX - 1);
-                take(vyp, gs[h + B::RW], C::TX, W, ly < C::TY - 1);
-                take(interior || z + 1 < geo.D, cz[k + 2], C::TX * C::TY, HW, k < C::TZ - 1);
-                const bool in = col_in && z < geo.D;
-                const bool st0 = has && m < gp, st1 = !has || m > gp;
-                const int state = !in ? STOUT : (st0 ? ST0 : (st1 ? ST1 : STP));
-                const int i = tid + k * C::NT;
-                const bool follow = in && st0 && tin;   // the arrow stays in the tile
-                nx[i] = follow ? i + lo : -1;           // ends are numbered below
-                if (in) par[p] = st0 ? p + go : p;
-                plateau |= state == STP;
-                stb |= (unsigned)state << (2 * k);
-                endb |= (unsigned)(in && !follow) << k;
-            }
-        }
-        // number the ends: warp counts, block prefix, one span of the global
+        if (interior)
+            init6_step1<T, false>(gs, nx, par, lo_tab, go_tab, tid, lx, ly, h0, p0, x, y, z0, geo, stb, endb,
+                                  plateau);
+        else
+            init6_step1<T, true>(gs, nx, par, lo_tab, go_tab, tid, lx, ly, h0, p0, x, y, z0, geo, stb, endb,
+                                 plateau);
+        // number the ends: warp counts, a warp scan, one span of the global
         // end list per tile (its offset is needed only at the end)
         {
             int wc = 0;
@@ -602,13 +619,17 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
         __syncthreads();  // the gradient box of stage s is no longer read
         if (TMA && tid == 0 && t + 2 * G < b.ntiles) init_issue<T, 6, TMA>(&tm, gs, &bars[s], b, t + 2 * G);
         int first = 0, nend = 0;
-        if (tid == 0) {
-            for (int w = 0; w < NW; w++) {
-                const int c = wbase[w];
-                wbase[w] = nend;
-                nend += c;
+        if (ly == 0) {
+            const int c = lane < NW ? wbase[lane] : 0;
+            int inc = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += u;
             }
-            first = atomicAdd(counters + CNT_ENDS, nend);
+            nend = __shfl_sync(0xffffffffu, inc, 31);
+            if (lane < NW) wbase[lane] = inc - c;
+            if (lane == 0) first = atomicAdd(counters + CNT_ENDS, nend);
         }
         __syncthreads();
         {
@@ -617,11 +638,10 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             for (int k = 0; k < C::TZ; k++) {
                 const bool e = (endb >> k) & 1u;
                 const unsigned bb = __ballot_sync(0xffffffffu, e);
-                if (e) nx[tid + k * C::NT] = -1 - (run + __popc(bb & ((1u << lane) - 1u)));
+                if (e) slotof[tid + k * C::NT] = (uint16_t)(run + __popc(bb & ((1u << lane) - 1u)));
                 run += __popc(bb);
             }
         }
-        __syncthreads();
 
         // step III inside the tile: pointer doubling, two hops a round.  A
         // value read while its owner is updating it is the old or the new
@@ -629,23 +649,24 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
         int cur[C::TZ];
 #pragma unroll
         for (int k = 0; k < C::TZ; k++) cur[k] = nx[tid + k * C::NT];
+        volatile int *vnx = nx;
         for (int round = 0; round < 32; round++) {
             int more = 0;
 #pragma unroll
             for (int h = 0; h < C::TZ; h += 8) {  // eight entries in flight
                 int nxt[8];
 #pragma unroll
-                for (int k = 0; k < 8; k++) nxt[k] = gather_if(cur[h + k], sbase);
+                for (int k = 0; k < 8; k++) nxt[k] = vnx[cur[h + k]];
 #pragma unroll
-                for (int k = 0; k < 8; k++) nxt[k] = gather_if(nxt[k], sbase);
+                for (int k = 0; k < 8; k++) nxt[k] = vnx[nxt[k]];
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
-                    store_if(cur[h + k], sbase + 4u * (unsigned)(tid + (h + k) * C::NT), nxt[k]);
-                    more |= nxt[k] >= 0;
+                    vnx[tid + (h + k) * C::NT] = nxt[k];
+                    more |= nxt[k] != cur[h + k];
                     cur[h + k] = nxt[k];
                 }
             }
-            if (!__syncthreads_or(more)) break;
+            if (!__syncthreads_or(more)) break;   // (also publishes slotof)
         }
         if (tid == 0) {
             s_first = first;
@@ -658,7 +679,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             for (int k = 0; k < C::TZ; k++) {
                 const unsigned sk = (stb >> (2 * k)) & 3u;
                 if (sk == (unsigned)STOUT) continue;
-                const int p = p0 + k * HW, slot = -1 - cur[k];   // cur[k] < 0 after 32 rounds
+                const int p = p0 + k * HW, slot = slotof[cur[k]];   // cur[k]: the end (32 rounds always suffice)
                 code[p] = (uint16_t)slot;
                 if ((endb >> k) & 1u) ends[fst + slot] = p;
                 if (sk != (unsigned)ST0) mi[p] = 0x7fffffff;
@@ -690,8 +711,8 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
         } else if (tid == 0) {
             plat[t] = 0;
         }
-        // (the __syncthreads_or above also orders this tile's nx, wbase and
-        // s_first reads before the next tile's writes)
+        // (the __syncthreads_or above also orders this tile's nx, slotof,
+        // wbase, s_first and go_tab reads before the next tile's writes)
     }
 }
 
