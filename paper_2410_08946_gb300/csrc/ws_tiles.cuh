@@ -37,6 +37,8 @@
 //               waterfall level, one pass writing all NL planes
 #pragma once
 
+#include <type_traits>
+
 #include "ws_kernels.cuh"
 #include "ws_tma.cuh"
 
@@ -1190,32 +1192,6 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
 }
 
 // ---------------------------------------------------------------------------
-// per-tile smallest-index table (3D path)
-// ---------------------------------------------------------------------------
-
-// Smallest pixel index p of root r, into the tile's root table (rk, rm);
-// a crowded table sends p straight to the global array.
-static __device__ __noinline__ void root_min(int *rk, int *rm, int nslots, int r, int p, int32_t *mi)
-{
-    volatile int *vk = rk;
-    unsigned s = ((unsigned)r * 0x9E3779B1u) >> 24;
-    s &= (unsigned)(nslots - 1);
-    for (int probe = 0; probe < 32; probe++) {
-        int k = vk[s];
-        if (k == -1) {
-            k = atomicCAS(rk + s, -1, r);
-            if (k == -1) k = r;
-        }
-        if (k == r) {
-            atomicMin(rm + s, p);
-            return;
-        }
-        s = (s + 1) & (unsigned)(nslots - 1);
-    }
-    atomicMin(mi + r, p);
-}
-
-// ---------------------------------------------------------------------------
 // k_chase, k_rag6: roots and region adjacency of the 3D path
 // ---------------------------------------------------------------------------
 
@@ -1269,12 +1245,12 @@ static __global__ void __launch_bounds__(NTHR) k_chase(const Batch b, int32_t *e
     }
 }
 
-// Shared-memory layout of k_rag6: the tile's slot -> root table, the roots
-// of the +x, +y, +z face pixels of the neighbouring tiles, the root table
-// for smallest indices, the edge hash, the per-warp boundary lists, then the
-// slot-code box and the
-// gradient box of the tile and its forward faces (x from x0, rows padded to
-// 16-byte multiples).
+// Shared-memory layout of k_rag6: the roots (then basin ids) of the +x, +y,
+// +z face pixels of the neighbouring tiles, the basin id of every slot of the
+// tile, the tile's basin list and its hash, the smallest index per basin,
+// the basin-pair pass matrix, the edge hash for crowded tiles, then the
+// slot-code box and the gradient box of the tile and its forward faces (x
+// from x0, rows padded to 16-byte multiples).
 template <typename T> struct Rag6Box {
     using C = TC<6>;
     static constexpr int BY = C::TY + 1, BZ = C::TZ + 1;
@@ -1282,29 +1258,36 @@ template <typename T> struct Rag6Box {
     static constexpr int GW = sizeof(T) == 1 ? C::TX + 16 : C::TX + 8;    // gradient row
     static constexpr int CBYTES = CW * BY * BZ * 2;
     static constexpr int GBYTES = GW * BY * BZ * (int)sizeof(T);
-    static constexpr int TR = C::NPIX;                                    // slots of one tile
-    static constexpr int HX = C::TY * C::TZ, HY = C::TX * C::TZ, HZ = C::TX * C::TY;
-    static constexpr int RT = 256, EH = 512;
-    static constexpr int OFF_TR = 0;
-    static constexpr int OFF_H = OFF_TR + TR * 4;
-    static constexpr int OFF_RK = OFF_H + (HX + HY + HZ) * 4;
-    static constexpr int OFF_RM = OFF_RK + RT * 4;
-    static constexpr int OFF_HK = OFF_RM + RT * 4;
-    static constexpr int OFF_HV = OFF_HK + EH * 8;
-    static constexpr int BL = 128;                  // boundary list entries per warp
-    static constexpr int OFF_BL = OFF_HV + EH * 4;  // (root, where) per entry
-    static constexpr int OFF_C = (OFF_BL + (C::NT / 32) * BL * 8 + 127) & ~127;
+    static constexpr int HX = C::TY * C::TZ, HY = C::TX * C::TZ, HZ = C::TX * C::TY, NH = HX + HY + HZ;
+    static constexpr int RB = 253;        // basins a tile can number (ids 0..RB-1)
+    static constexpr int RH = 512;        // basin hash slots
+    static constexpr int RM = 64;         // basins of the pass matrix
+    static constexpr int EH = 512;        // edge hash slots (tiles with more than RM basins)
+    static constexpr int OFF_HR = 0;                          // int32 [NH]
+    static constexpr int OFF_SS = OFF_HR + NH * 4;            // uint8 [NPIX]
+    static constexpr int OFF_RL = OFF_SS + C::NPIX;           // int32 [256]
+    static constexpr int OFF_RHK = OFF_RL + 256 * 4;          // int32 [RH]
+    static constexpr int OFF_RHV = OFF_RHK + RH * 4;          // int32 [RH]
+    static constexpr int OFF_RMIN = OFF_RHV + RH * 4;         // int32 [256]
+    static constexpr int OFF_PM = OFF_RMIN + 256 * 4;         // uint32 [RM * RM]
+    static constexpr int OFF_COL = OFF_PM + RM * RM * 4;      // uint4 [NT]: packed basin ids of each column
+    static constexpr int OFF_XF = OFF_COL + C::NT * 16;       // uint8 [TY][TZ]: ids of the +x face
+    static constexpr int OFF_YF = OFF_XF + C::TY * C::TZ;     // uint8 [TX][TZ]: ids of the +y face
+    static constexpr int WL = 128;                            // boundary items per warp and word
+    static constexpr int OFF_WL = OFF_YF + C::TX * C::TZ;     // uint16 [NT / 32][WL]
+    static constexpr int OFF_HK = (OFF_WL + (C::NT / 32) * WL * 2 + 7) & ~7;   // uint64 [EH]
+    static constexpr int OFF_HV = OFF_HK + EH * 8;            // uint32 [EH]
+    static constexpr int OFF_C = (OFF_HV + EH * 4 + 127) & ~127;
     static constexpr int OFF_G = OFF_C + ((CBYTES + 127) & ~127);
     static constexpr int SMEM = OFF_G + ((GBYTES + 127) & ~127);
     static_assert(OFF_HK % 8 == 0, "edge keys are 8-byte words");
 };
 
-// root of slot c of tile tn (a pixel of a neighbouring tile), -1 if invalid
-__device__ __forceinline__ int halo_root(bool valid, int c, int tn, const int2 *tends, const int32_t *ends,
-                                         DevStatus *status)
+// root of slot c of a neighbouring tile whose span of the end list is e,
+// -1 if invalid
+__device__ __forceinline__ int face_root(bool valid, int c, int2 e, const int32_t *ends, DevStatus *status)
 {
     if (!valid) return -1;
-    const int2 e = __ldg(tends + tn);
     if (c >= e.y) {  // only after an earlier device error
         record_error(status, DEV_NONCONVERGED, 13);
         return -1;
@@ -1312,18 +1295,23 @@ __device__ __forceinline__ int halo_root(bool valid, int c, int tn, const int2 *
     return __ldg(ends + e.x + c);
 }
 
-// Per 3D tile, one z column per thread: the root of every pixel (through its
-// slot code and the tile's table) into par, the smallest pixel index per
-// basin, and with do_rag Alg. 5 step V on the +x, +y, +z pixel pairs: the
-// pass value max(G(p), G(q)) of every pair of different basins.
+// Per 3D tile, one z column per thread: the root of every pixel into par,
+// the smallest pixel index per basin, and with do_rag Alg. 5 step V on the
+// +x, +y, +z pixel pairs: the pass value max(G(p), G(q)) of every pair of
+// different basins, min-reduced per pair.
+//   - The tile's basins (of its slots and of the forward faces) get 8-bit
+//     ids through a shared hash.  A thread packs its column's ids four to a
+//     register; the +z, +x (next lane) and +y (next warp, through shared
+//     memory) comparisons, and the -x, -y, -z ones for the smallest index,
+//     run four pixels per byte-SIMD instruction, and only the few pixels
+//     they flag are visited one by one.
+//   - With at most RM basins a pair's pass value goes straight into a
+//     shared RM x RM matrix by atomic min; tiles with more basins use the
+//     shared edge hash; tiles with more than RB basins take a per-pixel path
+//     that compares roots read from the global end list.
 //   - Smallest index: only a pixel with no pixel of its basin at -x, -y or
 //     -z inside the tile can hold the tile's smallest index of that basin;
-//     those few candidates go through the per-tile root table.
-//   - Pass values: the pixel loop only detects the pixels with a boundary
-//     in +x, +y or +z and appends (root, position, directions) to its warp's
-//     list (ballot-compacted stores, no divergent work); the lists are then
-//     worked through densely (every lane busy): pass values and the shared
-//     edge hash, which dedupes the pairs before the global region table.
+//     those candidates take a shared atomic min per basin id.
 template <typename T, bool TMA>
 __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ CUtensorMap tmc,
                                                        const __grid_constant__ CUtensorMap tmg, const Batch b,
@@ -1336,16 +1324,22 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
 {
     using C = TC<6>;
     using B = Rag6Box<T>;
-    static_assert(C::NT == C::TX * C::TY && C::TX == 32 && C::TY <= 16 && C::TZ <= 16, "column layout");
+    static_assert(C::NT == C::TX * C::TY && C::TX == 32 && C::TY == 16 && C::TZ == 16, "column layout");
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
-    int *tr = (int *)(smem + B::OFF_TR);
-    int *hx = (int *)(smem + B::OFF_H), *hy = hx + B::HX, *hz = hy + B::HY;
-    int *rk = (int *)(smem + B::OFF_RK);
-    int *rm = (int *)(smem + B::OFF_RM);
+    __shared__ int s_nr, s_full;
+    int *hr = (int *)(smem + B::OFF_HR);
+    int *hxr = hr, *hyr = hr + B::HX, *hzr = hyr + B::HY;
+    uint8_t *ss = smem + B::OFF_SS;
+    int *rl = (int *)(smem + B::OFF_RL);
+    int *rhk = (int *)(smem + B::OFF_RHK);
+    int *rhv = (int *)(smem + B::OFF_RHV);
+    int *rmin = (int *)(smem + B::OFF_RMIN);
+    unsigned *pm = (unsigned *)(smem + B::OFF_PM);
+    uint4 *colw = (uint4 *)(smem + B::OFF_COL);
+    uint8_t *xfb = smem + B::OFF_XF, *yfb = smem + B::OFF_YF;
     unsigned long long *hk = (unsigned long long *)(smem + B::OFF_HK);
     unsigned *hv = (unsigned *)(smem + B::OFF_HV);
-    int2 *bl = (int2 *)(smem + B::OFF_BL);
     uint16_t *cb = (uint16_t *)(smem + B::OFF_C);
     T *gb = (T *)(smem + B::OFF_G);
     const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
@@ -1361,19 +1355,14 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
         tma_load_3d(cb, &tmc, x0, y0, z0, &bar);
         if (do_rag) tma_load_3d(gb, &tmg, x0, y0, z0, &bar);
     }
-    {
-        const int2 te = __ldg(tends + t);
-        for (int i = tid; i < te.y; i += C::NT) tr[i] = __ldg(ends + te.x + i);
+    const int2 te = __ldg(tends + t);
+    const int ntx = tc.tg.ntx, nty = tc.tg.nty;
+    for (int i = tid; i < B::RH; i += C::NT) rhk[i] = -1;
+    if (tid < 256) rmin[tid] = 0x7fffffff;
+    if (tid == 0) {
+        s_nr = 0;
+        s_full = 0;
     }
-    if (tid < B::RT) {
-        rk[tid] = -1;
-        rm[tid] = 0x7fffffff;
-    }
-    if (do_rag)
-        for (int i = tid; i < B::EH; i += C::NT) {
-            hk[i] = EMPTY_KEY;
-            hv[i] = 0xffffffffu;
-        }
     if (!TMA) {
         const T *g = (const T *)tc.grad;
         for (int i = tid; i < B::CW * B::BY * B::BZ; i += C::NT) {
@@ -1393,101 +1382,287 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
                 gb[(bz * B::BY + by) * B::GW + bx] = in ? g[(zz * geo.H + yy) * geo.W + xx] : (T)0;
             }
     }
-    __syncthreads();   // tables filled (and the barrier initialised)
+    __syncthreads();   // tables cleared (and the barrier initialised)
+
+    const int x = x0 + lane, y = y0 + ly;
+    const bool col_in = x < geo.W && y < geo.H;
+    // number the tile's basins: its slots' roots and its forward faces' roots
+    auto rh_insert = [&](int r) {
+        if (r < 0) return;
+        volatile int *vk = rhk;
+        unsigned h = ((unsigned)r * 0x9E3779B1u) >> 23;   // 9 bits: RH == 512
+        for (int probe = 0; probe < B::RH; probe++) {
+            int k = vk[h];
+            if (k == -1) {
+                k = atomicCAS(rhk + h, -1, r);
+                if (k == -1) return;
+            }
+            if (k == r) return;
+            h = (h + 1) & (B::RH - 1);
+        }
+        s_full = 1;   // more than RH basins
+    };
+    auto rh_find = [&](int r) -> int {
+        if (r < 0) return 0xff;
+        unsigned h = ((unsigned)r * 0x9E3779B1u) >> 23;
+        for (int probe = 0; probe < B::RH; probe++) {
+            const int k = rhk[h];
+            if (k == r) return rhv[h];
+            if (k == -1) break;
+            h = (h + 1) & (B::RH - 1);
+        }
+        return B::RB;   // not numbered
+    };
+    // spans of the neighbouring tiles (for the face pixels), and the roots of
+    // this tile's slots: neither needs the boxes, so both go before the wait
+    const bool hasx = x0 + C::TX < geo.W, hasy = y0 + C::TY < geo.H, hasz = z0 + C::TZ < geo.D;
+    const int2 tex = do_rag && hasx && tid < B::HX ? __ldg(tends + t + 1) : make_int2(0, 0);
+    const int2 tey = do_rag && hasy ? __ldg(tends + t + ntx) : make_int2(0, 0);
+    const int2 tez = do_rag && hasz ? __ldg(tends + t + ntx * nty) : make_int2(0, 0);
+    for (int i = tid; i < te.y; i += C::NT) rh_insert(__ldg(ends + te.x + i));
     if (TMA) {
         const bool ok = mbar_wait(&bar, 0, status);
         if (__syncthreads_or(!ok)) return;
     }
-
-    const int x = x0 + lane, y = y0 + ly;
-    const bool col_in = x < geo.W && y < geo.H;
     if (do_rag) {
-        // roots of the forward face pixels, which belong to neighbouring tiles
-        const int ntx = tc.tg.ntx, nty = tc.tg.nty;
-        hz[tid] = halo_root(col_in && z0 + C::TZ < geo.D, cb[(C::TZ * B::BY + ly) * B::CW + lane], t + ntx * nty,
-                            tends, ends, status);
-        hy[tid] = halo_root(x < geo.W && y0 + C::TY < geo.H && z0 + ly < geo.D,
-                            cb[(ly * B::BY + C::TY) * B::CW + lane], t + ntx, tends, ends, status);
+        hzr[tid] = face_root(col_in && hasz, cb[(C::TZ * B::BY + ly) * B::CW + lane], tez, ends, status);
+        hyr[tid] = face_root(x < geo.W && hasy && z0 + ly < geo.D, cb[(ly * B::BY + C::TY) * B::CW + lane], tey,
+                             ends, status);
         if (tid < B::HX) {
             const int fy = tid % C::TY, fz = tid / C::TY;
-            hx[tid] = halo_root(x0 + C::TX < geo.W && y0 + fy < geo.H && z0 + fz < geo.D,
-                                cb[(fz * B::BY + fy) * B::CW + C::TX], t + 1, tends, ends, status);
+            hxr[tid] = face_root(hasx && y0 + fy < geo.H && z0 + fz < geo.D, cb[(fz * B::BY + fy) * B::CW + C::TX],
+                                 tex, ends, status);
         }
-        __syncthreads();
-    }
-
-    auto root_at = [&](bool valid, int c) -> int { return valid ? tr[c & (B::TR - 1)] : -1; };
-    const bool vy = y + 1 < geo.H;
-    // +x / +y / +z neighbour root of pixel (lx, wy, k) of the tile
-    auto nb_root = [&](int dir, int lx, int wy, int k) -> int {
-        const int pos = (k * B::BY + wy) * B::CW + lx;
-        if (dir == 0) return lx + 1 < C::TX ? root_at(x0 + lx + 1 < geo.W, cb[pos + 1]) : hx[wy + C::TY * k];
-        if (dir == 1) return wy + 1 < C::TY ? root_at(y0 + wy + 1 < geo.H, cb[pos + B::CW]) : hy[lx + C::TX * k];
-        return k + 1 < C::TZ ? root_at(z0 + k + 1 < geo.D, cb[pos + SZ]) : hz[wy * C::TX + lx];
-    };
-    // pass values of a warp's listed boundary pixels, every lane busy
-    int2 *wl = bl + ly * B::BL;
-    auto drain = [&](int n) {
-        for (int e = lane; e < n; e += 32) {
-            const int r = wl[e].x, w = wl[e].y;
-            const int lx = w & 31, k = (w >> 5) & 31, fl = w >> 10;
-            const int gpos = (k * B::BY + ly) * B::GW + lx;
-            const unsigned gp = gb[gpos];
-#pragma unroll
-            for (int dir = 0; dir < 3; dir++) {
-                if (!((fl >> dir) & 1)) continue;
-                const int rn = nb_root(dir, lx, ly, k);
-                const unsigned gq = gb[gpos + (dir == 0 ? 1 : (dir == 1 ? B::GW : GZ))];
-                const unsigned h = gp > gq ? gp : gq;
-                smem_edge_insert((unsigned)(r < rn ? r : rn), (unsigned)(r < rn ? rn : r), h, hk, hv, B::EH, keys,
-                                 vals, slots, ecount, gmask, status);
-            }
-        }
-    };
-    int nl = 0;    // entries in this warp's list
-    int pr = -1;   // root of (x, y, z - 1)
-    const int pcol = ly * B::CW + lane;
-    int p = base + (z0 * geo.H + y) * geo.W + x;
-    int rz = root_at(col_in && z0 < geo.D, cb[pcol]);
-#pragma unroll 1
-    for (int k = 0; k < C::TZ && z0 + k < geo.D; k++, p += geo.HW) {   // trip count uniform in the CTA
-        const int pos = pcol + k * SZ;
-        const int r = rz;
-        if (k + 1 < C::TZ) rz = root_at(col_in && z0 + k + 1 < geo.D, cb[pos + SZ]);
-        else rz = do_rag ? hz[tid] : -1;
-        // smallest index: a candidate has no pixel of its basin at -x, -y, -z in the tile
-        const int rxm = __shfl_up_sync(0xffffffffu, r, 1);
-        const int rym = ly > 0 ? root_at(col_in, cb[pos - B::CW]) : -1;
-        if (r >= 0) {
-            par[p] = r;
-            if (r != pr && r != rym && (lane == 0 || r != rxm)) root_min(rk, rm, B::RT, r, p, mi);
-        }
-        pr = r;
-        if (!do_rag) continue;
-        int rx = __shfl_down_sync(0xffffffffu, r, 1);
-        if (lane == 31) rx = hx[ly + C::TY * k];
-        const int ry = ly + 1 < C::TY ? root_at(vy, cb[pos + B::CW]) : hy[lane + C::TX * k];
-        const int fl = r < 0 ? 0
-                             : (rx >= 0 && rx != r ? 1 : 0) | (ry >= 0 && ry != r ? 2 : 0) | (rz >= 0 && rz != r ? 4 : 0);
-        const unsigned m = __ballot_sync(0xffffffffu, fl != 0);
-        if (fl) wl[nl + __popc(m & ((1u << lane) - 1u))] = make_int2(r, (fl << 10) | (k << 5) | lane);
-        nl += __popc(m);
-        if (nl > B::BL - 32) {   // warp-uniform: the list is nearly full
-            __syncwarp();
-            drain(nl);
-            __syncwarp();
-            nl = 0;
-        }
-    }
-    if (do_rag) {
-        __syncwarp();
-        drain(nl);
+        rh_insert(hzr[tid]);
+        rh_insert(hyr[tid]);
+        if (tid < B::HX) rh_insert(hxr[tid]);
     }
     __syncthreads();
-    if (tid < B::RT && rk[tid] >= 0) atomicMin(mi + rk[tid], rm[tid]);
+    for (int i = tid; i < B::RH; i += C::NT)
+        if (rhk[i] >= 0) {
+            const int id = atomicAdd(&s_nr, 1);
+            rhv[i] = id < B::RB ? id : B::RB;
+            if (id < B::RB) rl[id] = rhk[i];
+        }
+    __syncthreads();
+    const int nr = s_nr;
+    const int mode = (s_full || nr > B::RB) ? 2 : (nr > B::RM ? 1 : 0);   // uniform in the CTA
+    if (do_rag && mode == 0)
+        for (int i = tid; i < B::RM * B::RM; i += C::NT) pm[i] = 0xffffffffu;
+    if (do_rag && mode > 0)
+        for (int i = tid; i < B::EH; i += C::NT) {
+            hk[i] = EMPTY_KEY;
+            hv[i] = 0xffffffffu;
+        }
+    const int first = te.x;
+
+    auto edge = [&](int ida, int idb, unsigned h) {   // ids (mode 0, 1) or roots (mode 2)
+        if (mode == 0) {
+            const int a = ida < idb ? ida : idb, c2 = ida < idb ? idb : ida;
+            atomicMin(pm + a * B::RM + c2, h);
+        } else {
+            const int ra = mode < 2 ? rl[ida] : ida, rb = mode < 2 ? rl[idb] : idb;
+            smem_edge_insert((unsigned)(ra < rb ? ra : rb), (unsigned)(ra < rb ? rb : ra), h, hk, hv, B::EH, keys,
+                             vals, slots, ecount, gmask, status);
+        }
+    };
+    const int p0 = base + (z0 * geo.H + y) * geo.W + x;   // global index of (lane, ly, z = 0)
+    const int nz = geo.D - z0 < C::TZ ? geo.D - z0 : C::TZ;
+
+    if (mode < 2) {
+        for (int i = tid; i < te.y; i += C::NT) ss[i] = (uint8_t)rh_find(__ldg(ends + te.x + i));
+        if (do_rag) {   // ids of the forward faces
+            const int iz = rh_find(hzr[tid]);
+            hzr[tid] = iz;
+            yfb[lane * C::TZ + ly] = (uint8_t)rh_find(hyr[tid]);
+            if (tid < B::HX) xfb[(tid % C::TY) * C::TZ + tid / C::TY] = (uint8_t)rh_find(hxr[tid]);
+        }
+        __syncthreads();
+        // this column's ids, four to a register (byte k & 3 of word k >> 2;
+        // 0xff outside the image)
+        unsigned P[4];
+#pragma unroll
+        for (int w = 0; w < 4; w++) {
+            unsigned v = 0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int k = 4 * w + q;
+                const unsigned id = (col_in && k < nz) ? (unsigned)ss[cb[ly * B::CW + lane + k * SZ] & (C::NPIX - 1)]
+                                                       : 0xffu;
+                v |= id << (8 * q);
+            }
+            P[w] = v;
+        }
+        colw[tid] = make_uint4(P[0], P[1], P[2], P[3]);
+        const unsigned P4 = do_rag ? ((unsigned)hzr[tid] & 0xffu) : 0xffu;   // +z face pixel
+        // roots into par
+#pragma unroll
+        for (int k = 0; k < C::TZ; k++) {
+            const unsigned id = (P[k >> 2] >> (8 * (k & 3))) & 0xffu;
+            if (id != 0xffu) par[p0 + k * geo.HW] = rl[id];
+        }
+        __syncthreads();
+        // smallest index: candidates differ from their -z, -y, -x neighbours
+        {
+            const uint4 ym = ly > 0 ? colw[tid - 32] : make_uint4(~0u, ~0u, ~0u, ~0u);
+            const unsigned YM[4] = {ym.x, ym.y, ym.z, ym.w};
+#pragma unroll
+            for (int w = 0; w < 4; w++) {
+                const unsigned zm = __funnelshift_l(w > 0 ? P[w - 1] : ~0u, P[w], 8);   // bytes k - 1
+                unsigned xm = __shfl_up_sync(0xffffffffu, P[w], 1);
+                if (lane == 0) xm = ~0u;
+                unsigned cand = __vcmpne4(P[w], zm) & __vcmpne4(P[w], YM[w]) & __vcmpne4(P[w], xm) &
+                                __vcmpne4(P[w], 0xffffffffu);
+                while (cand) {
+                    const int q = (__ffs(cand) - 1) >> 3;
+                    cand &= ~(0xffu << (8 * q));
+                    const int k = 4 * w + q;
+                    atomicMin(rmin + ((P[w] >> (8 * q)) & 0xffu), p0 + k * geo.HW);
+                }
+            }
+        }
+        if (do_rag) {
+            // pass values of the +x, +y, +z pairs of different basins
+            const unsigned *ynw = ly + 1 < C::TY ? (const unsigned *)(colw + tid + 32) : (const unsigned *)yfb + 4 * lane;
+            const unsigned *xfw = (const unsigned *)xfb + 4 * ly;
+            const uint8_t *colb = (const uint8_t *)colw;   // byte k of column c: colb[c * 16 + k]
+            uint16_t *wlst = (uint16_t *)(smem + B::OFF_WL) + ly * B::WL;
+            auto pass = [&](auto matrix) {
+                constexpr bool MATRIX = decltype(matrix)::value;
+                auto note = [&](int ida, int idb, unsigned h) {
+                    const int a = ida < idb ? ida : idb, c2 = ida < idb ? idb : ida;
+                    if (MATRIX) {
+                        unsigned *e = pm + a * B::RM + c2;
+                        if (h < *e) atomicMin(e, h);
+                    } else {
+                        const int ra = rl[a], rb = rl[c2];
+                        smem_edge_insert((unsigned)(ra < rb ? ra : rb), (unsigned)(ra < rb ? rb : ra), h, hk, hv,
+                                         B::EH, keys, vals, slots, ecount, gmask, status);
+                    }
+                };
+                // 0x00 / 0xff bytes -> bits 0..3
+                auto bits = [](unsigned m) { return ((((m >> 7) & 0x01010101u) * 0x01020408u) >> 24) & 0xfu; };
+#pragma unroll
+                for (int w = 0; w < 4; w++) {
+                    // flag the pixels of word w with a boundary in +x, +y or +z
+                    const unsigned zn = __funnelshift_r(P[w], w < 3 ? P[w + 1] : P4, 8);   // bytes k + 1
+                    unsigned xn = __shfl_down_sync(0xffffffffu, P[w], 1);
+                    if (lane == 31) xn = xfw[w];
+                    const unsigned yn = ynw[w];
+                    const unsigned own = __vcmpne4(P[w], 0xffffffffu);
+                    const unsigned fz = bits(__vcmpne4(P[w], zn) & own & __vcmpne4(zn, 0xffffffffu));
+                    const unsigned fy = bits(__vcmpne4(P[w], yn) & own & __vcmpne4(yn, 0xffffffffu));
+                    const unsigned fx = bits(__vcmpne4(P[w], xn) & own & __vcmpne4(xn, 0xffffffffu));
+                    unsigned fa = fx | fy | fz;
+                    // compact them into the warp's list: (directions, k, lane)
+                    const int cnt = __popc(fa);
+                    int inc = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += v;
+                    }
+                    const int total = __shfl_sync(0xffffffffu, inc, 31);
+                    int pos = inc - cnt;
+                    while (fa) {
+                        const int q = __ffs(fa) - 1;
+                        fa &= fa - 1;
+                        const unsigned d = ((fx >> q) & 1u) | (((fy >> q) & 1u) << 1) | (((fz >> q) & 1u) << 2);
+                        wlst[pos++] = (uint16_t)((d << 9) | ((4 * w + q) << 5) | lane);
+                    }
+                    __syncwarp();
+                    // pass values of the listed pairs, every lane busy
+                    for (int e = lane; e < total; e += 32) {
+                        const int it = wlst[e];
+                        const int ls = it & 31, k = (it >> 5) & 15, d = it >> 9;
+                        const int ts = ly * 32 + ls;
+                        const int id = colb[ts * 16 + k];
+                        const int gpos = (k * B::BY + ly) * B::GW + ls;
+                        const unsigned gp = gb[gpos];
+                        if (d & 1) {
+                            const int nid = ls < 31 ? colb[(ts + 1) * 16 + k] : xfb[ly * C::TZ + k];
+                            const unsigned gq = gb[gpos + 1];
+                            note(id, nid, gp > gq ? gp : gq);
+                        }
+                        if (d & 2) {
+                            const int nid = ly + 1 < C::TY ? colb[(ts + 32) * 16 + k] : yfb[ls * C::TZ + k];
+                            const unsigned gq = gb[gpos + B::GW];
+                            note(id, nid, gp > gq ? gp : gq);
+                        }
+                        if (d & 4) {
+                            const int nid = k + 1 < C::TZ ? colb[ts * 16 + k + 1] : (hzr[ts] & 0xff);
+                            const unsigned gq = gb[gpos + GZ];
+                            note(id, nid, gp > gq ? gp : gq);
+                        }
+                    }
+                    __syncwarp();
+                }
+            };
+            if (mode == 0)
+                pass(std::true_type{});
+            else
+                pass(std::false_type{});
+        }
+    } else {
+        __syncthreads();   // edge hash cleared
+        // more than RB basins in the tile: per-pixel loop over roots read from
+        // the global end list
+        auto root_at = [&](bool valid, int c) -> int {
+            return valid ? __ldg(ends + first + (c & (C::NPIX - 1))) : -1;
+        };
+        const bool vy = y + 1 < geo.H;
+        int pid = -1;
+        const int pcol = ly * B::CW + lane, gcol = ly * B::GW + lane;
+        int iz = root_at(col_in && nz > 0, cb[pcol]);
+#pragma unroll 1
+        for (int k = 0; k < nz; k++) {   // trip count uniform in the CTA
+            const int pos = pcol + k * SZ, p = p0 + k * geo.HW;
+            const int id = iz;
+            if (k + 1 < C::TZ) iz = root_at(col_in && k + 1 < nz, cb[pos + SZ]);
+            else iz = do_rag ? hzr[tid] : -1;
+            const int ixm = __shfl_up_sync(0xffffffffu, id, 1);
+            const int iym = ly > 0 ? root_at(col_in, cb[pos - B::CW]) : -1;
+            if (id >= 0) {
+                par[p] = id;
+                if (id != pid && id != iym && (lane == 0 || id != ixm)) atomicMin(mi + id, p);
+            }
+            pid = id;
+            if (!do_rag) continue;
+            int ix = __shfl_down_sync(0xffffffffu, id, 1);
+            if (lane == 31) ix = hxr[ly + C::TY * k];
+            const int iy = ly + 1 < C::TY ? root_at(vy, cb[pos + B::CW]) : hyr[lane + C::TX * k];
+            if (id < 0) continue;
+            const int gpos = gcol + k * GZ;
+            const unsigned gp = gb[gpos];
+            if (ix >= 0 && ix != id) {
+                const unsigned gq = gb[gpos + 1];
+                edge(id, ix, gp > gq ? gp : gq);
+            }
+            if (iy >= 0 && iy != id) {
+                const unsigned gq = gb[gpos + B::GW];
+                edge(id, iy, gp > gq ? gp : gq);
+            }
+            if (iz >= 0 && iz != id) {
+                const unsigned gq = gb[gpos + GZ];
+                edge(id, iz, gp > gq ? gp : gq);
+            }
+        }
+    }
+    __syncthreads();
+    if (mode < 2 && tid < nr && tid < B::RB && rmin[tid] != 0x7fffffff) atomicMin(mi + rl[tid], rmin[tid]);
     if (!do_rag) return;
-    for (int i = tid; i < B::EH; i += C::NT)
-        if (hk[i] != EMPTY_KEY) edge_insert(hk[i], hv[i], keys, vals, slots, ecount, gmask, status);
+    if (mode == 0) {
+        for (int e = tid; e < B::RM * B::RM; e += C::NT) {
+            const unsigned h = pm[e];
+            if (h == 0xffffffffu) continue;
+            const int ra = rl[e / B::RM], rb = rl[e % B::RM];
+            const unsigned lo = (unsigned)(ra < rb ? ra : rb), hi = (unsigned)(ra < rb ? rb : ra);
+            edge_insert(((unsigned long long)lo << 32) | hi, h, keys, vals, slots, ecount, gmask, status);
+        }
+    } else {
+        for (int i = tid; i < B::EH; i += C::NT)
+            if (hk[i] != EMPTY_KEY) edge_insert(hk[i], hv[i], keys, vals, slots, ecount, gmask, status);
+    }
 }
 
 // ---------------------------------------------------------------------------
