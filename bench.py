@@ -47,16 +47,19 @@ FALLBACK_HBM_GBS = 6800.0
 # Algorithmic bytes per voxel of each phase (minimal input + output of the
 # function the phase computes; b = 2 bytes per uint16 sample).
 PHASE_BYTES = {
-    "step1": 2 + 4,              # k_init: read G, write the in-tile path end
-    "rag": 4 + 2 + 4,            # k_label: read path ends and G, write roots
+    "step1": 2 + 4 + 2,          # k_init6: read G, write the arrow (par) and the 16-bit end slot
+    "rag": 2 + 2 + 4,            # k_rag6: read end slots and G, write roots
     "level_write": 4 + 4 * NL,   # k_write_vec: read roots, write NL label planes
     "plateau": 2 + 4,            # k_plateau2 (plateau tiles only)
     "resolve_union": 2 + 4,      # k_resolve2 (plateau tiles only)
     "jump": 4 + 4,               # k_jump2 (plateau tiles only)
 }
-KERNEL_OF_PHASE = {"step1": "k_init", "plateau": "k_plateau2", "resolve_union": "k_resolve2",
-                   "jump": "k_jump2", "compact": "k_rank_*", "rag": "k_label", "levels": "k_levels",
-                   "level_write": "k_write_vec", "cleanup": "k_hash_clear"}
+KERNEL_OF_PHASE = {"step1": "k_init6", "plateau": "k_plateau2", "resolve_union": "k_resolve2",
+                   "jump": "k_jump2", "compact": "k_rank_*", "chase": "k_chase", "rag": "k_rag6",
+                   "levels": "k_levels", "level_write": "k_write_vec", "cleanup": "k_hash_clear"}
+# source file of each kernel (the traffic record is void once it changes)
+KERNEL_SOURCE = {"k_init6": "ws_tiles.cuh", "k_rag6": "ws_tiles.cuh", "k_chase": "ws_tiles.cuh",
+                 "k_write_vec": "ws_tiles.cuh", "k_levels": "ws_kernels.cuh"}
 
 
 def workload_name(side):
@@ -125,21 +128,56 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    kernel source has not changed since it was captured."""
+def _source_sha(kernel):
+    src = os.path.join(ROOT, "paper_2410_08946_gb300", "csrc", KERNEL_SOURCE.get(kernel, "ws_tiles.cuh"))
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def traffic_for(kernel, voxels):
+    """DRAM bytes (read + write) per launch of `kernel` on `voxels` voxels,
+    from the committed ncu record (bytes per voxel of a captured launch), if
+    the kernel's source has not changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_2410_08946_gb300", "csrc", "ws_kernels.cuh")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     ent = rec.get(kernel)
-    if not ent or ent.get("source_sha") != h:
+    if not ent or ent.get("source_sha") != _source_sha(kernel):
         return None
-    return ent.get("bytes_per_launch")
+    return ent["bytes_per_voxel"] * voxels
+
+
+def ingest_ncu(csv_path, voxels):
+    """Writes profiles/traffic.json from an ncu --csv capture with the
+    dram__bytes_read.sum / dram__bytes_write.sum metrics (one or more
+    launches per kernel on a volume of `voxels` voxels)."""
+    import csv
+    per = {}
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(f) if len(r) > 10]
+    hdr = rows[0]
+    for r in rows[1:]:
+        d = dict(zip(hdr, r))
+        name = d["Kernel Name"].split("<")[0].split("(")[0].replace("void ", "").strip().split("::")[-1]
+        if d["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            v = float(d["Metric Value"].replace(",", ""))
+            scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(d.get("Metric Unit", "byte"), 1)
+            per.setdefault((name, d["ID"]), 0.0)
+            per[(name, d["ID"])] += v * scale
+    by = {}
+    for (name, _), v in per.items():
+        by.setdefault(name, []).append(v)
+    out = {}
+    for name, vs in by.items():
+        if name in KERNEL_SOURCE:
+            out[name] = {"bytes_per_voxel": statistics.median(vs) / voxels, "launches": len(vs),
+                         "captured_voxels": voxels, "source_sha": _source_sha(name)}
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+    print(json.dumps(out))
 
 
 def cpu_baseline(side=320):
@@ -353,9 +391,14 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-image batch measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--ingest-ncu", metavar="CSV", help="write profiles/traffic.json from an ncu DRAM capture "
+                    "(dram__bytes_read.sum, dram__bytes_write.sum) of a --side S run, then exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.ingest_ncu:
+        ingest_ncu(args.ingest_ncu, args.side ** 3)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
 
@@ -434,7 +477,7 @@ def main():
     achieved = alg / (dom_ms / 1e3) / 1e9
     kern = KERNEL_OF_PHASE.get(dom, dom)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_for(kern), "kernel": kern, "phase": dom,
+                "traffic": traffic_for(kern, N), "kernel": kern, "phase": dom,
                 "alg_bytes_per_launch": alg, "peak_source": f"{peak_src} (copy, MEASURED_PEAKS.json hbm_gbs)"
                 if peak_src == "measured" else "fallback 6.8 TB/s"}
     path_bytes = (2 + 4 * NL) * N
