@@ -1273,7 +1273,7 @@ template <typename T> struct Rag6Box {
     static constexpr int OFF_COL = OFF_PM + RM * RM * 4;      // uint4 [NT]: packed basin ids of each column
     static constexpr int OFF_XF = OFF_COL + C::NT * 16;       // uint8 [TY][TZ]: ids of the +x face
     static constexpr int OFF_YF = OFF_XF + C::TY * C::TZ;     // uint8 [TX][TZ]: ids of the +y face
-    static constexpr int WL = 128;                            // boundary items per warp and word
+    static constexpr int WL = C::TX * C::TZ;                  // boundary items per warp (every pixel)
     static constexpr int OFF_WL = OFF_YF + C::TX * C::TZ;     // uint16 [NT / 32][WL]
     static constexpr int OFF_HK = (OFF_WL + (C::NT / 32) * WL * 2 + 7) & ~7;   // uint64 [EH]
     static constexpr int OFF_HV = OFF_HK + EH * 8;            // uint32 [EH]
@@ -1542,60 +1542,60 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
                 };
                 // 0x00 / 0xff bytes -> bits 0..3
                 auto bits = [](unsigned m) { return ((((m >> 7) & 0x01010101u) * 0x01020408u) >> 24) & 0xfu; };
+                // flag the column's pixels with a boundary in +x, +y or +z (bit k)
+                unsigned fx = 0, fy = 0, fz = 0;
 #pragma unroll
                 for (int w = 0; w < 4; w++) {
-                    // flag the pixels of word w with a boundary in +x, +y or +z
                     const unsigned zn = __funnelshift_r(P[w], w < 3 ? P[w + 1] : P4, 8);   // bytes k + 1
                     unsigned xn = __shfl_down_sync(0xffffffffu, P[w], 1);
                     if (lane == 31) xn = xfw[w];
                     const unsigned yn = ynw[w];
                     const unsigned own = __vcmpne4(P[w], 0xffffffffu);
-                    const unsigned fz = bits(__vcmpne4(P[w], zn) & own & __vcmpne4(zn, 0xffffffffu));
-                    const unsigned fy = bits(__vcmpne4(P[w], yn) & own & __vcmpne4(yn, 0xffffffffu));
-                    const unsigned fx = bits(__vcmpne4(P[w], xn) & own & __vcmpne4(xn, 0xffffffffu));
-                    unsigned fa = fx | fy | fz;
-                    // compact them into the warp's list: (directions, k, lane)
-                    const int cnt = __popc(fa);
-                    int inc = cnt;
+                    fz |= bits(__vcmpne4(P[w], zn) & own & __vcmpne4(zn, 0xffffffffu)) << (4 * w);
+                    fy |= bits(__vcmpne4(P[w], yn) & own & __vcmpne4(yn, 0xffffffffu)) << (4 * w);
+                    fx |= bits(__vcmpne4(P[w], xn) & own & __vcmpne4(xn, 0xffffffffu)) << (4 * w);
+                }
+                // compact them into the warp's list: (directions, k, lane)
+                unsigned fa = fx | fy | fz;
+                const int cnt = __popc(fa);
+                int inc = cnt;
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int v = __shfl_up_sync(0xffffffffu, inc, o);
-                        if (lane >= o) inc += v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, inc, 31);
+                int pos = inc - cnt;
+                while (fa) {
+                    const int k = __ffs(fa) - 1;
+                    fa &= fa - 1;
+                    const unsigned d = ((fx >> k) & 1u) | (((fy >> k) & 1u) << 1) | (((fz >> k) & 1u) << 2);
+                    wlst[pos++] = (uint16_t)((d << 9) | (k << 5) | lane);
+                }
+                __syncwarp();
+                // pass values of the listed pairs, every lane busy
+                for (int e = lane; e < total; e += 32) {
+                    const int it = wlst[e];
+                    const int ls = it & 31, k = (it >> 5) & 15, d = it >> 9;
+                    const int ts = ly * 32 + ls;
+                    const int id = colb[ts * 16 + k];
+                    const int gpos = (k * B::BY + ly) * B::GW + ls;
+                    const unsigned gp = gb[gpos];
+                    if (d & 1) {
+                        const int nid = ls < 31 ? colb[(ts + 1) * 16 + k] : xfb[ly * C::TZ + k];
+                        const unsigned gq = gb[gpos + 1];
+                        note(id, nid, gp > gq ? gp : gq);
                     }
-                    const int total = __shfl_sync(0xffffffffu, inc, 31);
-                    int pos = inc - cnt;
-                    while (fa) {
-                        const int q = __ffs(fa) - 1;
-                        fa &= fa - 1;
-                        const unsigned d = ((fx >> q) & 1u) | (((fy >> q) & 1u) << 1) | (((fz >> q) & 1u) << 2);
-                        wlst[pos++] = (uint16_t)((d << 9) | ((4 * w + q) << 5) | lane);
+                    if (d & 2) {
+                        const int nid = ly + 1 < C::TY ? colb[(ts + 32) * 16 + k] : yfb[ls * C::TZ + k];
+                        const unsigned gq = gb[gpos + B::GW];
+                        note(id, nid, gp > gq ? gp : gq);
                     }
-                    __syncwarp();
-                    // pass values of the listed pairs, every lane busy
-                    for (int e = lane; e < total; e += 32) {
-                        const int it = wlst[e];
-                        const int ls = it & 31, k = (it >> 5) & 15, d = it >> 9;
-                        const int ts = ly * 32 + ls;
-                        const int id = colb[ts * 16 + k];
-                        const int gpos = (k * B::BY + ly) * B::GW + ls;
-                        const unsigned gp = gb[gpos];
-                        if (d & 1) {
-                            const int nid = ls < 31 ? colb[(ts + 1) * 16 + k] : xfb[ly * C::TZ + k];
-                            const unsigned gq = gb[gpos + 1];
-                            note(id, nid, gp > gq ? gp : gq);
-                        }
-                        if (d & 2) {
-                            const int nid = ly + 1 < C::TY ? colb[(ts + 32) * 16 + k] : yfb[ls * C::TZ + k];
-                            const unsigned gq = gb[gpos + B::GW];
-                            note(id, nid, gp > gq ? gp : gq);
-                        }
-                        if (d & 4) {
-                            const int nid = k + 1 < C::TZ ? colb[ts * 16 + k + 1] : (hzr[ts] & 0xff);
-                            const unsigned gq = gb[gpos + GZ];
-                            note(id, nid, gp > gq ? gp : gq);
-                        }
+                    if (d & 4) {
+                        const int nid = k + 1 < C::TZ ? colb[ts * 16 + k + 1] : (hzr[ts] & 0xff);
+                        const unsigned gq = gb[gpos + GZ];
+                        note(id, nid, gp > gq ? gp : gq);
                     }
-                    __syncwarp();
                 }
             };
             if (mode == 0)
