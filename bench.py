@@ -229,7 +229,6 @@ def run_reference(args):
 def _pool_2d(seed):
     """4096^2 uint8 blob gradient (32 blobs per 256^2, the small-image density):
     the images of the batch and of the request stream are crops of it."""
-    import oracle  # noqa: F401  (the gradient of the pool is computed on the GPU below)
     from paper_2410_08946_gb300 import synth
     return synth.blob_image(4096, 4096, 8192, seed)
 
