@@ -180,6 +180,24 @@ def ingest_ncu(csv_path, voxels):
     print(json.dumps(out))
 
 
+def host_link_gbs(torch, nbytes=4 << 30):
+    """Host <-> device copy bandwidth of pinned memory (4 GiB each way)."""
+    n = nbytes // 4
+    dev = torch.empty(n, dtype=torch.int32, device="cuda")
+    host = torch.empty(n, dtype=torch.int32).pin_memory()
+    out = {}
+    for name, dst, src in (("d2h", host, dev), ("h2d", dev, host)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(2):
+            dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        out[name] = 2 * nbytes / (time.perf_counter() - t0) / 1e9
+    del dev, host
+    return out
+
+
 def cpu_baseline(side=320):
     """The oracle as it stands (one thread) on a bounded sample volume."""
     import oracle
@@ -511,6 +529,11 @@ def main():
         line["e2e"] = {"value": N * world / e2e_s / 1e9, "unit": "Gvox/s", "ms_per_step": e2e_s * 1e3,
                        "h2d_bytes_per_step": int(N * 2), "d2h_bytes_per_step": int(NL * N * 4 + NL * 4)}
         del grad_h, levels_h
+        link = host_link_gbs(torch)
+        line["e2e"]["host_link_gbs"] = link
+        # the copies alone at the measured link speed: the end-to-end ceiling
+        copy_s = N * 2 / (link["h2d"] * 1e9) + NL * N * 4 / (link["d2h"] * 1e9)
+        line["e2e"]["copy_bound_gvox_s"] = N / copy_s / 1e9
     if world == 1 and not args.no_batch:
         del levels_d
         torch.cuda.empty_cache()

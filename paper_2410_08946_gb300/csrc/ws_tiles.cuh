@@ -462,12 +462,14 @@ template <typename T> struct Init6Box {
 
 // Step I on the thread's column (z = 0..TZ-1): in-tile pointers into nx
 // (ends point at themselves), the arrow into par, states into stb (two bits
-// per pixel), ends into endb.  CHECK = false for a tile whose halo lies
-// inside the image.
+// per pixel), ends into endb, strict minima into minb; mi = INT_MAX for every
+// pixel that can be a root.  CHECK = false for a tile whose halo lies inside
+// the image.
 template <typename T, bool CHECK>
-__device__ __forceinline__ void init6_step1(const T *gs, int *nx, int32_t *par, const int *lo_tab, const int *go_tab,
-                                            int tid, int lx, int ly, int h0, int p0, int x, int y, int z0,
-                                            const Geo &geo, unsigned &stb, unsigned &endb, int &plateau)
+__device__ __forceinline__ void init6_step1(const T *gs, int *nx, int32_t *par, int32_t *mi, const int *lo_tab,
+                                            const int *go_tab, int tid, int lx, int ly, int h0, int p0, int x, int y,
+                                            int z0, const Geo &geo, unsigned &stb, unsigned &endb, unsigned &minb,
+                                            int &plateau)
 {
     using C = TC<6>;
     using B = InitBox<T, 6>;
@@ -508,9 +510,11 @@ __device__ __forceinline__ void init6_step1(const T *gs, int *nx, int32_t *par, 
         const int nn = has ? n : 0;
         nx[i] = follow ? i + lo_tab[nn] : i;
         if (in) par[p] = st0 ? p + go_tab[nn] : p;
+        if (in && !st0) mi[p] = 0x7fffffff;   // a root candidate: its smallest index is taken later
         plateau |= state == STP;
         stb |= (unsigned)state << (2 * k);
         endb |= (unsigned)(in && !follow) << k;
+        minb |= (unsigned)(state == ST1) << k;
     }
 }
 
@@ -603,20 +607,30 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
         const int p0 = base + (z0 * geo.H + y) * geo.W + x;   // global index of (lx, ly, z = 0)
         unsigned stb = 0;   // pixel states, two bits each
         unsigned endb = 0;  // bit k: pixel k of the column ends its in-tile path
+        unsigned minb = 0;  // bit k: pixel k of the column is a strict minimum
         int plateau = 0;
         if (interior)
-            init6_step1<T, false>(gs, nx, par, lo_tab, go_tab, tid, lx, ly, h0, p0, x, y, z0, geo, stb, endb,
-                                  plateau);
+            init6_step1<T, false>(gs, nx, par, mi, lo_tab, go_tab, tid, lx, ly, h0, p0, x, y, z0, geo, stb, endb,
+                                  minb, plateau);
         else
-            init6_step1<T, true>(gs, nx, par, lo_tab, go_tab, tid, lx, ly, h0, p0, x, y, z0, geo, stb, endb,
-                                 plateau);
-        // number the ends: warp counts, a warp scan, one span of the global
-        // end list per tile (its offset is needed only at the end)
+            init6_step1<T, true>(gs, nx, par, mi, lo_tab, go_tab, tid, lx, ly, h0, p0, x, y, z0, geo, stb, endb,
+                                 minb, plateau);
+        // the strict minima are roots: list them
+        for (unsigned m = minb; m; m &= m - 1)
+            roots[atomicAdd(counters + CNT_ROOTS, 1)] = p0 + (__ffs(m) - 1) * HW;
+        // number the ends: the thread's ends get consecutive slots after those
+        // of the lanes before it (warp scan) and of the warps before it
+        int lpre;
         {
-            int wc = 0;
+            const int ne = __popc(endb);
+            int inc = ne;
 #pragma unroll
-            for (int k = 0; k < C::TZ; k++) wc += __popc(__ballot_sync(0xffffffffu, (endb >> k) & 1u));
-            if (lane == 0) wbase[ly] = wc;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += u;
+            }
+            lpre = inc - ne;
+            if (lane == 31) wbase[ly] = inc;
         }
         __syncthreads();  // the gradient box of stage s is no longer read
         if (TMA && tid == 0 && t + 2 * G < b.ntiles) init_issue<T, 6, TMA>(&tm, gs, &bars[s], b, t + 2 * G);
@@ -634,15 +648,10 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             if (lane == 0) first = atomicAdd(counters + CNT_ENDS, nend);
         }
         __syncthreads();
-        {
-            int run = wbase[ly];
-#pragma unroll
-            for (int k = 0; k < C::TZ; k++) {
-                const bool e = (endb >> k) & 1u;
-                const unsigned bb = __ballot_sync(0xffffffffu, e);
-                if (e) slotof[tid + k * C::NT] = (uint16_t)(run + __popc(bb & ((1u << lane) - 1u)));
-                run += __popc(bb);
-            }
+        const int slot0 = wbase[ly] + lpre;   // the slot of this thread's first end
+        for (unsigned m = endb; m; m &= m - 1) {
+            const int k = __ffs(m) - 1;
+            slotof[tid + k * C::NT] = (uint16_t)(slot0 + __popc(endb & ((1u << k) - 1u)));
         }
 
         // step III inside the tile: pointer doubling, two hops a round.  A
@@ -679,24 +688,13 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             const int fst = s_first;
 #pragma unroll
             for (int k = 0; k < C::TZ; k++) {
-                const unsigned sk = (stb >> (2 * k)) & 3u;
-                if (sk == (unsigned)STOUT) continue;
-                const int p = p0 + k * HW, slot = slotof[cur[k]];   // cur[k]: the end (32 rounds always suffice)
-                code[p] = (uint16_t)slot;
-                if ((endb >> k) & 1u) ends[fst + slot] = p;
-                if (sk != (unsigned)ST0) mi[p] = 0x7fffffff;
+                if (((stb >> (2 * k)) & 3u) == (unsigned)STOUT) continue;
+                code[p0 + k * HW] = slotof[cur[k]];   // cur[k]: the end (32 rounds always suffice)
             }
-        }
-        // list the strict minima (roots known now)
-#pragma unroll
-        for (int k = 0; k < C::TZ; k++) {
-            const bool isr = ((stb >> (2 * k)) & 3u) == (unsigned)ST1;
-            const unsigned bb = __ballot_sync(0xffffffffu, isr);
-            if (!bb) continue;
-            int rb = 0;
-            if (lane == 0) rb = atomicAdd(counters + CNT_ROOTS, __popc(bb));
-            rb = __shfl_sync(0xffffffffu, rb, 0);
-            if (isr) roots[rb + __popc(bb & ((1u << lane) - 1u))] = p0 + k * HW;
+            for (unsigned m = endb; m; m &= m - 1) {
+                const int k = __ffs(m) - 1;
+                ends[fst + slot0 + __popc(endb & ((1u << k) - 1u))] = p0 + k * HW;
+            }
         }
         if (__syncthreads_or(plateau)) {
 #pragma unroll
