@@ -443,10 +443,9 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
 //   - a pixel whose arrow leaves the tile, a minimum and a plateau pixel end
 //     their in-tile paths; the ends of tile t get slots 0..n-1, ends[first +
 //     slot] is the end pixel and tends[t] = (first, n);
-//   - pointer doubling (ends point at themselves; two hops a round, a
-//     thread's column of pointers in registers, every load of a round issued
-//     before any store) takes every pixel to its end: code[p] is the slot of
-//     p's end.
+//   - pointer doubling (ends point at themselves; a thread's column of
+//     pointers in registers, every load of a round issued before any store)
+//     takes every pixel to its end: code[p] is the slot of p's end.
 // Step I picks the lowest neighbour with one integer minimum over packed
 // keys (value << 3 | 7 - n, so that ties go to the later neighbour n in
 // ascending index order) and has no divergent branches.
@@ -654,9 +653,9 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             slotof[tid + k * C::NT] = (uint16_t)(slot0 + __popc(endb & ((1u << k) - 1u)));
         }
 
-        // step III inside the tile: pointer doubling, two hops a round.  A
-        // value read while its owner is updating it is the old or the new
-        // pointer of a pixel further down the same path, or the path's end.
+        // step III inside the tile: pointer doubling.  A value read while its
+        // owner is updating it is the old or the new pointer of a pixel further
+        // down the same path, or the path's end.
         int cur[C::TZ];
 #pragma unroll
         for (int k = 0; k < C::TZ; k++) cur[k] = nx[tid + k * C::NT];
@@ -668,8 +667,6 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
                 int nxt[8];
 #pragma unroll
                 for (int k = 0; k < 8; k++) nxt[k] = vnx[cur[h + k]];
-#pragma unroll
-                for (int k = 0; k < 8; k++) nxt[k] = vnx[nxt[k]];
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
                     vnx[tid + (h + k) * C::NT] = nxt[k];
