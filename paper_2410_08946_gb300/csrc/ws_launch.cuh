@@ -188,7 +188,8 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
         PhaseScope ps(c, PH_RESOLVE, s);
         const int grid = b.ntiles < c->num_sms * 8 ? b.ntiles : c->num_sms * 8;
         k_resolve2<T, CONN><<<grid, C::NT, 0, s>>>(b, w.par, w.dist, w.plat, w.tlist, w.counters, c->status);
-        c->launches += 1;
+        k_union2<T, CONN><<<grid, NTHR, 0, s>>>(b, w.par, w.dist, w.plat, w.tlist, w.counters, c->status);
+        c->launches += 2;
     }
     if ((e = reset_barrier(c, s)) != cudaSuccess) return set_cuda_error(c, e, "memset");
     {

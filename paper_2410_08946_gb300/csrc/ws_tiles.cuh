@@ -185,6 +185,12 @@ __device__ __forceinline__ int tile_of(const TileGeo &tg, int x, int y, int z)
     return ((z / tg.TZ) * tg.nty + y / tg.TY) * tg.ntx + x / tg.TX;
 }
 
+// the same with the tile sizes of CONN known at compile time (shifts)
+template <int CONN> __device__ __forceinline__ int tile_of_c(const TileGeo &tg, int x, int y, int z)
+{
+    return ((z / TT<CONN>::TZ) * tg.nty + y / TT<CONN>::TY) * tg.ntx + x / TT<CONN>::TX;
+}
+
 // state codes kept in registers by k_init
 enum : int { ST0 = 0, ST1 = 1, STP = 2, STOUT = 3 };
 
@@ -757,7 +763,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const Batch b, int32_
                     gs[i] = (int)g[q];
                     // a pixel of a tile without plateau pixels that is equal to a
                     // plateau neighbour has a lower neighbour: distance 0
-                    ds[i] = plat[tc.tile0 + tile_of(tc.tg, x, y, z)] ? __ldcg(dist + tc.base + q) : 0;
+                    ds[i] = plat[tc.tile0 + tile_of_c<CONN>(tc.tg, x, y, z)] ? __ldcg(dist + tc.base + q) : 0;
                 } else {
                     gs[i] = -1;
                     ds[i] = INF_D;
@@ -840,6 +846,41 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const Batch b, int32_
 // k_resolve2: step II pointer choice and step IV Union on plateau tiles
 // ---------------------------------------------------------------------------
 
+// find / union in a tile-local union-find (the smaller local index is the
+// root; atomicCAS links a root to a smaller root)
+__device__ __forceinline__ int lu_find(int *lab, int a)
+{
+    volatile int *v = lab;
+    for (int it = 0; it < (1 << 16); it++) {
+        const int b = v[a];
+        if (b == a) return a;
+        const int c = v[b];
+        if (c == b) return b;
+        v[a] = c;   // path halving
+        a = c;
+    }
+    return a;
+}
+
+__device__ __forceinline__ void lu_union(int *lab, int a, int b)
+{
+    for (int it = 0; it < (1 << 16); it++) {
+        a = lu_find(lab, a);
+        b = lu_find(lab, b);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(lab + a, a, b) == a) return;
+    }
+}
+
+// Step II pointer choice on the plateau tiles, and step IV inside each tile:
+// the minimal-plateau pixels of a tile are joined in a shared-memory union-find
+// and each points at its component's smallest pixel (k_union2 joins the
+// components across tile borders).
 template <typename T, int CONN>
 __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const Batch b, int32_t *par, const int32_t *__restrict__ dist,
                                                            const uint8_t *__restrict__ plat,
@@ -847,6 +888,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const Batch b, int32_
                                                            const int32_t *counters, DevStatus *status)
 {
     using C = TC<CONN>;
+    __shared__ int lab[C::NPIX];   // tile-local union-find of the minimal-plateau pixels (-1: other pixel)
     const int ntl = counters[CNT_TILES];
     for (int j = blockIdx.x; j < ntl; j += gridDim.x) {
         const TileCtx tc = tile_ctx<CONN>(b, tlist[j]);
@@ -855,36 +897,96 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const Batch b, int32_
         for (int i = threadIdx.x; i < C::NPIX; i += C::NT) {
             const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
             const int x = tc.x0 + lx, y = tc.y0 + ly, z = tc.z0 + lz;
+            int l = -1;
+            if (x < geo.W && y < geo.H && z < geo.D) {
+                const int p = (z * geo.H + y) * geo.W + x;
+                const int d = dist[tc.base + p];
+                if (d >= INF_D) {
+                    l = i;
+                } else if (d > 0) {
+                    const unsigned gp = g[p];
+                    int best = -1;
+#pragma unroll
+                    for (int n = 0; n < Nb<CONN>::n; n++) {
+                        const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
+                        if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
+                        const int q = (zz * geo.H + yy) * geo.W + xx;
+                        if (g[q] != gp) continue;
+                        const int dq = plat[tc.tile0 + tile_of_c<CONN>(tc.tg, xx, yy, zz)] ? dist[tc.base + q] : 0;
+                        if (dq == d - 1 && q > best) best = q;
+                    }
+                    if (best < 0) {
+                        record_error(status, DEV_NONCONVERGED, 7);
+                        best = p;
+                    }
+                    par[tc.base + p] = tc.base + best;
+                }
+            }
+            lab[i] = l;
+        }
+        __syncthreads();
+        // unions with the forward neighbours inside the tile
+        for (int i = threadIdx.x; i < C::NPIX; i += C::NT) {
+            if (lab[i] < 0) continue;
+            const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+            const unsigned gp = g[((tc.z0 + lz) * geo.H + tc.y0 + ly) * geo.W + tc.x0 + lx];
+#pragma unroll
+            for (int n = Half<CONN>::first; n < Nb<CONN>::n; n++) {
+                const int xx = lx + Nb<CONN>::dx(n), yy = ly + Nb<CONN>::dy(n), zz = lz + Nb<CONN>::dz(n);
+                if (xx < 0 || xx >= C::TX || yy < 0 || yy >= C::TY || zz < 0 || zz >= C::TZ) continue;
+                const int jn = (zz * C::TY + yy) * C::TX + xx;
+                if (lab[jn] < 0) continue;
+                if (g[((tc.z0 + zz) * geo.H + tc.y0 + yy) * geo.W + tc.x0 + xx] == gp) lu_union(lab, i, jn);
+            }
+        }
+        __syncthreads();
+        // every minimal-plateau pixel points at its in-tile component's smallest pixel
+        for (int i = threadIdx.x; i < C::NPIX; i += C::NT) {
+            if (lab[i] < 0) continue;
+            const int r = lu_find(lab, i);
+            const int rx = r % C::TX, ry = (r / C::TX) % C::TY, rz = r / (C::TX * C::TY);
+            const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+            par[tc.base + ((tc.z0 + lz) * geo.H + tc.y0 + ly) * geo.W + tc.x0 + lx] =
+                tc.base + ((tc.z0 + rz) * geo.H + tc.y0 + ry) * geo.W + tc.x0 + rx;
+        }
+        __syncthreads();   // lab is reused by the next tile
+    }
+}
+
+// Step IV across tile borders: every minimal-plateau pixel of a plateau tile
+// is joined (global union-find, smaller index as root) with its forward
+// neighbours of equal value that are minimal-plateau pixels of other tiles.
+template <typename T, int CONN>
+__global__ void __launch_bounds__(NTHR) k_union2(const Batch b, int32_t *par, const int32_t *__restrict__ dist,
+                                               const uint8_t *__restrict__ plat, const int32_t *__restrict__ tlist,
+                                               const int32_t *counters, DevStatus *status)
+{
+    using C = TC<CONN>;
+    const int ntl = counters[CNT_TILES];
+    for (int j = blockIdx.x; j < ntl; j += gridDim.x) {
+        const TileCtx tc = tile_ctx<CONN>(b, tlist[j]);
+        const Geo &geo = tc.geo;
+        const T *g = (const T *)tc.grad;
+        for (int i = threadIdx.x; i < C::NPIX; i += NTHR) {
+            const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+            // only pixels with a forward neighbour outside the tile
+            const bool border = lx == C::TX - 1 || ly == C::TY - 1 || (C::D3 && lz == C::TZ - 1) ||
+                                (CONN == 8 && lx == 0);
+            if (!border) continue;
+            const int x = tc.x0 + lx, y = tc.y0 + ly, z = tc.z0 + lz;
             if (x >= geo.W || y >= geo.H || z >= geo.D) continue;
             const int p = (z * geo.H + y) * geo.W + x;
-            const int d = dist[tc.base + p];
-            if (d <= 0) continue;   // state 0 or minimum
+            if (dist[tc.base + p] < INF_D) continue;
             const unsigned gp = g[p];
-            if (d < INF_D) {
-                int best = -1;
 #pragma unroll
-                for (int n = 0; n < Nb<CONN>::n; n++) {
-                    const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
-                    if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
-                    const int q = (zz * geo.H + yy) * geo.W + xx;
-                    if (g[q] != gp) continue;
-                    const int dq = plat[tc.tile0 + tile_of(tc.tg, xx, yy, zz)] ? dist[tc.base + q] : 0;
-                    if (dq == d - 1 && q > best) best = q;
-                }
-                if (best < 0) {
-                    record_error(status, DEV_NONCONVERGED, 7);
-                    best = p;
-                }
-                par[tc.base + p] = tc.base + best;
-            } else {
-#pragma unroll
-                for (int n = Half<CONN>::first; n < Nb<CONN>::n; n++) {
-                    const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
-                    if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
-                    if (!plat[tc.tile0 + tile_of(tc.tg, xx, yy, zz)]) continue;
-                    const int q = (zz * geo.H + yy) * geo.W + xx;
-                    if (dist[tc.base + q] >= INF_D && g[q] == gp) uf_union(par, tc.base + p, tc.base + q, status);
-                }
+            for (int n = Half<CONN>::first; n < Nb<CONN>::n; n++) {
+                const int ax = lx + Nb<CONN>::dx(n), ay = ly + Nb<CONN>::dy(n), az = lz + Nb<CONN>::dz(n);
+                if (ax >= 0 && ax < C::TX && ay >= 0 && ay < C::TY && az >= 0 && az < C::TZ) continue;   // in the tile
+                const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
+                if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz < 0 || zz >= geo.D) continue;
+                if (!plat[tc.tile0 + tile_of_c<CONN>(tc.tg, xx, yy, zz)]) continue;
+                const int q = (zz * geo.H + yy) * geo.W + xx;
+                if (dist[tc.base + q] >= INF_D && g[q] == gp) uf_union(par, tc.base + p, tc.base + q, status);
             }
         }
     }
