@@ -416,7 +416,10 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
                 roots[rb + __popc(bb & ((1u << lane) - 1u))] = base + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
             }
         }
-        if (__syncthreads_or(plateau)) {
+        // dist: on plateau tiles the start of step II; in 2D on every tile
+        // (k_jump2 tells plateau pixels from the others by it)
+        const bool pl = __syncthreads_or(plateau);
+        if (pl || !C::D3) {
 #pragma unroll
             for (int k = 0; k < C::PER; k++) {
                 if (st[k] == STOUT) continue;
@@ -425,6 +428,8 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ C
                 const int p = base + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
                 dist[p] = st[k] == ST0 ? 0 : (st[k] == ST1 ? -2 : INF_D);
             }
+        }
+        if (pl) {
             if (tid == 0) {
                 plat[t] = 1;
                 act[t] = 1;
@@ -1004,30 +1009,32 @@ __global__ void __launch_bounds__(NTHR) k_jump2(const Batch b, int32_t *par, con
 {
     using C = TC<CONN>;
     const int tid = threadIdx.x, lane = tid & 31;
-    const long long total = (long long)counters[CNT_TILES] * C::NPIX;
-    const long long stride = (long long)gridDim.x * NTHR;
-    const long long iters = (total + stride - 1) / stride;
+    const int ntl = counters[CNT_TILES];
     for (int r = 0;; r++) {
         if (blockIdx.x == 0 && tid == 0) status->changed[(r + 1) % 3] = 0;
         int ch = 0;
-        for (long long it = 0; it < iters; it++) {
-            const long long e = it * stride + (long long)blockIdx.x * NTHR + tid;
-            if (e >= total) continue;
-            const TileCtx tc = tile_ctx<CONN>(b, tlist[e / C::NPIX]);
-            const int i = (int)(e % C::NPIX);
-            const int x = tc.x0 + i % C::TX, y = tc.y0 + (i / C::TX) % C::TY, z = tc.z0 + i / (C::TX * C::TY);
-            if (x >= tc.geo.W || y >= tc.geo.H || z >= tc.geo.D) continue;
-            const int p = tc.base + (z * tc.geo.H + y) * tc.geo.W + x;
-            const int l0 = __ldcg(par + p);
-            int l = l0;
-            for (int k = 0; k < RR; k++) {
-                const int l2 = __ldcg(par + l);
-                if (l2 == l) break;
-                l = l2;
-            }
-            if (l != l0) {
-                __stcg(par + p, l);
-                ch = 1;
+        for (int j = blockIdx.x; j < ntl; j += gridDim.x) {   // one tile at a time per block
+            const TileCtx tc = tile_ctx<CONN>(b, tlist[j]);
+            for (int i = tid; i < C::NPIX; i += NTHR) {
+                const int x = tc.x0 + i % C::TX, y = tc.y0 + (i / C::TX) % C::TY, z = tc.z0 + i / (C::TX * C::TY);
+                if (x >= tc.geo.W || y >= tc.geo.H || z >= tc.geo.D) continue;
+                const int p = tc.base + (z * tc.geo.H + y) * tc.geo.W + x;
+                // 2D: only plateau pixels jump, and only across plateau pixels
+                // (the rest of a path is chased tile by tile later; dist is
+                // valid on every tile).  3D: every pixel of a plateau tile jumps.
+                if (!C::D3 && dist[p] <= 0) continue;
+                const int l0 = __ldcg(par + p);
+                int l = l0;
+                for (int k = 0; k < RR; k++) {
+                    if (!C::D3 && dist[l] <= 0) break;
+                    const int l2 = __ldcg(par + l);
+                    if (l2 == l) break;
+                    l = l2;
+                }
+                if (l != l0) {
+                    __stcg(par + p, l);
+                    ch = 1;
+                }
             }
         }
         const unsigned bl = __ballot_sync(0xffffffffu, ch);
@@ -1044,25 +1051,26 @@ __global__ void __launch_bounds__(NTHR) k_jump2(const Batch b, int32_t *par, con
         }
     }
     // roots of minimal plateaux
-    for (long long it = 0; it < iters; it++) {
-        const long long e = it * stride + (long long)blockIdx.x * NTHR + tid;
-        bool isr = false;
-        int p = 0;
-        if (e < total) {
-            const TileCtx tc = tile_ctx<CONN>(b, tlist[e / C::NPIX]);
-            const int i = (int)(e % C::NPIX);
-            const int x = tc.x0 + i % C::TX, y = tc.y0 + (i / C::TX) % C::TY, z = tc.z0 + i / (C::TX * C::TY);
-            if (x < tc.geo.W && y < tc.geo.H && z < tc.geo.D) {
-                p = tc.base + (z * tc.geo.H + y) * tc.geo.W + x;
-                isr = dist[p] >= INF_D && __ldcg(par + p) == p;
+    for (int j = blockIdx.x; j < ntl; j += gridDim.x) {
+        const TileCtx tc = tile_ctx<CONN>(b, tlist[j]);
+        for (int i0 = 0; i0 < C::NPIX; i0 += NTHR) {   // warp-uniform trip count
+            const int i = i0 + tid;
+            bool isr = false;
+            int p = 0;
+            if (i < C::NPIX) {
+                const int x = tc.x0 + i % C::TX, y = tc.y0 + (i / C::TX) % C::TY, z = tc.z0 + i / (C::TX * C::TY);
+                if (x < tc.geo.W && y < tc.geo.H && z < tc.geo.D) {
+                    p = tc.base + (z * tc.geo.H + y) * tc.geo.W + x;
+                    isr = dist[p] >= INF_D && __ldcg(par + p) == p;
+                }
             }
+            const unsigned bl = __ballot_sync(0xffffffffu, isr);
+            if (!bl) continue;
+            int rb = 0;
+            if (lane == 0) rb = atomicAdd(counters + CNT_ROOTS, __popc(bl));
+            rb = __shfl_sync(0xffffffffu, rb, 0);
+            if (isr) roots[rb + __popc(bl & ((1u << lane) - 1u))] = p;
         }
-        const unsigned bl = __ballot_sync(0xffffffffu, isr);
-        if (!bl) continue;
-        int rb = 0;
-        if (lane == 0) rb = atomicAdd(counters + CNT_ROOTS, __popc(bl));
-        rb = __shfl_sync(0xffffffffu, rb, 0);
-        if (isr) roots[rb + __popc(bl & ((1u << lane) - 1u))] = p;
     }
 }
 
