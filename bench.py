@@ -407,7 +407,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-image batch measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--ingest-ncu", metavar="CSV", help="write profiles/traffic.json from an ncu DRAM capture "
                     "(dram__bytes_read.sum, dram__bytes_write.sum) of a --side S run, then exit")
     args = ap.parse_args()
