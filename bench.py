@@ -48,8 +48,8 @@ FALLBACK_HBM_GBS = 6800.0
 # function the phase computes; b = 2 bytes per uint16 sample).
 PHASE_BYTES = {
     "step1": 2 + 4 + 2,          # k_init6: read G, write the arrow (par) and the 16-bit end slot
-    "rag": 2 + 2 + 4,            # k_rag6: read end slots and G, write roots
-    "level_write": 4 + 4 * NL,   # k_write_vec: read roots, write NL label planes
+    "rag": 2 + 2,                # k_rag6: read end slots and G (per-basin and per-pair results only)
+    "level_write": 2 + 4 * NL,   # k_write6: read end slots, write NL label planes
     "plateau": 2 + 4,            # k_plateau2 (plateau tiles only)
     "resolve_union": 2 + 4,      # k_resolve2 (plateau tiles only)
     "jump": 4 + 4,               # k_jump2 (plateau tiles only)
@@ -59,7 +59,7 @@ KERNEL_OF_PHASE = {"step1": "k_init6", "plateau": "k_plateau2", "resolve_union":
                    "levels": "k_levels", "level_write": "k_write_vec", "cleanup": "k_hash_clear"}
 # source file of each kernel (the traffic record is void once it changes)
 KERNEL_SOURCE = {"k_init6": "ws_tiles.cuh", "k_rag6": "ws_tiles.cuh", "k_chase": "ws_tiles.cuh",
-                 "k_write_vec": "ws_tiles.cuh", "k_levels": "ws_kernels.cuh"}
+                 "k_write6": "ws_tiles.cuh", "k_levels": "ws_kernels.cuh"}
 
 
 def workload_name(side):

@@ -292,10 +292,30 @@ template <int CONN> static void batch_descs(int n, const Geo *geos, const ws_ite
 }
 
 // One pass writing level 0 (canonical ids) and levels 1..NL-1 of one image.
-static inline ws_status run_write(ws_context *c, const Geo &geo, int NL, int32_t *out, cudaStream_t s)
+static inline ws_status run_write(ws_context *c, const Geo &geo, int NL, int32_t *out, bool d3, cudaStream_t s)
 {
     Workspace &w = c->w;
     PhaseScope ps(c, PH_LEVEL_WRITE, s);
+    if (d3) {   // 3D: from the voxels' end slots, tile by tile
+        Batch b{};
+        b.one.W = geo.W;
+        b.one.H = geo.H;
+        b.one.D = geo.D;
+        b.one.HW = geo.HW;
+        b.one.N = geo.N;
+        b.one.out = out;
+        const TileGeo tg = tiles_for<6>(geo);
+        b.one.ntx = tg.ntx;
+        b.one.nty = tg.nty;
+        b.one.ntz = tg.ntz;
+        b.ntiles = tg.ntiles;
+        b.npix = geo.N;
+        k_write6<<<b.ntiles, TT<6>::NT, 0, s>>>(b, w.code, w.ends, w.tends, w.aux, w.gmap, w.kmax, NL, nullptr,
+                                                w.counters + CNT_ROOTS);
+        c->launches += 1;
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "write launch");
+    }
     const bool vec = (geo.N % 4 == 0) && (((uintptr_t)out & 15) == 0);
     const int grid = pixel_grid(c, vec ? geo.N / 4 : geo.N);
     if (vec)
@@ -340,7 +360,7 @@ template <typename T, int CONN> static ws_status run_watershed(ws_context *c, co
     const Batch b = single_batch<CONN>(geo, grad, labels, nullptr);
     ws_status st = run_core<T, CONN>(c, b, false, s);
     if (st != WS_OK) return st;
-    if ((st = run_write(c, geo, 1, labels, s)) != WS_OK) return st;
+    if ((st = run_write(c, geo, 1, labels, CONN == 6, s)) != WS_OK) return st;
     if (count) {
         k_copy_int<<<1, 32, 0, s>>>(c->w.counters + CNT_ROOTS, count);
         c->launches += 1;
@@ -364,7 +384,7 @@ template <typename T, int CONN> static ws_status run_segment(ws_context *c, cons
         k_copy_int<<<1, 32, 0, s>>>(w.counters + CNT_ROOTS, counts);
         c->launches += 1;
     }
-    return run_write(c, geo, NL, levels, s);
+    return run_write(c, geo, NL, levels, CONN == 6, s);
 }
 
 // A batch of images (same dtype and connectivity) in one launch per phase:
@@ -405,8 +425,12 @@ template <typename T, int CONN> static ws_status run_segment_batch(ws_context *c
     if (NL > 1 && (st = run_levels(c, NL, w.aux, w.counters + CNT_ROOTS, w.lcount, s)) != WS_OK) return st;
     {
         PhaseScope ps(c, PH_LEVEL_WRITE, s);
-        k_write_batch<<<pixel_grid(c, b.npix), NTHR, 0, s>>>(b, w.par, w.aux, w.gmap, w.kmax, NL, w.rbase,
-                                                             w.counters + CNT_ROOTS);
+        if (CONN == 6)   // 3D: from the voxels' end slots, tile by tile
+            k_write6<<<b.ntiles, TT<6>::NT, 0, s>>>(b, w.code, w.ends, w.tends, w.aux, w.gmap, w.kmax, NL, w.rbase,
+                                                    w.counters + CNT_ROOTS);
+        else
+            k_write_batch<<<pixel_grid(c, b.npix), NTHR, 0, s>>>(b, w.par, w.aux, w.gmap, w.kmax, NL, w.rbase,
+                                                                 w.counters + CNT_ROOTS);
         k_counts_batch<<<(n + NTHR - 1) / NTHR, NTHR, 0, s>>>(b, w.gmap, w.kmax, NL, w.rbase, w.lcount);
         c->launches += 2;
     }

@@ -1400,8 +1400,8 @@ __device__ __forceinline__ int face_root(bool valid, int c, int2 e, const int32_
     return __ldg(ends + e.x + c);
 }
 
-// Per 3D tile, one z column per thread: the root of every pixel into par,
-// the smallest pixel index per basin, and with do_rag Alg. 5 step V on the
+// Per 3D tile, one z column per thread: the smallest pixel index per basin,
+// and with do_rag Alg. 5 step V on the
 // +x, +y, +z pixel pairs: the pass value max(G(p), G(q)) of every pair of
 // different basins, min-reduced per pair.
 //   - The tile's basins (of its slots and of the forward faces) get 8-bit
@@ -1600,12 +1600,6 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
         }
         colw[tid] = make_uint4(P[0], P[1], P[2], P[3]);
         const unsigned P4 = do_rag ? ((unsigned)hzr[tid] & 0xffu) : 0xffu;   // +z face pixel
-        // roots into par
-#pragma unroll
-        for (int k = 0; k < C::TZ; k++) {
-            const unsigned id = (P[k >> 2] >> (8 * (k & 3))) & 0xffu;
-            if (id != 0xffu) par[p0 + k * geo.HW] = rl[id];
-        }
         __syncthreads();
         // smallest index: candidates differ from their -z, -y, -x neighbours
         {
@@ -1727,10 +1721,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
             else iz = do_rag ? hzr[tid] : -1;
             const int ixm = __shfl_up_sync(0xffffffffu, id, 1);
             const int iym = ly > 0 ? root_at(col_in, cb[pos - B::CW]) : -1;
-            if (id >= 0) {
-                par[p] = id;
-                if (id != pid && id != iym && (lane == 0 || id != ixm)) atomicMin(mi + id, p);
-            }
+            if (id >= 0 && id != pid && id != iym && (lane == 0 || id != ixm)) atomicMin(mi + id, p);
             pid = id;
             if (!do_rag) continue;
             int ix = __shfl_down_sync(0xffffffffu, id, 1);
@@ -1894,6 +1885,102 @@ static __global__ void __launch_bounds__(NTHR) k_write_batch(const Batch b, cons
         for (int k = 1; k < NL; k++) {
             const int32_t *gm = gmap + (size_t)(k - 1) * kstride;
             d.out[(size_t)k * d.N + p] = c >= 0 ? gm[c] - gm[rb] : -1;
+        }
+    }
+}
+
+// 3D label write, one CTA per tile: every voxel's canonical id and its id on
+// each waterfall level, from its 16-bit end slot and a per-tile table (slot
+// -> root, after k_chase, in ends; root -> id through idmap; id -> level
+// ids through gmap), one plane per level.  A tile with more slots than the
+// table holds maps each voxel through the global arrays.  Batched calls:
+// rbase holds each image's first basin id (single image: nullptr).
+static constexpr int kWrite6Tab = 12288;   // level ids held in shared memory per tile
+
+static __global__ void __launch_bounds__(TT<6>::NT, 3) k_write6(const Batch b, const uint16_t *__restrict__ code,
+                                                             const int32_t *__restrict__ ends,
+                                                             const int2 *__restrict__ tends,
+                                                             const int32_t *__restrict__ idmap,
+                                                             const int32_t *__restrict__ gmap, size_t kstride,
+                                                             int NL, const int32_t *__restrict__ rbase,
+                                                             const int32_t *__restrict__ k0_ptr)
+{
+    using C = TC<6>;
+    constexpr int GX = C::TX / 4;                  // groups of four x per row
+    constexpr int G = C::NPIX / 4 / C::NT;         // groups per thread
+    static_assert(C::NPIX % (4 * C::NT) == 0, "whole groups per thread");
+    __shared__ int lv[kWrite6Tab];   // lv[k * n + slot]: id of the slot's basin on level k
+    const int tid = threadIdx.x;
+    const int t = blockIdx.x;
+    const int ii = img_of_tile(b, t);
+    const ImgDesc d = img_desc(b, ii);
+    const TileCtx tc = tile_ctx<6>(b, t);
+    const int2 te = tends[t];
+    // the voxels' end slots first (their loads overlap the table build):
+    // thread group g covers x = x0 + 4 (tid % GX) .. + 3 of row tid / GX + g * NT / GX
+    const int gx = tc.x0 + 4 * (tid % GX);
+    const bool vec = (d.W % 4 == 0) && (d.base % 4 == 0) && (((uintptr_t)d.out & 15) == 0);
+    int q[G];
+    uint2 cv[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        const int row = tid / GX + g * (C::NT / GX);   // (y, z) row of the tile
+        const int y = tc.y0 + row % C::TY, z = tc.z0 + row / C::TY;
+        q[g] = (y < d.H && z < d.D && gx < d.W) ? (z * d.H + y) * d.W + gx : -1;
+        cv[g] = make_uint2(0, 0);
+        if (q[g] >= 0) {
+            if (vec) {
+                cv[g] = __ldg(reinterpret_cast<const uint2 *>(code + d.base + q[g]));
+            } else {
+                unsigned c4[4] = {0, 0, 0, 0};
+                for (int u = 0; u < 4; u++)
+                    if (gx + u < d.W) c4[u] = code[d.base + q[g] + u];
+                cv[g] = make_uint2(c4[0] | (c4[1] << 16), c4[2] | (c4[3] << 16));
+            }
+        }
+    }
+    const int K0 = *k0_ptr;
+    const int rb = rbase ? rbase[ii] : 0;
+    const int n = te.y;
+    const bool tab = n * NL <= kWrite6Tab;
+    auto level_of = [&](int s, int k) -> int {   // level-k id of slot s's basin
+        const int c = safe_id(idmap, ends[te.x + s], K0);
+        if (c < 0) return -1;
+        if (k == 0) return c - rb;
+        const int32_t *gm = gmap + (size_t)(k - 1) * kstride;
+        return gm[c] - (rbase ? gm[rb] : 0);
+    };
+    if (tab) {
+        for (int s = tid; s < n; s += C::NT) {
+            const int c = safe_id(idmap, ends[te.x + s], K0);
+            lv[s] = c >= 0 ? c - rb : -1;
+            for (int k = 1; k < NL; k++) {
+                const int32_t *gm = gmap + (size_t)(k - 1) * kstride;
+                lv[k * n + s] = c >= 0 ? gm[c] - (rbase ? gm[rb] : 0) : -1;
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        if (q[g] < 0) continue;
+        const int s0 = cv[g].x & 0x1fff, s1 = (cv[g].x >> 16) & 0x1fff, s2 = cv[g].y & 0x1fff,
+                  s3 = (cv[g].y >> 16) & 0x1fff;
+        for (int l = 0; l < NL; l++) {
+            int4 o;
+            if (tab) {
+                o = make_int4(lv[l * n + s0], lv[l * n + s1], lv[l * n + s2], lv[l * n + s3]);
+            } else {
+                o = make_int4(level_of(s0, l), level_of(s1, l), level_of(s2, l), level_of(s3, l));
+            }
+            int32_t *dst = d.out + (size_t)l * d.N + q[g];
+            if (vec && gx + 3 < d.W) {
+                __stcs(reinterpret_cast<int4 *>(dst), o);
+            } else {
+                const int ov[4] = {o.x, o.y, o.z, o.w};
+                for (int u = 0; u < 4; u++)
+                    if (gx + u < d.W) __stcs(dst + u, ov[u]);
+            }
         }
     }
 }
