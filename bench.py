@@ -56,7 +56,7 @@ PHASE_BYTES = {
 }
 KERNEL_OF_PHASE = {"step1": "k_init6", "plateau": "k_plateau2", "resolve_union": "k_resolve2",
                    "jump": "k_jump2", "compact": "k_rank_*", "chase": "k_chase", "rag": "k_rag6",
-                   "levels": "k_levels", "level_write": "k_write_vec", "cleanup": "k_hash_clear"}
+                   "levels": "k_levels", "level_write": "k_write6", "cleanup": "k_edges_compact"}
 # source file of each kernel (the traffic record is void once it changes)
 KERNEL_SOURCE = {"k_init6": "ws_tiles.cuh", "k_rag6": "ws_tiles.cuh", "k_chase": "ws_tiles.cuh",
                  "k_write6": "ws_tiles.cuh", "k_levels": "ws_kernels.cuh"}
