@@ -1518,31 +1518,38 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
         }
         return B::RB;   // not numbered
     };
-    // spans of the neighbouring tiles (for the face pixels), and the roots of
-    // this tile's slots: neither needs the boxes, so both go before the wait
+    // Neither the roots of this tile's slots nor those of its forward face
+    // pixels need the boxes: their codes are read from global memory, so all
+    // of it goes before the wait.  The thread's first slot root stays in a
+    // register for the ids below.
     const bool hasx = x0 + C::TX < geo.W, hasy = y0 + C::TY < geo.H, hasz = z0 + C::TZ < geo.D;
-    const int2 tex = do_rag && hasx && tid < B::HX ? __ldg(tends + t + 1) : make_int2(0, 0);
-    const int2 tey = do_rag && hasy ? __ldg(tends + t + ntx) : make_int2(0, 0);
-    const int2 tez = do_rag && hasz ? __ldg(tends + t + ntx * nty) : make_int2(0, 0);
-    for (int i = tid; i < te.y; i += C::NT) rh_insert(__ldg(ends + te.x + i));
+    const int rown = tid < te.y ? __ldg(ends + te.x + tid) : -1;
+    int fzr = -1, fyr = -1, fxr = -1;   // roots of the face pixels (lane, ly, TZ), (lane, TY, ly), (TX, fy, fz)
+    if (do_rag) {
+        const int fy = tid % C::TY, fz = tid / C::TY;
+        const bool vz = col_in && hasz, vy = x < geo.W && hasy && z0 + ly < geo.D;
+        const bool vx = tid < B::HX && hasx && y0 + fy < geo.H && z0 + fz < geo.D;
+        const int2 tez = vz ? __ldg(tends + t + ntx * nty) : make_int2(0, 0);
+        const int2 tey = vy ? __ldg(tends + t + ntx) : make_int2(0, 0);
+        const int2 tex = vx ? __ldg(tends + t + 1) : make_int2(0, 0);
+        const int cz = vz ? __ldg(code + base + ((z0 + C::TZ) * geo.H + y) * geo.W + x) : 0;
+        const int cy = vy ? __ldg(code + base + ((z0 + ly) * geo.H + y0 + C::TY) * geo.W + x) : 0;
+        const int cx = vx ? __ldg(code + base + ((z0 + fz) * geo.H + y0 + fy) * geo.W + x0 + C::TX) : 0;
+        fzr = face_root(vz, cz, tez, ends, status);
+        fyr = face_root(vy, cy, tey, ends, status);
+        fxr = face_root(vx, cx, tex, ends, status);
+    }
+    rh_insert(rown);
+    for (int i = tid + C::NT; i < te.y; i += C::NT) rh_insert(__ldg(ends + te.x + i));
+    rh_insert(fzr);
+    rh_insert(fyr);
+    rh_insert(fxr);
     if (TMA) {
         const bool ok = mbar_wait(&bar, 0, status);
         if (__syncthreads_or(!ok)) return;
+    } else {
+        __syncthreads();
     }
-    if (do_rag) {
-        hzr[tid] = face_root(col_in && hasz, cb[(C::TZ * B::BY + ly) * B::CW + lane], tez, ends, status);
-        hyr[tid] = face_root(x < geo.W && hasy && z0 + ly < geo.D, cb[(ly * B::BY + C::TY) * B::CW + lane], tey,
-                             ends, status);
-        if (tid < B::HX) {
-            const int fy = tid % C::TY, fz = tid / C::TY;
-            hxr[tid] = face_root(hasx && y0 + fy < geo.H && z0 + fz < geo.D, cb[(fz * B::BY + fy) * B::CW + C::TX],
-                                 tex, ends, status);
-        }
-        rh_insert(hzr[tid]);
-        rh_insert(hyr[tid]);
-        if (tid < B::HX) rh_insert(hxr[tid]);
-    }
-    __syncthreads();
     for (int i = tid; i < B::RH; i += C::NT)
         if (rhk[i] >= 0) {
             const int id = atomicAdd(&s_nr, 1);
@@ -1574,8 +1581,14 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
     const int p0 = base + (z0 * geo.H + y) * geo.W + x;   // global index of (lane, ly, z = 0)
     const int nz = geo.D - z0 < C::TZ ? geo.D - z0 : C::TZ;
 
+    if (do_rag) {   // the face roots (mode 2 compares roots)
+        hzr[tid] = fzr;
+        hyr[tid] = fyr;
+        if (tid < B::HX) hxr[tid] = fxr;
+    }
     if (mode < 2) {
-        for (int i = tid; i < te.y; i += C::NT) ss[i] = (uint8_t)rh_find(__ldg(ends + te.x + i));
+        if (tid < te.y) ss[tid] = (uint8_t)rh_find(rown);
+        for (int i = tid + C::NT; i < te.y; i += C::NT) ss[i] = (uint8_t)rh_find(__ldg(ends + te.x + i));
         if (do_rag) {   // ids of the forward faces
             const int iz = rh_find(hzr[tid]);
             hzr[tid] = iz;
