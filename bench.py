@@ -251,6 +251,58 @@ def _pool_2d(seed):
     return synth.blob_image(4096, 4096, 8192, seed)
 
 
+def run_small_configs(ctx, torch, reps=20):
+    """Configs 0 and 1 (the 2D cases): 256^2 blob image, gradient + watershed +
+    NL=3 (latency, us); 4096^2 blob gradient quantised to 16 levels, 4- and
+    8-connectivity, NL=6 (Gpx/s and the algorithmic HBM fraction, b + 4 NL =
+    25 B/px).  Device-resident inputs; median of `reps` CUDA-event timings."""
+    import statistics
+    from paper_2410_08946_gb300 import synth
+    peak, _ = hbm_peak()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ctx.check()
+        return statistics.median(ts), min(ts)
+
+    out = {}
+    img0 = torch.from_numpy(synth.blob_image(256, 256, 32, SEED - 2)).cuda()
+    g0 = torch.empty_like(img0)
+    lv0 = torch.empty((3, 256, 256), dtype=torch.int32, device="cuda")
+    c0 = torch.empty(3, dtype=torch.int32, device="cuda")
+
+    def cfg0():
+        ctx.gradient(img0, 0, out=g0)
+        ctx.segment(g0, 4, 3, lv0, c0)
+    med, best = timed(cfg0)
+    out["config0"] = {"workload": "2D 256x256 uint8 blob image: gradient + watershed + waterfall NL=3, "
+                                  "4-connectivity", "us_median": med * 1e3, "us_min": best * 1e3}
+    img1 = torch.from_numpy(synth.blob_image(4096, 4096, 2000, SEED - 1)).cuda()
+    g1 = ctx.gradient(img1, 4)
+    N1 = 4096 * 4096
+    lv1 = torch.empty((6, 4096, 4096), dtype=torch.int32, device="cuda")
+    c1 = torch.empty(6, dtype=torch.int32, device="cuda")
+    for conn in (4, 8):
+        med, best = timed(lambda: ctx.segment(g1, conn, 6, lv1, c1))
+        out[f"config1_conn{conn}"] = {
+            "workload": f"2D 4096x4096 uint8 blob gradient quantised to 16 levels, {conn}-connectivity, "
+                        "watershed + waterfall NL=6", "ms_median": med, "gpx_s": N1 / med / 1e6,
+            "alg_hbm_frac": 25 * N1 / (med / 1e3) / 1e9 / peak, "levels_counts": c1.cpu().tolist()}
+    del lv1, g1, img1
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_batch(ctx, binding, torch, n=512, NL=6, conn=4, reps=3):
     """Config 3: n 2D uint8 images, sides log-uniform in [64, 2048], as one
     CUDA-graph replay of the batched pipeline vs n per-image ws_segment calls."""
@@ -537,6 +589,7 @@ def main():
     if world == 1 and not args.no_batch:
         del levels_d
         torch.cuda.empty_cache()
+        line["small_configs"] = run_small_configs(ctx, torch)
         line["batch"] = run_batch(ctx, binding, torch)
     if world == 1 and not args.no_serve:
         line["serve"] = run_serve(ctx, binding, torch, seconds=args.serve_seconds)

@@ -155,7 +155,9 @@ ws_status ws_gradient(ws_context *ctx, const uint8_t *img_d, const ws_shape *sha
  * its plateau; ties between equally near neighbours go to the larger pixel
  * index, as Eq. 1 does for steepest descent).
  *   grad_d        gradient samples, dtype WS_U8 or WS_U16, [N]
- *   connectivity  4 or 8 (ndim 2), 6 (ndim 3; 26 returns WS_ERR_UNSUPPORTED)
+ *   connectivity  4 or 8 (ndim 2), 6 or 26 (ndim 3): the face neighbours, or
+ *                 every voxel of the 3x3x3 cube around (Sec. 3.1: unit distance
+ *                 in the chosen metric)
  *   labels_d      int32 [N] output, canonical basin ids 0..K-1
  *   count_d       int32 [1] output, K (may be NULL)
  */
@@ -249,7 +251,7 @@ typedef struct ws_server ws_server;
 typedef struct {
     const void *grad;     /* gradient samples [N]: host memory if on_host, else device memory */
     int32_t on_host;      /* 1: grad and the outputs are host memory (copied by the server) */
-    int32_t connectivity; /* 4 / 8 (2D) or 6 (3D) */
+    int32_t connectivity; /* 4 / 8 (2D) or 6 / 26 (3D) */
     ws_dtype dtype;
     int32_t NL;           /* levels, counting level 0 */
     ws_shape shape;

@@ -305,9 +305,8 @@ static ws_status make_geo(ws_context *c, const ws_shape *shape, Geo *g)
 static ws_status check_conn(ws_context *c, const ws_shape *shape, int conn)
 {
     if (shape->ndim == 2 && (conn == 4 || conn == 8)) return WS_OK;
-    if (shape->ndim == 3 && conn == 6) return WS_OK;
-    if (shape->ndim == 3 && conn == 26) return set_error(c, WS_ERR_UNSUPPORTED, "26-connectivity is not implemented");
-    return set_error(c, WS_ERR_INVALID, "connectivity must be 4 or 8 (2D) or 6 (3D)");
+    if (shape->ndim == 3 && (conn == 6 || conn == 26)) return WS_OK;
+    return set_error(c, WS_ERR_INVALID, "connectivity must be 4 or 8 (2D) or 6 or 26 (3D)");
 }
 
 static ws_status prep(ws_context *c, const void *grad, int dtype, const ws_shape *shape, int conn, Geo *g,

@@ -128,6 +128,17 @@ template <> struct Nb<6> {
     __device__ static constexpr int dz(int i) { return i == 0 ? -1 : (i == 5 ? 1 : 0); }
 };
 
+// 26-connectivity: every (dz, dy, dx) in {-1, 0, 1}^3 but the centre, in
+// ascending linear-offset order (cell c = 9 (dz + 1) + 3 (dy + 1) + dx + 1,
+// the centre c = 13 skipped)
+template <> struct Nb<26> {
+    static constexpr int n = 26;
+    __device__ static constexpr int cell(int i) { return i < 13 ? i : i + 1; }
+    __device__ static constexpr int dx(int i) { return cell(i) % 3 - 1; }
+    __device__ static constexpr int dy(int i) { return (cell(i) / 3) % 3 - 1; }
+    __device__ static constexpr int dz(int i) { return cell(i) / 9 - 1; }
+};
+
 template <int CONN> struct Dim {
     static constexpr int nd = (CONN == 4 || CONN == 8) ? 2 : 3;
 };

@@ -9,6 +9,7 @@ const Launchers *launchers_u16(int conn)
     case 4: return Inst<uint16_t, 4>::get();
     case 8: return Inst<uint16_t, 8>::get();
     case 6: return Inst<uint16_t, 6>::get();
+    case 26: return Inst<uint16_t, 26>::get();
     default: return nullptr;
     }
 }

@@ -143,8 +143,8 @@ extern "C" ws_status ws_watershed_static(const void *grad_d, ws_dtype dtype, con
         W * H * D > (int64_t)kMaxPixels)
         return WS_ERR_INVALID;  // larger than WS_STATIC_MAX_PIXELS: use ws_watershed
     const bool ok2 = shape->ndim == 2 && (connectivity == 4 || connectivity == 8);
-    const bool ok3 = shape->ndim == 3 && connectivity == 6;
-    if (!ok2 && !ok3) return shape->ndim == 3 && connectivity == 26 ? WS_ERR_UNSUPPORTED : WS_ERR_INVALID;
+    const bool ok3 = shape->ndim == 3 && (connectivity == 6 || connectivity == 26);
+    if (!ok2 && !ok3) return WS_ERR_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();

@@ -54,6 +54,9 @@ template <> struct TT<8> {
 template <> struct TT<6> {
     static constexpr int TX = 32, TY = 16, TZ = 16, NT = 512;
 };
+template <> struct TT<26> {
+    static constexpr int TX = 32, TY = 16, TZ = 16, NT = 512;
+};
 
 
 template <int CONN> struct TC {
@@ -64,9 +67,12 @@ template <int CONN> struct TC {
     // halo box on both sides (k_init, k_plateau2)
     static constexpr int HX = TX + 2, HY = TY + 2, HZ = D3 ? TZ + 2 : 1;
     static constexpr int HS = HX * HY * HZ;
-    // forward box of k_label: +1 on every axis, and -1 in x for 8-connectivity
-    static constexpr int BXL = CONN == 8 ? 1 : 0;
-    static constexpr int BX = TX + 1 + BXL, BY = TY + 1, BZ = D3 ? TZ + 1 : 1;
+    // forward box of k_label: +1 on every axis, and -1 in x / y where a
+    // forward neighbour lies there
+    // (forward neighbours reach x - 1 in 8- and 26-connectivity, y - 1 in 26)
+    static constexpr int BXL = (CONN == 8 || CONN == 26) ? 1 : 0;
+    static constexpr int BYL = CONN == 26 ? 1 : 0;
+    static constexpr int BX = TX + 1 + BXL, BY = TY + 1 + BYL, BZ = D3 ? TZ + 1 : 1;
     static constexpr int BS = BX * BY * BZ;
     static constexpr int HASH = 1024;  // shared-memory edge slots per CTA
 };
@@ -234,7 +240,7 @@ __device__ __forceinline__ int init_step1(const T *gs, int *nx, int (&st)[TC<CON
 {
     using C = TC<CONN>;
     using B = InitBox<T, CONN>;
-    constexpr bool COL = C::D3 && C::NT == C::TX * C::TY;  // slot k is z = k of column tid
+    constexpr bool COL = CONN == 6 && C::NT == C::TX * C::TY;  // slot k is z = k of column tid
     int plateau = 0;
     unsigned cz[C::PER + 2];
     if (COL) {
@@ -976,7 +982,7 @@ __global__ void __launch_bounds__(NTHR) k_union2(const Batch b, int32_t *par, co
             const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
             // only pixels with a forward neighbour outside the tile
             const bool border = lx == C::TX - 1 || ly == C::TY - 1 || (C::D3 && lz == C::TZ - 1) ||
-                                (CONN == 8 && lx == 0);
+                                ((CONN == 8 || CONN == 26) && lx == 0) || (CONN == 26 && ly == 0);
             if (!border) continue;
             const int x = tc.x0 + lx, y = tc.y0 + ly, z = tc.z0 + lz;
             if (x >= geo.W || y >= geo.H || z >= geo.D) continue;
@@ -1169,8 +1175,8 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
             mbar_init(&bar, 1);
             mbar_fence_init();
             mbar_arrive_expect_tx(&bar, B::PBYTES + (do_rag ? B::GBYTES : 0));
-            tma_load_3d(pb, &tmp, x0 - B::AP, y0, z0, &bar);
-            if (do_rag) tma_load_3d(gb, &tmg, x0 - B::AG, y0, z0, &bar);
+            tma_load_3d(pb, &tmp, x0 - B::AP, y0 - C::BYL, z0, &bar);
+            if (do_rag) tma_load_3d(gb, &tmg, x0 - B::AG, y0 - C::BYL, z0, &bar);
         }
     }
     for (int i = tid; i < B::DSLOTS; i += C::NT) dk[i] = -1;
@@ -1194,10 +1200,10 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
             const int i = tid + k * C::NT;
             if (i >= C::BS) break;
             const int bx = i % C::BX, by = (i / C::BX) % C::BY, bz = i / (C::BX * C::BY);
-            const int x = x0 - C::BXL + bx, y = y0 + by, z = z0 + bz;
+            const int x = x0 - C::BXL + bx, y = y0 - C::BYL + by, z = z0 + bz;
             const int pos = (bz * C::BY + by) * B::RWP + bx + B::AP - C::BXL;
             int r = -1;
-            if (x >= 0 && x < geo.W && y < geo.H && z < geo.D) {
+            if (x >= 0 && x < geo.W && y >= 0 && y < geo.H && z < geo.D) {
                 if (TMA) {
                     r = pb[pos];
                 } else {
@@ -1266,8 +1272,8 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
         const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
         const bool in = x < geo.W && y < geo.H && z < geo.D;
-        const int bp = (lz * C::BY + ly) * B::RWP + lx + B::AP;
-        const int bg = (lz * C::BY + ly) * B::RWG + lx + B::AG;
+        const int bp = (lz * C::BY + ly + C::BYL) * B::RWP + lx + B::AP;
+        const int bg = (lz * C::BY + ly + C::BYL) * B::RWG + lx + B::AG;
         const int r = in ? pb[bp] : -1;
         const int p = in ? base + (z * geo.H + y) * geo.W + x : 0;
         if (in) par[p] = r;
@@ -1282,7 +1288,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
         for (int n = Half<CONN>::first; n < Nb<CONN>::n; n++) {
             const int dn = Nb<CONN>::dz(n) * C::BY + Nb<CONN>::dy(n);
             const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
-            if (xx < 0 || xx >= geo.W || yy >= geo.H || zz >= geo.D) continue;
+            if (xx < 0 || xx >= geo.W || yy < 0 || yy >= geo.H || zz >= geo.D) continue;
             const int rq = pb[bp + dn * B::RWP + Nb<CONN>::dx(n)];
             if (rq == r) continue;
             const unsigned gq = gb[bg + dn * B::RWG + Nb<CONN>::dx(n)];

@@ -290,7 +290,10 @@ def test_invalid_arguments(ctx):
     assert e.value.status == binding.WS_ERR_INVALID
     v = dev(np.zeros((4, 4, 4), np.uint16))
     with pytest.raises(binding.WsError) as e:
-        ctx.watershed(v, 26)
-    assert e.value.status == binding.WS_ERR_UNSUPPORTED
+        ctx.watershed(v, 8)          # a 2D connectivity on a volume
+    assert e.value.status == binding.WS_ERR_INVALID
+    with pytest.raises(binding.WsError) as e:
+        ctx.watershed(img, 26)       # a 3D connectivity on an image
+    assert e.value.status == binding.WS_ERR_INVALID
     with pytest.raises(binding.WsError):
         ctx.segment(img, 4, 0)
