@@ -17,6 +17,9 @@ Parity status per function (pins are in tests/test_oracle_*.py):
                         simulation, invariants, 1D property of Sec. 3.1)
   waterfall ........... pinned (brute force on tiny images, invariants)
   gradient2d .......... pinned by closed forms only (the paper names no operator)
+  region_graph ........ pinned (brute force over all pixel pairs on tiny images,
+                        closed-form block grids, a hand-worked example, the
+                        lowest-pass rule reproducing the pinned waterfall)
 """
 from __future__ import annotations
 
@@ -64,8 +67,9 @@ def _load():
         lib.orc_roots_without_merge.argtypes = [P, I, I, P, I, P]
         lib.orc_waterfall.argtypes = [P, P, I, I, P, I, I, P, P]
         lib.orc_segment.argtypes = [P, I, I, P, I, I, P, P]
+        lib.orc_region_graph.argtypes = [P, P, I, I, P, I, P, I, I, i64, P, P, P, i64, P, P, P, P]
         for f in ("orc_gradient2d", "orc_step1", "orc_plateau_distance", "orc_watershed",
-                  "orc_roots_without_merge", "orc_waterfall", "orc_segment"):
+                  "orc_roots_without_merge", "orc_waterfall", "orc_segment", "orc_region_graph"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -186,3 +190,41 @@ def segment(grad: np.ndarray, conn: int, NL: int):
     counts = np.empty(NL, dtype=np.int32)
     _check(_load().orc_segment(_ptr(g), bps, ndim, _ptr(dims), conn, NL, _ptr(levels), _ptr(counts)))
     return levels, counts
+
+
+def region_graph(labels: np.ndarray, grad: np.ndarray, conn: int, values: np.ndarray | None = None):
+    """Region graph of one labelling (Sec. 6 node/edge export, Alg. 5 step V
+    pass values).  labels: ids >= 0 with the gradient's shape; values: None or
+    (C, *shape) uint8/uint16 (a single plane may omit C).  Returns a dict with
+    row_ptr int64[K+1], col int32[nnz], pass uint32[nnz] (symmetric CSR, columns
+    ascending), size int64[K], sum uint64[K, C], mean float64[K, C]; K = max id + 1."""
+    g, bps, ndim, dims = _prep(grad)
+    L = np.ascontiguousarray(labels, dtype=np.int32).reshape(g.shape)
+    N = L.size
+    if L.min() < 0:
+        raise ValueError("labels must be >= 0")
+    K = int(L.max()) + 1
+    if values is None:
+        C, vbps, v = 0, 1, np.zeros(1, dtype=np.uint8)
+    else:
+        v = np.ascontiguousarray(values)
+        if v.dtype not in (np.uint8, np.uint16):
+            raise TypeError("values must be uint8 or uint16")
+        v = v.reshape(-1, N)
+        C, vbps = v.shape[0], v.dtype.itemsize
+    if conn not in (4, 8, 6, 26):
+        raise ValueError("connectivity must be 4, 8, 6 or 26")
+    cap = N * conn  # one record per ordered neighbour pair at most
+    row_ptr = np.empty(K + 1, dtype=np.int64)
+    col = np.empty(max(cap, 1), dtype=np.int32)
+    pas = np.empty(max(cap, 1), dtype=np.uint32)
+    nnz = np.zeros(1, dtype=np.int64)
+    size = np.empty(K, dtype=np.int64)
+    ssum = np.empty((K, max(C, 1)), dtype=np.uint64)
+    mean = np.empty((K, max(C, 1)), dtype=np.float64)
+    _check(_load().orc_region_graph(_ptr(L), _ptr(g), bps, ndim, _ptr(dims), conn, _ptr(v), vbps, C, K,
+                                    _ptr(row_ptr), _ptr(col), _ptr(pas), cap, _ptr(nnz), _ptr(size),
+                                    _ptr(ssum), _ptr(mean)))
+    n = int(nnz[0])
+    return {"row_ptr": row_ptr, "col": col[:n].copy(), "pass": pas[:n].copy(), "size": size,
+            "sum": ssum[:, :C].copy(), "mean": mean[:, :C].copy()}

@@ -31,6 +31,12 @@
  *   R4  the waterfall is the graph form: level k+1 joins every pair of level-k
  *       regions whose lowest pass (Alg. 5 step V) is the lowest pass of one of
  *       the two; NL counts level 0 (Sec. 4, the NL definition).
+ *   R5  the region graph handed to a graph network (Sec. 6, waterfall regions
+ *       in place of superpixels): one node per region id 0..K-1 of a labelling,
+ *       an edge between two regions exactly when a pixel of one has a pixel of
+ *       the other in N(p), weighted by pass(A,B) of Alg. 5 step V; node
+ *       features are the pixel count and, per channel of a value image, the sum
+ *       and the mean (sum / count; 0 for an id no pixel carries).
  *
  * Parity pins (tests/test_oracle_*.py): the worked examples of Sec. 3.3 and
  * Sec. 3.4 (tests/golden/), exhaustive tiny images against a literal
@@ -585,4 +591,89 @@ int orc_segment(const void *grad, int bps, int ndim, const int64_t *dims, int co
     geom_t g;
     geom_init(&g, ndim, dims, conn);
     return orc_waterfall(levels, grad, bps, ndim, dims, conn, NL, levels + g.N, counts);
+}
+
+/* ------------------------------------------------------------------------ */
+/* G: region graph of one labelling (reading R5)                             */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Region adjacency of the labelling L (ids in [0, K)) as a symmetric CSR:
+ * row A lists, in increasing order, every region B != A with a pixel in N(p)
+ * of a pixel p of A, and pass[] holds pass(A,B) = the smallest
+ * max(G(p), G(q)) over those pixel pairs (Alg. 5 step V).  col/pass have room
+ * for cap entries; *nnz_out gets the number written (twice the edges).
+ * size[A] = pixels of A; with C > 0 channels of values (channel-major planes
+ * of N samples, vbps bytes each), sum[A*C + c] and mean[A*C + c] =
+ * sum / size (0 when size is 0).
+ */
+int orc_region_graph(const int32_t *L, const void *grad, int bps, int ndim, const int64_t *dims, int conn,
+                     const void *values, int vbps, int C, int64_t K, int64_t *row_ptr, int32_t *col,
+                     uint32_t *pass, int64_t cap, int64_t *nnz_out, int64_t *size, uint64_t *sum, double *mean)
+{
+    geom_t g;
+    if (geom_init(&g, ndim, dims, conn) != ORC_OK || (bps != 1 && bps != 2) || K < 1 || C < 0 ||
+        (C > 0 && vbps != 1 && vbps != 2))
+        return ORC_EINVAL;
+    int64_t N = g.N;
+    for (int64_t p = 0; p < N; p++)
+        if (L[p] < 0 || L[p] >= K) return ORC_EINVAL;
+
+    /* node features: plain counting */
+    for (int64_t A = 0; A < K; A++) size[A] = 0;
+    for (int64_t i = 0; i < K * C; i++) sum[i] = 0;
+    for (int64_t p = 0; p < N; p++) {
+        size[L[p]]++;
+        for (int c = 0; c < C; c++) sum[(int64_t)L[p] * C + c] += sample(values, vbps, (int64_t)c * N + p);
+    }
+    for (int64_t A = 0; A < K; A++)
+        for (int c = 0; c < C; c++)
+            mean[A * C + c] = size[A] ? (double)sum[A * C + c] / (double)size[A] : 0.0;
+
+    /* one record (L[p], L[q], max(G(p), G(q))) per ordered neighbour pair of
+       different regions, so both directions of every edge are present */
+    int64_t np = 0, pcap = 1024;
+    pair_t *pairs = (pair_t *)malloc(sizeof(pair_t) * (size_t)pcap);
+    if (!pairs) return ORC_ENOMEM;
+    int64_t nb[26];
+    for (int64_t p = 0; p < N; p++) {
+        int n = neighbours(&g, p, nb);
+        for (int i = 0; i < n; i++) {
+            int64_t q = nb[i];
+            if (L[p] == L[q]) continue;
+            if (np == pcap) {
+                pcap *= 2;
+                pair_t *t = (pair_t *)realloc(pairs, sizeof(pair_t) * (size_t)pcap);
+                if (!t) {
+                    free(pairs);
+                    return ORC_ENOMEM;
+                }
+                pairs = t;
+            }
+            uint32_t gp = sample(grad, bps, p), gq = sample(grad, bps, q);
+            pairs[np].a = L[p];
+            pairs[np].b = L[q];
+            pairs[np].h = gp > gq ? gp : gq;
+            np++;
+        }
+    }
+    /* sorted by (A, B, height): the first record of each (A, B) holds pass(A,B) */
+    qsort(pairs, (size_t)np, sizeof(pair_t), cmp_pair);
+    for (int64_t A = 0; A <= K; A++) row_ptr[A] = 0;
+    int64_t nnz = 0;
+    for (int64_t i = 0; i < np; i++) {
+        if (i > 0 && pairs[i].a == pairs[i - 1].a && pairs[i].b == pairs[i - 1].b) continue;
+        if (nnz == cap) {
+            free(pairs);
+            return ORC_ENOMEM;
+        }
+        col[nnz] = (int32_t)pairs[i].b;
+        pass[nnz] = pairs[i].h;
+        row_ptr[pairs[i].a + 1]++;
+        nnz++;
+    }
+    for (int64_t A = 0; A < K; A++) row_ptr[A + 1] += row_ptr[A];
+    *nnz_out = nnz;
+    free(pairs);
+    return ORC_OK;
 }
