@@ -255,7 +255,8 @@ def run_small_configs(ctx, torch, reps=20):
     """Configs 0 and 1 (the 2D cases): 256^2 blob image, gradient + watershed +
     NL=3 (latency, us); 4096^2 blob gradient quantised to 16 levels, 4- and
     8-connectivity, NL=6 (Gpx/s and the algorithmic HBM fraction, b + 4 NL =
-    25 B/px).  Device-resident inputs; median of `reps` CUDA-event timings."""
+    25 B/px); and a 512^3 volume in 6- and 26-connectivity.  Device-resident
+    inputs; median of `reps` CUDA-event timings."""
     import statistics
     from paper_2410_08946_gb300 import synth
     peak, _ = hbm_peak()
@@ -299,6 +300,19 @@ def run_small_configs(ctx, torch, reps=20):
                         "watershed + waterfall NL=6", "ms_median": med, "gpx_s": N1 / med / 1e6,
             "alg_hbm_frac": 25 * N1 / (med / 1e3) / 1e9 / peak, "levels_counts": c1.cpu().tolist()}
     del lv1, g1, img1
+    torch.cuda.empty_cache()
+    # 26-connectivity (a NEXT row): 512^3 distance volume, same seed density as 928^3
+    side = 512
+    v = torch.from_numpy(synth.distance_volume(side, side, side, sample_seeds(side), seed=SEED)).cuda()
+    lv2 = torch.empty((NL,) + tuple(v.shape), dtype=torch.int32, device="cuda")
+    c2 = torch.empty(NL, dtype=torch.int32, device="cuda")
+    for conn in (6, 26):
+        med, best = timed(lambda: ctx.segment(v, conn, NL, lv2, c2))
+        out[f"volume512_conn{conn}"] = {
+            "workload": f"3D 512^3 uint16 distance volume, {conn}-connectivity, watershed + waterfall NL={NL}",
+            "ms_median": med, "gvox_s": side ** 3 / med / 1e6,
+            "alg_hbm_frac": (2 + 4 * NL) * side ** 3 / (med / 1e3) / 1e9 / peak, "levels_counts": c2.cpu().tolist()}
+    del lv2, v
     torch.cuda.empty_cache()
     return out
 
