@@ -181,6 +181,44 @@ ws_status ws_waterfall(ws_context *ctx, const int32_t *labels0_d, const void *gr
                        int32_t *counts_d, ws_stream_t stream);
 
 /*
+ * Region graph of one labelling, for graph-network pre-processing (Sec. 6: the
+ * regions of a waterfall level replace superpixels as the nodes of the graph).
+ * Node A is region id A (0..K-1, K = largest id + 1; ids no pixel carries are
+ * isolated nodes of size 0).  Regions A != B share an edge when a pixel of A
+ * has a pixel of B in its neighbourhood N(p) (Sec. 3.1, the connectivity
+ * below); the edge weight is pass(A, B) of Alg. 5 step V, the smallest
+ * max(G(p), G(q)) over those pixel pairs.  The graph is built into the context
+ * and read out with ws_region_graph_read.  This call synchronises `stream`
+ * (the sizes of the result are returned to the host).
+ *   labels_d      int32 [N] ids >= 0 and below N (a level plane of ws_segment,
+ *                 or any labelling); otherwise WS_ERR_INVALID
+ *   grad_d        gradient [N] of `dtype`, the heights of the pass values
+ *   values_d      value image for the node features: `channels` planes of N
+ *                 samples, channel-major, WS_U8 or WS_U16 (NULL if channels = 0)
+ *   regions       host int64 output: K (may be NULL)
+ *   entries       host int64 output: CSR entries, twice the edge count (may be NULL)
+ * Errors: WS_ERR_OOM when the region table is full (raise
+ * ws_tuning.edge_capacity) or the workspace budget is exhausted.
+ */
+ws_status ws_region_graph(ws_context *ctx, const int32_t *labels_d, const void *grad_d, ws_dtype dtype,
+                          const ws_shape *shape, int connectivity, const void *values_d, ws_dtype values_dtype,
+                          int channels, int64_t *regions, int64_t *entries, ws_stream_t stream);
+
+/*
+ * Copies the last graph built by ws_region_graph in this context into caller
+ * device buffers (each may be NULL to skip it); enqueued on `stream`:
+ *   row_ptr_d  int64  [K+1]      CSR row starts (symmetric adjacency)
+ *   col_d      int32  [entries]  neighbours of each row, increasing ids
+ *   pass_d     uint32 [entries]  pass(A, B) of each entry
+ *   size_d     int64  [K]        pixels per region
+ *   sum_d      uint64 [K*channels]  value sums, region-major
+ *   mean_d     double [K*channels]  sum / size (0 for an empty id)
+ * WS_ERR_INVALID if no graph has been built.
+ */
+ws_status ws_region_graph_read(ws_context *ctx, int64_t *row_ptr_d, int32_t *col_d, uint32_t *pass_d,
+                               int64_t *size_d, uint64_t *sum_d, double *mean_d, ws_stream_t stream);
+
+/*
  * The whole hierarchy of Alg. 4: ws_watershed followed by ws_waterfall.
  *   levels_d  int32 [NL*N] output, level 0 first
  *   counts_d  int32 [NL] output (may be NULL)

@@ -100,6 +100,9 @@ def load(path: str = LIB_PATH):
             "ws_poll": ([P, ctypes.c_uint64, ctypes.c_int64], I),
             "ws_cancel": ([P, ctypes.c_uint64], I),
             "ws_server_destroy": ([P], None),
+            "ws_region_graph": ([P, P, P, I, SH, I, P, I, I, ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ctypes.c_int64), P], I),
+            "ws_region_graph_read": ([P, P, P, P, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -255,6 +258,45 @@ class Context:
         self._ok(self.lib.ws_waterfall(self.handle, _dev(labels0), _dev(grad), _dtype_code(grad), ctypes.byref(sh),
                                        int(conn), int(NL), _dev(levels), _dev(counts), _stream(stream)))
         return levels[: NL - 1], counts
+
+    def region_graph(self, labels, grad, conn: int, values=None, stream=None):
+        """Region graph of one labelling (ws_region_graph + ws_region_graph_read).
+        values: None or a (C, *shape) / shape-sized uint8 or uint16 CUDA tensor.
+        Returns a dict of CUDA tensors: row_ptr int64[K+1], col int32[nnz],
+        pass int32[nnz] (the uint32 pass values, all below 2^16), size int64[K],
+        sum int64[K, C] (uint64 sums, all below 2^63), mean float64[K, C]."""
+        import torch
+        if labels.dtype != torch.int32 or tuple(labels.shape) != tuple(grad.shape):
+            raise TypeError("labels must be int32 with the gradient's shape")
+        C, vptr, vcode = 0, None, WS_U8
+        if values is not None:
+            if values.dtype not in (torch.uint8, torch.uint16):
+                raise TypeError("values must be uint8 or uint16")
+            C = values.numel() // grad.numel()
+            if C * grad.numel() != values.numel():
+                raise ValueError("values must hold whole planes of the image")
+            vptr, vcode = _dev(values), _dtype_code(values)
+        sh = _shape_of(grad.shape)
+        K, nnz = ctypes.c_int64(), ctypes.c_int64()
+        st = _stream(stream)
+        self._ok(self.lib.ws_region_graph(self.handle, _dev(labels), _dev(grad), _dtype_code(grad),
+                                          ctypes.byref(sh), int(conn), vptr, vcode, C, ctypes.byref(K),
+                                          ctypes.byref(nnz), st))
+        K, nnz = K.value, nnz.value
+        dev = grad.device
+        out = {"row_ptr": torch.empty(K + 1, dtype=torch.int64, device=dev),
+               "col": torch.empty(max(nnz, 1), dtype=torch.int32, device=dev),
+               "pass": torch.empty(max(nnz, 1), dtype=torch.int32, device=dev),
+               "size": torch.empty(K, dtype=torch.int64, device=dev),
+               "sum": torch.empty((K, max(C, 1)), dtype=torch.int64, device=dev),
+               "mean": torch.empty((K, max(C, 1)), dtype=torch.float64, device=dev)}
+        self._ok(self.lib.ws_region_graph_read(self.handle, _dev(out["row_ptr"]), _dev(out["col"]),
+                                               _dev(out["pass"]), _dev(out["size"]),
+                                               _dev(out["sum"]) if C else None,
+                                               _dev(out["mean"]) if C else None, st))
+        out["col"], out["pass"] = out["col"][:nnz], out["pass"][:nnz]
+        out["sum"], out["mean"] = out["sum"][:, :C], out["mean"][:, :C]
+        return out
 
     def segment(self, grad, conn: int, NL: int, levels=None, counts=None, stream=None):
         import torch

@@ -229,7 +229,8 @@ PhaseScope::~PhaseScope()
 
 static const char *const PHASE_NAMES[NPHASE] = {"step1",       "plateau", "resolve_union", "jump",
                                                 "compact",     "rag",     "levels",        "level_write",
-                                                "cleanup",     "gradient", "copy",          "chase"};
+                                                "cleanup",     "gradient", "copy",          "chase",
+                                                "export"};
 
 ws_status ensure_ends(ws_context *c, size_t N, size_t ntiles)
 {
@@ -253,6 +254,61 @@ ws_status ensure_ends(ws_context *c, size_t N, size_t ntiles)
         w.ntends = grown(ntiles, have, false);
         if ((st = dalloc(c, &w.tends, w.ntends * 8))) {
             w.ntends = 0;
+            return st;
+        }
+    }
+    return WS_OK;
+}
+
+// Region-graph export arrays: K regions (node sizes and CSR row starts), `sums`
+// value sums, `entries` directed edge entries (two key/value buffers for the
+// radix sort, digit counts of 4096-entry tiles).
+ws_status ensure_rgraph(ws_context *c, size_t K, size_t sums, size_t entries)
+{
+    Workspace::RGraph &r = c->w.rg;
+    ws_status st;
+    if (!r.misc && (st = dalloc(c, &r.misc, 16))) return st;
+    if (K > r.kcap) {
+        const size_t have = r.kcap;
+        dfree(c, &r.size, r.kcap * 8);
+        dfree(c, &r.row, (r.kcap + 1) * 4);
+        r.kcap = grown(K, have, false);
+        if ((st = dalloc(c, &r.size, r.kcap * 8)) || (st = dalloc(c, &r.row, (r.kcap + 1) * 4))) {
+            dfree(c, &r.size, r.kcap * 8);
+            r.kcap = 0;
+            return st;
+        }
+    }
+    if (sums > r.scap) {
+        const size_t have = r.scap;
+        dfree(c, &r.sum, r.scap * 8);
+        r.scap = grown(sums, have, false);
+        if ((st = dalloc(c, &r.sum, r.scap * 8))) {
+            r.scap = 0;
+            return st;
+        }
+    }
+    if (entries > r.ecap) {
+        const size_t have = r.ecap;
+        for (int i = 0; i < 2; i++) {
+            dfree(c, &r.key[i], r.ecap * 8);
+            dfree(c, &r.val[i], r.ecap * 4);
+        }
+        dfree(c, &r.hist, r.hcap * 4);
+        dfree(c, &r.hsum, (r.hcap / 2048 + 2) * 4);
+        r.ecap = grown(entries, have, false);
+        r.hcap = 256 * ((r.ecap + 4095) / 4096);
+        for (int i = 0; i < 2; i++)
+            if ((st = dalloc(c, &r.key[i], r.ecap * 8)) || (st = dalloc(c, &r.val[i], r.ecap * 4))) break;
+        if (st == WS_OK && !(st = dalloc(c, &r.hist, r.hcap * 4))) st = dalloc(c, &r.hsum, (r.hcap / 2048 + 2) * 4);
+        if (st) {
+            for (int i = 0; i < 2; i++) {
+                dfree(c, &r.key[i], r.ecap * 8);
+                dfree(c, &r.val[i], r.ecap * 4);
+            }
+            dfree(c, &r.hist, r.hcap * 4);
+            dfree(c, &r.hsum, (r.hcap / 2048 + 2) * 4);
+            r.ecap = r.hcap = 0;
             return st;
         }
     }
@@ -387,6 +443,10 @@ void ws_context_destroy(ws_context *c)
                     w.gmap,  w.newmin, w.uf,     w.rank,   w.bsum,   w.kcount, w.grad_stage, w.levels_stage,
                     w.counts_stage, w.descs, w.rbase, w.lcount, w.ea, w.eb, w.ecnt, w.code, w.ends, w.tends};
     for (void *p : ptrs)
+        if (p) cudaFree(p);
+    const Workspace::RGraph &r = w.rg;
+    void *rptrs[] = {r.size, r.sum, r.row, r.key[0], r.key[1], r.val[0], r.val[1], r.hist, r.hsum, r.misc};
+    for (void *p : rptrs)
         if (p) cudaFree(p);
     for (auto &r : c->prof.pending) {
         cudaEventDestroy(r.a);
@@ -545,6 +605,37 @@ ws_status ws_waterfall(ws_context *c, const int32_t *labels0_d, const void *grad
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = launch_count_labels(c, labels0_d, g.N, s))) return st;
     return L->waterfall(c, labels0_d, grad_d, g, NL, levels_d, counts_d, (size_t)g.N, s);
+}
+
+ws_status ws_region_graph(ws_context *c, const int32_t *labels_d, const void *grad_d, ws_dtype dtype,
+                          const ws_shape *shape, int conn, const void *values_d, ws_dtype values_dtype, int channels,
+                          int64_t *regions, int64_t *entries, ws_stream_t stream)
+{
+    Geo g;
+    const Launchers *L = nullptr;
+    ws_status st = prep(c, grad_d, dtype, shape, conn, &g, &L);
+    if (st) return st;
+    if (!labels_d) return set_error(c, WS_ERR_INVALID, "NULL labels");
+    if (channels < 0 || channels > 65536) return set_error(c, WS_ERR_INVALID, "channels must be in 0..65536");
+    if (channels > 0 && !values_d) return set_error(c, WS_ERR_INVALID, "NULL values with channels > 0");
+    if (channels > 0 && values_dtype != WS_U8 && values_dtype != WS_U16)
+        return set_error(c, WS_ERR_INVALID, "values dtype must be WS_U8 or WS_U16");
+    long long K = 0, n = 0;
+    st = region_graph_build(c, labels_d, grad_d, dtype, g, conn, values_d, values_dtype, channels, &K, &n,
+                            (cudaStream_t)stream);
+    if (st) return st;
+    if (regions) *regions = K;
+    if (entries) *entries = n;
+    return WS_OK;
+}
+
+ws_status ws_region_graph_read(ws_context *c, int64_t *row_ptr_d, int32_t *col_d, uint32_t *pass_d,
+                               int64_t *size_d, uint64_t *sum_d, double *mean_d, ws_stream_t stream)
+{
+    if (!c) return WS_ERR_INVALID;
+    c->err.clear();
+    cudaSetDevice(c->device);
+    return region_graph_read(c, row_ptr_d, col_d, pass_d, size_d, sum_d, mean_d, (cudaStream_t)stream);
 }
 
 ws_status ws_segment(ws_context *c, const void *grad_d, ws_dtype dtype, const ws_shape *shape, int conn, int NL,

@@ -68,6 +68,23 @@ struct Workspace {
     int32_t *bsum = nullptr;        // per-block sums for device-wide scans [4096]
     int32_t *kcount = nullptr;      // K0 of the last watershed [1]
     int32_t *lcount = nullptr;      // region count per level of the last batch [kMaxLevels]
+    // region-graph export (ws_region_graph): the last graph built
+    struct RGraph {
+        long long K = 0, nnz = 0;   // regions, directed entries (twice the edges)
+        int C = 0;                  // value channels
+        int valid = 0;              // a graph is held
+        int sorted = 0;             // which key/val buffer holds the sorted entries
+        int shift = 0;              // bits of a column in a key
+        size_t kcap = 0, scap = 0, ecap = 0, hcap = 0;
+        unsigned long long *size = nullptr;   // pixels per region          [kcap]
+        unsigned long long *sum = nullptr;    // value sums, region-major   [scap]
+        int32_t *row = nullptr;               // CSR row starts             [kcap + 1]
+        unsigned long long *key[2] = {};      // (row << shift | col)       [ecap]
+        uint32_t *val[2] = {};                // pass values                [ecap]
+        int32_t *hist = nullptr;              // radix digit counts, then offsets [hcap]
+        int32_t *hsum = nullptr;              // scan chunk sums            [hcap / 2048 + 2]
+        int32_t *misc = nullptr;              // largest id, negative-id flag, edges, K [4]
+    } rg;
     // host-copy staging for ws_segment_host
     size_t host_n = 0, grad_n = 0;
     uint8_t *grad_stage = nullptr;  // device copy of a host gradient
@@ -89,6 +106,7 @@ enum Phase {
     PH_GRADIENT,      // blur + Sobel
     PH_COPY,          // host <-> device copies of ws_segment_host
     PH_CHASE,         // roots of the 3D tiles' path ends
+    PH_EXPORT,        // region-graph export
     NPHASE
 };
 
@@ -150,6 +168,7 @@ ws_status ensure_edges(ws_context *c, size_t cap);
 ws_status ensure_regions(ws_context *c, size_t kmax, int levels);
 ws_status ensure_batch(ws_context *c, size_t n);
 ws_status ensure_ends(ws_context *c, size_t N, size_t ntiles);
+ws_status ensure_rgraph(ws_context *c, size_t K, size_t sums, size_t entries);
 ws_status set_error_msg(ws_context *c, ws_status st, const char *msg);
 ws_status set_cuda_error(ws_context *c, cudaError_t e, const char *what);
 
@@ -180,6 +199,14 @@ const Launchers *launchers_u16(int conn);
 
 // K0 = max(labels) + 1 into c->w.kcount (ws_gradient.cu).
 ws_status launch_count_labels(ws_context *c, const int32_t *labels, int N, cudaStream_t s);
+
+// Region-graph export (ws_rgraph.cu): builds the graph of `labels` into c->w.rg
+// and returns K and the directed entry count (synchronises the stream).
+ws_status region_graph_build(ws_context *c, const int32_t *labels, const void *grad, int dtype, const Geo &g,
+                             int conn, const void *values, int vdtype, int C, long long *K, long long *nnz,
+                             cudaStream_t s);
+ws_status region_graph_read(ws_context *c, int64_t *row_ptr, int32_t *col, uint32_t *pass, int64_t *size,
+                            uint64_t *sum, double *mean, cudaStream_t s);
 
 // Gradient (ws_gradient.cu).
 ws_status launch_gradient(ws_context *c, const uint8_t *img, int W, int H, int shift, uint8_t *grad,
