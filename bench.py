@@ -255,7 +255,8 @@ def run_small_configs(ctx, torch, reps=20):
     """Configs 0 and 1 (the 2D cases): 256^2 blob image, gradient + watershed +
     NL=3 (latency, us); 4096^2 blob gradient quantised to 16 levels, 4- and
     8-connectivity, NL=6 (Gpx/s and the algorithmic HBM fraction, b + 4 NL =
-    25 B/px); and a 512^3 volume in 6- and 26-connectivity.  Device-resident
+    25 B/px); a 512^3 volume in 6- and 26-connectivity; the region-graph export of
+    two of its level planes.  Device-resident
     inputs; median of `reps` CUDA-event timings."""
     import statistics
     from paper_2410_08946_gb300 import synth
@@ -312,6 +313,19 @@ def run_small_configs(ctx, torch, reps=20):
             "workload": f"3D 512^3 uint16 distance volume, {conn}-connectivity, watershed + waterfall NL={NL}",
             "ms_median": med, "gvox_s": side ** 3 / med / 1e6,
             "alg_hbm_frac": (2 + 4 * NL) * side ** 3 / (med / 1e3) / 1e9 / peak, "levels_counts": c2.cpu().tolist()}
+        if conn == 6:
+            # region-graph export (the Sec. 6 graph) of level planes 0 and 3, the gradient as
+            # the one value channel; algorithmic bytes: labels 4 + G 2 + values 2 per voxel
+            for k in (0, 3):
+                med, best = timed(lambda: ctx.region_graph(lv2[k], v, conn, values=v))
+                G = ctx.region_graph(lv2[k], v, conn, values=v)
+                out[f"region_graph512_level{k}"] = {
+                    "workload": f"region graph of level {k} of the 512^3 6-connectivity segmentation: CSR with "
+                                "pass values, sizes, sums and means of one uint16 channel",
+                    "ms_median": med, "gvox_s": side ** 3 / med / 1e6, "regions": int(G["size"].numel()),
+                    "edges": int(G["col"].numel()) // 2,
+                    "alg_hbm_frac": 8 * side ** 3 / (med / 1e3) / 1e9 / peak}
+                del G
     del lv2, v
     torch.cuda.empty_cache()
     return out

@@ -7,9 +7,9 @@
 // count and the per-channel sums of a value image.
 //
 //   k_label_range    the largest id (K = largest + 1), and a flag for negative ids
-//   k_region_stats   pixel count and value sums per region: lanes holding the
-//                    same id combine (match_any, reduce_add), one lane per id
-//                    adds to global memory
+//   k_region_stats   pixel count and value sums per region: runs of equal ids
+//                    in each thread's 8 pixels, the last run combined across
+//                    the warp (match_any, reduce_add) before its atomic
 //   k_rag            (shared with ws_waterfall) the distinct region pairs with
 //                    their smallest pixel-pair height, into the region table;
 //   k_edges_compact  the table to a dense list of (a < b, pass)
@@ -55,24 +55,88 @@ __global__ void k_put_int(int32_t *p, int v)
     if (blockIdx.x == 0 && threadIdx.x == 0) *p = v;
 }
 
-template <typename V>
+// Each thread takes 8 consecutive pixels and adds up runs of equal ids; a run
+// that ends inside the 8 goes to global memory at once, the thread's last run
+// is first combined across the warp (lanes with the same id: match_any,
+// reduce_add), so a region that covers whole warps costs one atomic per 256
+// pixels.  VEC: 16-byte label loads and one vector load of values per channel
+// (pointers 16-byte aligned, N a multiple of 8).
+constexpr int SPIX = 8;
+
+template <typename V, bool VEC>
 __global__ void __launch_bounds__(NTHR) k_region_stats(const int32_t *__restrict__ L, const V *__restrict__ vals,
                                                        long long N, int C, unsigned long long *size,
                                                        unsigned long long *sum)
 {
     const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * NTHR;
-    for (long long base = (long long)blockIdx.x * NTHR; base < N; base += stride) {
-        const long long p = base + threadIdx.x;
-        const bool in = p < N;
-        const int r = in ? L[p] : -1;
-        const unsigned grp = __match_any_sync(0xffffffffu, r);
-        const bool lead = in && lane == __ffs(grp) - 1;
-        if (lead) atomicAdd(size + r, (unsigned long long)__popc(grp));
+    const long long nch = (N + SPIX - 1) / SPIX;
+    for (long long q0 = (long long)blockIdx.x * NTHR; q0 < nch; q0 += (long long)gridDim.x * NTHR) {
+        const long long p0 = (q0 + threadIdx.x) * SPIX;
+        const bool full = p0 + SPIX <= N;
+        int lab[SPIX];
+        if (VEC && full) {
+            const int4 u = *reinterpret_cast<const int4 *>(L + p0);
+            const int4 w = *reinterpret_cast<const int4 *>(L + p0 + 4);
+            lab[0] = u.x; lab[1] = u.y; lab[2] = u.z; lab[3] = u.w;
+            lab[4] = w.x; lab[5] = w.y; lab[6] = w.z; lab[7] = w.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < SPIX; j++) lab[j] = p0 + j < N ? L[p0 + j] : -1;
+        }
+        // sizes
+        int cur = lab[0];
+        unsigned cnt = 0;
+#pragma unroll
+        for (int j = 0; j < SPIX; j++) {
+            if (lab[j] != cur) {
+                if (cur >= 0) atomicAdd(size + cur, (unsigned long long)cnt);
+                cur = lab[j];
+                cnt = 0;
+            }
+            cnt += lab[j] >= 0;
+        }
+        const unsigned grp = __match_any_sync(0xffffffffu, cur);
+        const bool lead = cur >= 0 && lane == __ffs(grp) - 1;
+        const unsigned tot = __reduce_add_sync(grp, cnt);
+        if (lead) atomicAdd(size + cur, (unsigned long long)tot);
+        // value sums, channel by channel (the same runs)
         for (int c = 0; c < C; c++) {
-            const unsigned v = in ? (unsigned)vals[(size_t)c * N + p] : 0u;
-            const unsigned s = __reduce_add_sync(grp, v);   // <= 32 * 65535
-            if (lead) atomicAdd(sum + (size_t)r * C + c, (unsigned long long)s);
+            const V *vp = vals + (size_t)c * N + p0;
+            unsigned v[SPIX];
+            if (VEC && full) {
+                if constexpr (sizeof(V) == 2) {
+                    const uint4 u = *reinterpret_cast<const uint4 *>(vp);
+                    const unsigned w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        v[2 * j] = w4[j] & 0xffffu;
+                        v[2 * j + 1] = w4[j] >> 16;
+                    }
+                } else {
+                    const uint2 u = *reinterpret_cast<const uint2 *>(vp);
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        v[j] = (u.x >> (8 * j)) & 0xffu;
+                        v[4 + j] = (u.y >> (8 * j)) & 0xffu;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < SPIX; j++) v[j] = p0 + j < N ? (unsigned)vp[j] : 0u;
+            }
+            int cr = lab[0];
+            unsigned sm = 0;
+#pragma unroll
+            for (int j = 0; j < SPIX; j++) {
+                if (lab[j] != cr) {
+                    if (cr >= 0) atomicAdd(sum + (size_t)cr * C + c, (unsigned long long)sm);
+                    cr = lab[j];
+                    sm = 0;
+                }
+                sm += v[j];   // 0 past the end
+            }
+            const unsigned st = __reduce_add_sync(grp, sm);   // <= 32 * 8 * 65535
+            if (lead) atomicAdd(sum + (size_t)cur * C + c, (unsigned long long)st);
         }
     }
 }
@@ -277,10 +341,17 @@ ws_status region_graph_build(ws_context *c, const int32_t *L, const void *grad, 
         e = cudaMemsetAsync(r.size, 0, (size_t)K * 8, s);
         if (e == cudaSuccess && C > 0) e = cudaMemsetAsync(r.sum, 0, (size_t)K * C * 8, s);
         if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
-        if (vdtype == WS_U16)
-            k_region_stats<uint16_t><<<grid_for(c, N), NTHR, 0, s>>>(L, (const uint16_t *)values, N, C, r.size, r.sum);
-        else
-            k_region_stats<uint8_t><<<grid_for(c, N), NTHR, 0, s>>>(L, (const uint8_t *)values, N, C, r.size, r.sum);
+        const bool vec = ((uintptr_t)L & 15) == 0 && ((uintptr_t)values & 15) == 0 && N % SPIX == 0;
+        const int sg = grid_for(c, (N + SPIX - 1) / SPIX);
+        if (vdtype == WS_U16) {
+            const uint16_t *vv = (const uint16_t *)values;
+            if (vec) k_region_stats<uint16_t, true><<<sg, NTHR, 0, s>>>(L, vv, N, C, r.size, r.sum);
+            else k_region_stats<uint16_t, false><<<sg, NTHR, 0, s>>>(L, vv, N, C, r.size, r.sum);
+        } else {
+            const uint8_t *vv = (const uint8_t *)values;
+            if (vec) k_region_stats<uint8_t, true><<<sg, NTHR, 0, s>>>(L, vv, N, C, r.size, r.sum);
+            else k_region_stats<uint8_t, false><<<sg, NTHR, 0, s>>>(L, vv, N, C, r.size, r.sum);
+        }
         const bool ok = dtype == WS_U16 ? launch_rag_conn<uint16_t>(c, grad, geo, conn, L, s)
                                         : launch_rag_conn<uint8_t>(c, grad, geo, conn, L, s);
         if (!ok) return set_error_msg(c, WS_ERR_UNSUPPORTED, "connectivity");
