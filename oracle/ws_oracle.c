@@ -31,7 +31,7 @@
  *   R4  the waterfall is the graph form: level k+1 joins every pair of level-k
  *       regions whose lowest pass (Alg. 5 step V) is the lowest pass of one of
  *       the two; NL counts level 0 (Sec. 4, the NL definition).
- *   R5  the region graph handed to a graph network (Sec. 6, waterfall regions
+ *   R10 the region graph handed to a graph network (Sec. 6, waterfall regions
  *       in place of superpixels): one node per region id 0..K-1 of a labelling,
  *       an edge between two regions exactly when a pixel of one has a pixel of
  *       the other in N(p), weighted by pass(A,B) of Alg. 5 step V; node
@@ -594,7 +594,7 @@ int orc_segment(const void *grad, int bps, int ndim, const int64_t *dims, int co
 }
 
 /* ------------------------------------------------------------------------ */
-/* G: region graph of one labelling (reading R5)                             */
+/* G: region graph of one labelling (reading R10)                             */
 /* ------------------------------------------------------------------------ */
 
 /*
