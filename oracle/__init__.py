@@ -17,6 +17,8 @@ Parity status per function (pins are in tests/test_oracle_*.py):
                         simulation, invariants, 1D property of Sec. 3.1)
   waterfall ........... pinned (brute force on tiny images, invariants)
   gradient2d .......... pinned by closed forms only (the paper names no operator)
+  waterfall_reconstruct pinned (hand-derived 1D example, a Python replay of
+                        Alg. 5 steps V-VI over all pixel pairs between watersheds)
   region_graph ........ pinned (brute force over all pixel pairs on tiny images,
                         closed-form block grids, a hand-worked example, the
                         lowest-pass rule reproducing the pinned waterfall)
@@ -68,8 +70,10 @@ def _load():
         lib.orc_waterfall.argtypes = [P, P, I, I, P, I, I, P, P]
         lib.orc_segment.argtypes = [P, I, I, P, I, I, P, P]
         lib.orc_region_graph.argtypes = [P, P, I, I, P, I, P, I, I, i64, P, P, P, i64, P, P, P, P]
+        lib.orc_waterfall_reconstruct.argtypes = [P, I, I, P, I, I, P, P]
         for f in ("orc_gradient2d", "orc_step1", "orc_plateau_distance", "orc_watershed",
-                  "orc_roots_without_merge", "orc_waterfall", "orc_segment", "orc_region_graph"):
+                  "orc_roots_without_merge", "orc_waterfall", "orc_segment", "orc_region_graph",
+                  "orc_waterfall_reconstruct"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -189,6 +193,17 @@ def segment(grad: np.ndarray, conn: int, NL: int):
     levels = np.empty((NL,) + g.shape, dtype=np.int32)
     counts = np.empty(NL, dtype=np.int32)
     _check(_load().orc_segment(_ptr(g), bps, ndim, _ptr(dims), conn, NL, _ptr(levels), _ptr(counts)))
+    return levels, counts
+
+
+def waterfall_reconstruct(grad: np.ndarray, conn: int, NL: int):
+    """Paper-literal waterfall (Alg. 4 with Alg. 5's image reconstruction).
+    Returns (levels[NL, *shape] int32, counts[NL])."""
+    g, bps, ndim, dims = _prep(grad)
+    levels = np.empty((NL,) + g.shape, dtype=np.int32)
+    counts = np.empty(NL, dtype=np.int32)
+    _check(_load().orc_waterfall_reconstruct(_ptr(g), bps, ndim, _ptr(dims), conn, NL, _ptr(levels),
+                                             _ptr(counts)))
     return levels, counts
 
 

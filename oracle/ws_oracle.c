@@ -31,6 +31,9 @@
  *   R4  the waterfall is the graph form: level k+1 joins every pair of level-k
  *       regions whose lowest pass (Alg. 5 step V) is the lowest pass of one of
  *       the two; NL counts level 0 (Sec. 4, the NL definition).
+ *   R11 the paper-literal waterfall (Alg. 4 with Alg. 5's reconstruction):
+ *       the constant M of step V is the sample type's maximum (255 / 65535),
+ *       so a region without neighbours is raised to that maximum;
  *   R10 the region graph handed to a graph network (Sec. 6, waterfall regions
  *       in place of superpixels): one node per region id 0..K-1 of a labelling,
  *       an edge between two regions exactly when a pixel of one has a pixel of
@@ -676,4 +679,69 @@ int orc_region_graph(const int32_t *L, const void *grad, int bps, int ndim, cons
     *nnz_out = nnz;
     free(pairs);
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* P: paper-literal waterfall by image reconstruction (reading R11)          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Hierarchy of Alg. 4 with the image reconstruction of Alg. 5: level 0 is the
+ * watershed of I = G; while a next level is wanted,
+ *   step V:  newmin(A) = the smallest height(p, q) = max(I(p), I(q)) over
+ *            pixels p of A and neighbours q of p in another region (M, the
+ *            sample type's maximum, when A has no such pair);
+ *   step VI: I(p) = newmin(L(p)) wherever I(p) < newmin(L(p));
+ * and level n+1 is the watershed of the raised image.  levels holds NL planes
+ * (level 0 first), counts the region count of each.  Unlike the graph form,
+ * a level need not be a union of regions of the level below.
+ */
+int orc_waterfall_reconstruct(const void *grad, int bps, int ndim, const int64_t *dims, int conn, int NL,
+                              int32_t *levels, int32_t *counts)
+{
+    geom_t g;
+    if (geom_init(&g, ndim, dims, conn) != ORC_OK || (bps != 1 && bps != 2) || NL < 1) return ORC_EINVAL;
+    const int64_t N = g.N;
+    const uint32_t M = bps == 1 ? 0xffu : 0xffffu;
+    void *img = malloc((size_t)N * (size_t)bps);
+    uint32_t *newmin = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(N + 1));
+    int rc = ORC_ENOMEM;
+    if (!img || !newmin) goto out;
+    memcpy(img, grad, (size_t)N * (size_t)bps);
+    for (int n = 0; n < NL; n++) {
+        int32_t *L = levels + (int64_t)n * N;
+        int32_t K;
+        rc = orc_watershed(img, bps, ndim, dims, conn, L, &K, NULL, NULL, NULL);
+        if (rc != ORC_OK) goto out;
+        counts[n] = K;
+        if (n == NL - 1) break;
+        /* step V */
+        for (int64_t A = 0; A < K; A++) newmin[A] = M;
+        int64_t nb[26];
+        for (int64_t p = 0; p < N; p++) {
+            int m = neighbours(&g, p, nb);
+            for (int i = 0; i < m; i++) {
+                int64_t q = nb[i];
+                if (L[q] == L[p]) continue;
+                uint32_t a = sample(img, bps, p), b = sample(img, bps, q);
+                uint32_t h = a > b ? a : b;
+                if (h < newmin[L[p]]) newmin[L[p]] = h;
+            }
+        }
+        /* step VI */
+        for (int64_t p = 0; p < N; p++) {
+            uint32_t v = sample(img, bps, p);
+            if (v < newmin[L[p]]) {
+                if (bps == 1)
+                    ((uint8_t *)img)[p] = (uint8_t)newmin[L[p]];
+                else
+                    ((uint16_t *)img)[p] = (uint16_t)newmin[L[p]];
+            }
+        }
+    }
+    rc = ORC_OK;
+out:
+    free(img);
+    free(newmin);
+    return rc;
 }
