@@ -181,6 +181,22 @@ ws_status ws_waterfall(ws_context *ctx, const int32_t *labels0_d, const void *gr
                        int32_t *counts_d, ws_stream_t stream);
 
 /*
+ * The paper's own waterfall (Alg. 4 with the image reconstruction of Alg. 5):
+ * level 0 is the watershed of G; for every further level, step V takes each
+ * region's lowest pass newmin(A) (the smallest max(I(p), I(q)) over its
+ * border pairs; M = 255 / 65535 when A has no neighbour), step VI raises every
+ * pixel below newmin(L(p)) to it, and the watershed of the raised image is the
+ * next level.  Unlike ws_segment's graph form, a level need not be a union of
+ * regions of the level below (a pixel can change basin).  The caller's
+ * gradient is not modified (the raised image lives in the workspace).
+ *   levels_d  int32 [NL*N] output, level 0 first, canonical ids per level
+ *   counts_d  int32 [NL] output (may be NULL);  1 <= NL <= 64
+ */
+ws_status ws_waterfall_reconstruct(ws_context *ctx, const void *grad_d, ws_dtype dtype, const ws_shape *shape,
+                                   int connectivity, int NL, int32_t *levels_d, int32_t *counts_d,
+                                   ws_stream_t stream);
+
+/*
  * Region graph of one labelling, for graph-network pre-processing (Sec. 6: the
  * regions of a waterfall level replace superpixels as the nodes of the graph).
  * Node A is region id A (0..K-1, K = largest id + 1; ids no pixel carries are

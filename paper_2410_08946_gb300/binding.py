@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
             "ws_region_graph": ([P, P, P, I, SH, I, P, I, I, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64), P], I),
             "ws_region_graph_read": ([P, P, P, P, P, P, P, P], I),
+            "ws_waterfall_reconstruct": ([P, P, I, SH, I, I, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -258,6 +259,17 @@ class Context:
         self._ok(self.lib.ws_waterfall(self.handle, _dev(labels0), _dev(grad), _dtype_code(grad), ctypes.byref(sh),
                                        int(conn), int(NL), _dev(levels), _dev(counts), _stream(stream)))
         return levels[: NL - 1], counts
+
+    def waterfall_reconstruct(self, grad, conn: int, NL: int, levels=None, counts=None, stream=None):
+        """Paper-literal waterfall (ws_waterfall_reconstruct): NL label planes."""
+        import torch
+        if levels is None:
+            levels = torch.empty((NL,) + tuple(grad.shape), dtype=torch.int32, device=grad.device)
+        counts = torch.empty(NL, dtype=torch.int32, device=grad.device) if counts is None else counts
+        sh = _shape_of(grad.shape)
+        self._ok(self.lib.ws_waterfall_reconstruct(self.handle, _dev(grad), _dtype_code(grad), ctypes.byref(sh),
+                                                   int(conn), int(NL), _dev(levels), _dev(counts), _stream(stream)))
+        return levels, counts
 
     def region_graph(self, labels, grad, conn: int, values=None, stream=None):
         """Region graph of one labelling (ws_region_graph + ws_region_graph_read).

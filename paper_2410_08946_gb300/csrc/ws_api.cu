@@ -230,7 +230,7 @@ PhaseScope::~PhaseScope()
 static const char *const PHASE_NAMES[NPHASE] = {"step1",       "plateau", "resolve_union", "jump",
                                                 "compact",     "rag",     "levels",        "level_write",
                                                 "cleanup",     "gradient", "copy",          "chase",
-                                                "export"};
+                                                "export",      "reconstruct"};
 
 ws_status ensure_ends(ws_context *c, size_t N, size_t ntiles)
 {
@@ -313,6 +313,18 @@ ws_status ensure_rgraph(ws_context *c, size_t K, size_t sums, size_t entries)
         }
     }
     return WS_OK;
+}
+
+ws_status ensure_rec(ws_context *c, size_t bytes)
+{
+    Workspace &w = c->w;
+    if (bytes <= w.rec_n) return WS_OK;
+    const size_t have = w.rec_n;
+    dfree(c, (uint8_t **)&w.rec, w.rec_n);
+    w.rec_n = grown(bytes, have, false);
+    ws_status st = dalloc(c, (uint8_t **)&w.rec, w.rec_n);
+    if (st) w.rec_n = 0;
+    return st;
 }
 
 ws_status ensure_batch(ws_context *c, size_t n)
@@ -445,7 +457,7 @@ void ws_context_destroy(ws_context *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     const Workspace::RGraph &r = w.rg;
-    void *rptrs[] = {r.size, r.sum, r.row, r.key[0], r.key[1], r.val[0], r.val[1], r.hist, r.hsum, r.misc};
+    void *rptrs[] = {r.size, r.sum, r.row, r.key[0], r.key[1], r.val[0], r.val[1], r.hist, r.hsum, r.misc, w.rec};
     for (void *p : rptrs)
         if (p) cudaFree(p);
     for (auto &r : c->prof.pending) {
@@ -605,6 +617,18 @@ ws_status ws_waterfall(ws_context *c, const int32_t *labels0_d, const void *grad
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = launch_count_labels(c, labels0_d, g.N, s))) return st;
     return L->waterfall(c, labels0_d, grad_d, g, NL, levels_d, counts_d, (size_t)g.N, s);
+}
+
+ws_status ws_waterfall_reconstruct(ws_context *c, const void *grad_d, ws_dtype dtype, const ws_shape *shape,
+                                   int conn, int NL, int32_t *levels_d, int32_t *counts_d, ws_stream_t stream)
+{
+    Geo g;
+    const Launchers *L = nullptr;
+    ws_status st = prep(c, grad_d, dtype, shape, conn, &g, &L);
+    if (st) return st;
+    if (!levels_d) return set_error(c, WS_ERR_INVALID, "NULL levels");
+    if (NL < 1 || NL > kMaxLevels) return set_error(c, WS_ERR_INVALID, "NL must be in 1..64");
+    return L->reconstruct(c, grad_d, g, NL, levels_d, counts_d, (cudaStream_t)stream);
 }
 
 ws_status ws_region_graph(ws_context *c, const int32_t *labels_d, const void *grad_d, ws_dtype dtype,

@@ -85,6 +85,9 @@ struct Workspace {
         int32_t *hsum = nullptr;              // scan chunk sums            [hcap / 2048 + 2]
         int32_t *misc = nullptr;              // largest id, negative-id flag, edges, K [4]
     } rg;
+    // reconstructed image of the paper-literal waterfall
+    size_t rec_n = 0;
+    void *rec = nullptr;
     // host-copy staging for ws_segment_host
     size_t host_n = 0, grad_n = 0;
     uint8_t *grad_stage = nullptr;  // device copy of a host gradient
@@ -107,6 +110,7 @@ enum Phase {
     PH_COPY,          // host <-> device copies of ws_segment_host
     PH_CHASE,         // roots of the 3D tiles' path ends
     PH_EXPORT,        // region-graph export
+    PH_RECON,         // image reconstruction (Alg. 5 steps V-VI)
     NPHASE
 };
 
@@ -169,6 +173,7 @@ ws_status ensure_regions(ws_context *c, size_t kmax, int levels);
 ws_status ensure_batch(ws_context *c, size_t n);
 ws_status ensure_ends(ws_context *c, size_t N, size_t ntiles);
 ws_status ensure_rgraph(ws_context *c, size_t K, size_t sums, size_t entries);
+ws_status ensure_rec(ws_context *c, size_t bytes);
 ws_status set_error_msg(ws_context *c, ws_status st, const char *msg);
 ws_status set_cuda_error(ws_context *c, cudaError_t e, const char *what);
 
@@ -188,6 +193,8 @@ struct Launchers {
                                const void *descs_dev, cudaStream_t);
     size_t desc_bytes;                // sizeof one image descriptor
     void (*descs)(int n, const Geo *geos, const ws_item *items, void *out);  // host descriptors, desc_bytes each
+    ws_status (*reconstruct)(ws_context *, const void *grad, const Geo &, int NL, int32_t *levels, int32_t *counts,
+                             cudaStream_t);
 };
 
 // dtype: 0 = u8, 1 = u16; conn: 4, 8, 6.  Returns nullptr when unsupported.

@@ -30,6 +30,9 @@
 //                    cooperative launch
 //   k_level_write    levels[k][p] = map_k[L0[p]] for all k in one pass
 //   k_edges_compact  region table -> dense edge list (and the table emptied)
+// ws_waterfall_reconstruct (the paper-literal hierarchy of Alg. 4):
+//   k_fill_newmin, k_newmin, k_raise
+//                    Alg. 5 steps V and VI between two watersheds
 #pragma once
 
 #include <cooperative_groups.h>
@@ -344,6 +347,60 @@ static __global__ void __launch_bounds__(NTHR) k_rag(const T *__restrict__ g, Ge
             unsigned hmin = __reduce_min_sync(grp, h);
             if (lane == __ffs(grp) - 1) edge_insert(key, hmin, keys, vals, slots, ecount, mask, status);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// paper-literal waterfall: image reconstruction (Alg. 5 steps V, VI)
+// ---------------------------------------------------------------------------
+
+// newmin[0..K) = ~0 (K read on the device: the watershed's region count).
+static __global__ void __launch_bounds__(NTHR) k_fill_newmin(uint32_t *newmin, const int32_t *kptr)
+{
+    const int K = *kptr;
+    for (int a = blockIdx.x * NTHR + threadIdx.x; a < K; a += gridDim.x * NTHR) newmin[a] = 0xffffffffu;
+}
+
+// Step V: newmin(L(p)) = min over neighbours q in another region of
+// max(I(p), I(q)).  Each unordered pixel pair is visited once (forward
+// neighbours) and lowers both regions; a lane reads the current value first
+// and issues the atomic only when it lowers it.
+template <typename T, int CONN>
+static __global__ void __launch_bounds__(NTHR) k_newmin(const T *__restrict__ I, Geo geo, const int32_t *__restrict__ L,
+                                                        uint32_t *newmin)
+{
+    for (int p = blockIdx.x * NTHR + threadIdx.x; p < geo.N; p += gridDim.x * NTHR) {
+        int x, y, z;
+        coords(geo, p, x, y, z);
+        const int A = L[p];
+        const unsigned ip = I[p];
+#pragma unroll
+        for (int i = Half<CONN>::first; i < Nb<CONN>::n; i++) {
+            int q;
+            if (!nb_at<CONN>(geo, x, y, z, i, q)) continue;
+            const int B = L[q];
+            if (B == A) continue;
+            const unsigned iq = I[q];
+            const unsigned h = ip > iq ? ip : iq;
+            if (h < __ldcg(newmin + A)) atomicMin(newmin + A, h);
+            if (h < __ldcg(newmin + B)) atomicMin(newmin + B, h);
+        }
+    }
+}
+
+// Step VI: out(p) = newmin(L(p)) where I(p) is below it, else I(p); a region
+// with no neighbour has newmin = M, the sample type's maximum.  in == out is
+// allowed (element-wise).
+template <typename T>
+static __global__ void __launch_bounds__(NTHR) k_raise(const T *in, T *out, const int32_t *__restrict__ L,
+                                                       const uint32_t *__restrict__ newmin, int N)
+{
+    constexpr unsigned M = sizeof(T) == 1 ? 0xffu : 0xffffu;
+    for (int p = blockIdx.x * NTHR + threadIdx.x; p < N; p += gridDim.x * NTHR) {
+        unsigned nm = __ldg(newmin + L[p]);
+        nm = nm < M ? nm : M;
+        const unsigned v = in[p];
+        out[p] = (T)(v < nm ? nm : v);
     }
 }
 

@@ -497,6 +497,40 @@ template <typename T, int CONN> static ws_status run_waterfall(ws_context *c, co
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "waterfall launch");
 }
 
+// ---------------------------------------------------------------------------
+// paper-literal waterfall: watershed, then image reconstruction, per level
+// ---------------------------------------------------------------------------
+
+// Level n is the watershed of I_n (I_0 = G); I_{n+1} is I_n raised by Alg. 5
+// steps V-VI into the workspace image w.rec (the caller's gradient is never
+// written).  counts: NL device ints (w.lcount when the caller gives none).
+template <typename T, int CONN> static ws_status run_reconstruct(ws_context *c, const void *grad, const Geo &geo,
+                                                                 int NL, int32_t *levels, int32_t *counts,
+                                                                 cudaStream_t s)
+{
+    Workspace &w = c->w;
+    ws_status st;
+    if (NL > 1) {
+        if ((st = ensure_rec(c, (size_t)geo.N * sizeof(T))) != WS_OK) return st;
+        if ((st = ensure_regions(c, (size_t)geo.N / 2 + 2, 1)) != WS_OK) return st;
+    }
+    int32_t *cnt = counts ? counts : w.lcount;
+    const void *I = grad;
+    for (int n = 0; n < NL; n++) {
+        int32_t *L = levels + (size_t)n * geo.N;
+        if ((st = run_watershed<T, CONN>(c, I, geo, L, cnt + n, s)) != WS_OK) return st;
+        if (n == NL - 1) break;
+        PhaseScope ps(c, PH_RECON, s);
+        k_fill_newmin<<<pixel_grid(c, geo.N / 2 + 2), NTHR, 0, s>>>(w.newmin, cnt + n);
+        k_newmin<T, CONN><<<pixel_grid(c, geo.N), NTHR, 0, s>>>((const T *)I, geo, L, w.newmin);
+        k_raise<T><<<pixel_grid(c, geo.N), NTHR, 0, s>>>((const T *)I, (T *)w.rec, L, w.newmin, geo.N);
+        c->launches += 3;
+        I = w.rec;
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "reconstruct launch");
+}
+
 template <int CONN> static void descs_host(int n, const Geo *geos, const ws_item *items, void *out)
 {
     std::vector<ImgDesc> v;
@@ -509,7 +543,8 @@ template <typename T, int CONN> struct Inst {
     {
         static const Launchers L = {&run_watershed<T, CONN>, &run_step1<T, CONN>, &run_plateau_distance<T, CONN>,
                                     &run_waterfall<T, CONN>, &run_segment<T, CONN>,
-                                    &run_segment_batch<T, CONN>, sizeof(ImgDesc), &descs_host<CONN>};
+                                    &run_segment_batch<T, CONN>, sizeof(ImgDesc), &descs_host<CONN>,
+                                    &run_reconstruct<T, CONN>};
         return &L;
     }
 };
