@@ -256,7 +256,7 @@ def run_small_configs(ctx, torch, reps=20):
     NL=3 (latency, us); 4096^2 blob gradient quantised to 16 levels, 4- and
     8-connectivity, NL=6 (Gpx/s and the algorithmic HBM fraction, b + 4 NL =
     25 B/px); a 512^3 volume in 6- and 26-connectivity; the region-graph export of
-    two of its level planes.  Device-resident
+    two of its level planes; the paper-literal waterfall on it.  Device-resident
     inputs; median of `reps` CUDA-event timings."""
     import statistics
     from paper_2410_08946_gb300 import synth
@@ -326,6 +326,36 @@ def run_small_configs(ctx, torch, reps=20):
                     "edges": int(G["col"].numel()) // 2,
                     "alg_hbm_frac": 8 * side ** 3 / (med / 1e3) / 1e9 / peak}
                 del G
+        if conn == 6:
+            # the paper-literal waterfall (Alg. 4 with Alg. 5's reconstruction) on the same volume,
+            # and how far it strays from the graph form: per level, the share of voxels outside the
+            # best-overlapping graph-form region of their literal region (a report, not the path)
+            lv3 = torch.empty_like(lv2)
+            c3 = torch.empty_like(c2)
+            med, best = timed(lambda: ctx.waterfall_reconstruct(v, conn, NL, lv3, c3))
+            ctx.segment(v, conn, NL, lv2, c2)
+            ctx.check()
+            ctx.phase_times()
+            ctx.set_profiling(True)
+            ctx.waterfall_reconstruct(v, conn, NL, lv3, c3)
+            rphases = {k: round(t[0], 3) for k, t in ctx.phase_times().items() if t[1]}
+            ctx.set_profiling(False)
+            ctx.check()
+            dis = []
+            for k in range(NL):
+                Kg = int(c2[k])
+                key = lv3[k].reshape(-1).long() * Kg + lv2[k].reshape(-1).long()
+                uniq, cnt = torch.unique(key, return_counts=True)
+                bestov = torch.zeros(int(c3[k]), dtype=torch.long, device="cuda")
+                bestov.scatter_reduce_(0, uniq // Kg, cnt, reduce="amax")
+                dis.append(1.0 - float(bestov.sum()) / side ** 3)
+                del key, uniq, cnt, bestov
+            out["reconstruct512_conn6"] = {
+                "workload": f"3D 512^3 uint16 distance volume, 6-connectivity, paper-literal waterfall (watershed "
+                            f"of each reconstructed image) NL={NL}",
+                "ms_median": med, "gvox_s": side ** 3 / med / 1e6, "levels_counts": c3.cpu().tolist(),
+                "graph_form_counts": c2.cpu().tolist(), "voxels_off_graph_form": dis, "phases_ms": rphases}
+            del lv3, c3
     del lv2, v
     torch.cuda.empty_cache()
     return out
