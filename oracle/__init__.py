@@ -17,6 +17,8 @@ Parity status per function (pins are in tests/test_oracle_*.py):
                         simulation, invariants, 1D property of Sec. 3.1)
   waterfall ........... pinned (brute force on tiny images, invariants)
   gradient2d .......... pinned by closed forms only (the paper names no operator)
+  gradient3d .......... pinned by closed forms, symmetries and the 2D operator
+                        on volumes constant along z
   waterfall_reconstruct pinned (hand-derived 1D example, a Python replay of
                         Alg. 5 steps V-VI over all pixel pairs between watersheds)
   region_graph ........ pinned (brute force over all pixel pairs on tiny images,
@@ -71,9 +73,10 @@ def _load():
         lib.orc_segment.argtypes = [P, I, I, P, I, I, P, P]
         lib.orc_region_graph.argtypes = [P, P, I, I, P, I, P, I, I, i64, P, P, P, i64, P, P, P, P]
         lib.orc_waterfall_reconstruct.argtypes = [P, I, I, P, I, I, P, P]
+        lib.orc_gradient3d.argtypes = [P, I, i64, i64, i64, I, P]
         for f in ("orc_gradient2d", "orc_step1", "orc_plateau_distance", "orc_watershed",
                   "orc_roots_without_merge", "orc_waterfall", "orc_segment", "orc_region_graph",
-                  "orc_waterfall_reconstruct"):
+                  "orc_waterfall_reconstruct", "orc_gradient3d"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -126,6 +129,17 @@ def gradient2d(img: np.ndarray, quant_shift: int = 0) -> np.ndarray:
     H, W = img.shape
     out = np.empty((H, W), dtype=np.uint8)
     _check(_load().orc_gradient2d(_ptr(img), W, H, int(quant_shift), _ptr(out)))
+    return out
+
+
+def gradient3d(vol: np.ndarray, shift: int = 0) -> np.ndarray:
+    """3D blur + Sobel + exact isqrt, >> shift, clip 65535: uint16 (D, H, W)."""
+    v = np.ascontiguousarray(vol)
+    if v.dtype not in (np.uint8, np.uint16) or v.ndim != 3:
+        raise TypeError("volume must be a 3D uint8 or uint16 array")
+    D, H, W = v.shape
+    out = np.empty((D, H, W), dtype=np.uint16)
+    _check(_load().orc_gradient3d(_ptr(v), v.dtype.itemsize, W, H, D, int(shift), _ptr(out)))
     return out
 
 

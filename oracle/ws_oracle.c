@@ -31,6 +31,8 @@
  *   R4  the waterfall is the graph form: level k+1 joins every pair of level-k
  *       regions whose lowest pass (Alg. 5 step V) is the lowest pass of one of
  *       the two; NL counts level 0 (Sec. 4, the NL definition).
+ *   R12 the 3D gradient: the 2D operators of orc_gradient2d extended to a
+ *       third axis (the paper names no operator for volumes either);
  *   R11 the paper-literal waterfall (Alg. 4 with Alg. 5's reconstruction):
  *       the constant M of step V is the sample type's maximum (255 / 65535),
  *       so a region without neighbours is raised to that maximum;
@@ -181,6 +183,55 @@ int orc_gradient2d(const uint8_t *img, int64_t W, int64_t H, int quant_shift, ui
             if (mag > 255) mag = 255;
             grad[y * W + x] = (uint8_t)(mag >> quant_shift);
         }
+    free(blur);
+    return ORC_OK;
+}
+
+/*
+ * The same two steps for a volume (reading R12: the 3D counterparts of the
+ * 2D operators): 5x5x5 binomial blur [1 4 6 4 1]^3 with round-half-up
+ * (sum + 2048) >> 12, 3x3x3 Sobel (central difference [-1 0 1] along one axis,
+ * [1 2 1] smoothing along the other two), exact floor square root of
+ * gx^2 + gy^2 + gz^2, shifted right by shift and clipped to 65535.  Borders
+ * replicate the edge voxel, for the blur and for the blurred volume.
+ * img: bps = 1 or 2 bytes per voxel, [D][H][W]; grad: uint16 [D][H][W].
+ */
+int orc_gradient3d(const void *img, int bps, int64_t W, int64_t H, int64_t D, int shift, uint16_t *grad)
+{
+    static const int w[5] = {1, 4, 6, 4, 1};
+    static const int sw[3] = {1, 2, 1};
+    if (W < 1 || H < 1 || D < 1 || shift < 0 || shift > 31 || (bps != 1 && bps != 2)) return ORC_EINVAL;
+    const int64_t N = W * H * D;
+    int64_t *blur = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    if (!blur) return ORC_ENOMEM;
+#define IDX(z, y, x) ((clampi((z), 0, D - 1) * H + clampi((y), 0, H - 1)) * W + clampi((x), 0, W - 1))
+    for (int64_t z = 0; z < D; z++)
+        for (int64_t y = 0; y < H; y++)
+            for (int64_t x = 0; x < W; x++) {
+                int64_t acc = 0;
+                for (int k = -2; k <= 2; k++)
+                    for (int j = -2; j <= 2; j++)
+                        for (int i = -2; i <= 2; i++)
+                            acc += (int64_t)w[k + 2] * w[j + 2] * w[i + 2] *
+                                   (int64_t)sample(img, bps, IDX(z + k, y + j, x + i));
+                blur[(z * H + y) * W + x] = (acc + 2048) >> 12;
+            }
+    for (int64_t z = 0; z < D; z++)
+        for (int64_t y = 0; y < H; y++)
+            for (int64_t x = 0; x < W; x++) {
+                int64_t gx = 0, gy = 0, gz = 0;
+                for (int a = -1; a <= 1; a++)
+                    for (int b = -1; b <= 1; b++) {
+                        const int64_t wt = (int64_t)sw[a + 1] * sw[b + 1];
+                        /* d/dx: (a, b) range over (z, y); d/dy: over (z, x); d/dz: over (y, x) */
+                        gx += wt * (blur[IDX(z + a, y + b, x + 1)] - blur[IDX(z + a, y + b, x - 1)]);
+                        gy += wt * (blur[IDX(z + a, y + 1, x + b)] - blur[IDX(z + a, y - 1, x + b)]);
+                        gz += wt * (blur[IDX(z + 1, y + a, x + b)] - blur[IDX(z - 1, y + a, x + b)]);
+                    }
+                uint64_t mag = orc_isqrt_u64((uint64_t)(gx * gx + gy * gy + gz * gz)) >> shift;
+                grad[(z * H + y) * W + x] = (uint16_t)(mag > 65535 ? 65535 : mag);
+            }
+#undef IDX
     free(blur);
     return ORC_OK;
 }
