@@ -256,7 +256,7 @@ def run_small_configs(ctx, torch, reps=20):
     NL=3 (latency, us); 4096^2 blob gradient quantised to 16 levels, 4- and
     8-connectivity, NL=6 (Gpx/s and the algorithmic HBM fraction, b + 4 NL =
     25 B/px); a 512^3 volume in 6- and 26-connectivity; the region-graph export of
-    two of its level planes; the paper-literal waterfall on it.  Device-resident
+    two of its level planes; the paper-literal waterfall on it; its 3D gradient.  Device-resident
     inputs; median of `reps` CUDA-event timings."""
     import statistics
     from paper_2410_08946_gb300 import synth
@@ -307,6 +307,13 @@ def run_small_configs(ctx, torch, reps=20):
     v = torch.from_numpy(synth.distance_volume(side, side, side, sample_seeds(side), seed=SEED)).cuda()
     lv2 = torch.empty((NL,) + tuple(v.shape), dtype=torch.int32, device="cuda")
     c2 = torch.empty(NL, dtype=torch.int32, device="cuda")
+    # 3D gradient (blur + Sobel magnitude) of the same volume: 2 B in + 2 B out per voxel
+    g3 = torch.empty_like(v)
+    med, best = timed(lambda: ctx.gradient3d(v, 0, out=g3))
+    out["gradient3d_512"] = {"workload": "3D gradient of the 512^3 uint16 volume: 5x5x5 binomial blur, 3x3x3 Sobel, "
+                                         "exact isqrt, uint16 out", "ms_median": med,
+                             "gvox_s": side ** 3 / med / 1e6, "alg_hbm_frac": 4 * side ** 3 / (med / 1e3) / 1e9 / peak}
+    del g3
     for conn in (6, 26):
         med, best = timed(lambda: ctx.segment(v, conn, NL, lv2, c2))
         out[f"volume512_conn{conn}"] = {

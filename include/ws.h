@@ -150,6 +150,18 @@ ws_status ws_gradient(ws_context *ctx, const uint8_t *img_d, const ws_shape *sha
                       uint8_t *grad_d, ws_stream_t stream);
 
 /*
+ * The same two steps for a volume (the paper names no operator; these are the
+ * 3D counterparts of ws_gradient's): 5x5x5 binomial blur [1 4 6 4 1]^3 with
+ * (sum + 2048) >> 12, 3x3x3 Sobel (central difference along one axis, [1 2 1]
+ * along the other two), exact floor square root of gx^2 + gy^2 + gz^2, then
+ * >> shift (0..31) and clipped to 65535.  Borders replicate the edge voxel.
+ *   vol_d   uint8 or uint16 (dtype) [D*H*W], shape->ndim must be 3
+ *   grad_d  uint16 [D*H*W] output; must not overlap vol_d
+ */
+ws_status ws_gradient3d(ws_context *ctx, const void *vol_d, ws_dtype dtype, const ws_shape *shape, int shift,
+                        uint16_t *grad_d, ws_stream_t stream);
+
+/*
  * Watershed, steps I-IV of Alg. 1 with the step II result of Sec. 3.3 / Alg. 3
  * (each non-minimal plateau pixel drains towards the nearest lower border of
  * its plateau; ties between equally near neighbours go to the larger pixel

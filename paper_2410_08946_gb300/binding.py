@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
                                  ctypes.POINTER(ctypes.c_int64), P], I),
             "ws_region_graph_read": ([P, P, P, P, P, P, P, P], I),
             "ws_waterfall_reconstruct": ([P, P, I, SH, I, I, P, P, P], I),
+            "ws_gradient3d": ([P, P, I, SH, I, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -222,6 +223,17 @@ class Context:
         sh = _shape_of(img.shape)
         self._ok(self.lib.ws_gradient(self.handle, _dev(img), ctypes.byref(sh), int(quant_shift), _dev(out),
                                       _stream(stream)))
+        return out
+
+    def gradient3d(self, vol, shift: int = 0, out=None, stream=None):
+        """3D blur + Sobel magnitude of a uint8 / uint16 volume -> uint16 volume."""
+        import torch
+        if vol.dim() != 3:
+            raise TypeError("gradient3d takes a 3D volume")
+        out = torch.empty(vol.shape, dtype=torch.uint16, device=vol.device) if out is None else out
+        sh = _shape_of(vol.shape)
+        self._ok(self.lib.ws_gradient3d(self.handle, _dev(vol), _dtype_code(vol), ctypes.byref(sh), int(shift),
+                                        _dev(out), _stream(stream)))
         return out
 
     def step1(self, grad, conn: int, stream=None):

@@ -570,6 +570,27 @@ ws_status ws_gradient(ws_context *c, const uint8_t *img_d, const ws_shape *shape
     return launch_gradient(c, img_d, g.W, g.H, quant_shift, grad_d, (cudaStream_t)stream);
 }
 
+ws_status ws_gradient3d(ws_context *c, const void *vol_d, ws_dtype dtype, const ws_shape *shape, int shift,
+                        uint16_t *grad_d, ws_stream_t stream)
+{
+    if (!c) return WS_ERR_INVALID;
+    c->err.clear();
+    Geo g;
+    ws_status st = make_geo(c, shape, &g);
+    if (st) return st;
+    if (shape->ndim != 3) return set_error(c, WS_ERR_UNSUPPORTED, "ws_gradient3d takes volumes (ndim 3)");
+    if (!vol_d || !grad_d) return set_error(c, WS_ERR_INVALID, "NULL buffer");
+    if (dtype != WS_U8 && dtype != WS_U16) return set_error(c, WS_ERR_INVALID, "dtype must be WS_U8 or WS_U16");
+    if (shift < 0 || shift > 31) return set_error(c, WS_ERR_INVALID, "shift must be 0..31");
+    if (g.D > 65535 * 8) return set_error(c, WS_ERR_UNSUPPORTED, "depth above 524280");
+    const size_t bps = dtype == WS_U8 ? 1 : 2;
+    const char *a = (const char *)vol_d, *b = (const char *)grad_d;
+    if (a < b + (size_t)g.N * 2 && b < a + (size_t)g.N * bps)
+        return set_error(c, WS_ERR_INVALID, "volume and gradient overlap");
+    cudaSetDevice(c->device);
+    return launch_gradient3d(c, vol_d, (int)bps, g.W, g.H, g.D, shift, grad_d, (cudaStream_t)stream);
+}
+
 ws_status ws_step1(ws_context *c, const void *grad_d, ws_dtype dtype, const ws_shape *shape, int conn,
                    uint8_t *states_d, int32_t *arrows_d, ws_stream_t stream)
 {

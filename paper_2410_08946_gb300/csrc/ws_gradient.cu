@@ -1,5 +1,6 @@
 // ws_gradient.cu -- pipeline steps 1-2 of Sec. 1 (minimal smoothing, then
-// gradient magnitude; optional per Fig. 2), and a label-count helper.
+// gradient magnitude; optional per Fig. 2) for images and volumes, and a
+// label-count helper.
 //
 // One CTA produces a 32 x 16 tile of the gradient:
 //   1. the 38 x 22 input window (3-pixel halo, replicated border) is staged
@@ -74,6 +75,103 @@ __global__ void __launch_bounds__(256) k_gradient(const uint8_t *__restrict__ im
     }
 }
 
+// ---------------------------------------------------------------------------
+// 3D: one CTA produces a 32 x 8 x 8 tile of the gradient of a volume
+// ---------------------------------------------------------------------------
+//   1. the 38 x 14 x 14 input window (3-voxel halo, replicated border) is
+//      staged in shared memory;
+//   2. the 5x5x5 binomial blur is taken as three exact integer passes (x, y,
+//      z; sums below 2^29, rounded once: (sum + 2048) >> 12) at the 34 x 10 x
+//      10 positions the Sobel stencil reads; a position outside the volume
+//      takes the blur of the nearest border voxel, like the 2D kernel;
+//   3. 3x3x3 Sobel, exact floor square root of gx^2 + gy^2 + gz^2 (float
+//      estimate corrected by 64-bit integer comparisons), >> shift, clip.
+constexpr int G3X = 32, G3Y = 8, G3Z = 8;
+constexpr int I3X = G3X + 6, I3Y = G3Y + 6, I3Z = G3Z + 6;   // input window
+constexpr int B3X = G3X + 2, B3Y = G3Y + 2, B3Z = G3Z + 2;   // blur window
+constexpr int S3A = I3Z * I3Y * I3X;   // input window, then the x-y sums  (>= I3Z * B3Y * B3X)
+constexpr int S3B = I3Z * I3Y * B3X;   // x sums, then the blur            (>= B3Z * B3Y * B3X)
+constexpr int G3_SMEM = (S3A + S3B) * 4;
+
+__device__ __forceinline__ unsigned isqrt64_exact(unsigned long long v)
+{
+    unsigned long long r = (unsigned long long)sqrtf((float)v);
+    while (r * r > v) r--;
+    while ((r + 1) * (r + 1) <= v) r++;
+    return (unsigned)r;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_gradient3d(const V *__restrict__ img, int W, int H, int D, int shift,
+                                                    uint16_t *__restrict__ out)
+{
+    extern __shared__ unsigned g3s[];
+    unsigned *A = g3s, *B = g3s + S3A;
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * G3X, y0 = blockIdx.y * G3Y, z0 = blockIdx.z * G3Z;
+    for (int i = tid; i < S3A; i += 256) {
+        const int ix = i % I3X, iy = (i / I3X) % I3Y, iz = i / (I3X * I3Y);
+        const int gx = clampi(x0 - 3 + ix, 0, W - 1), gy = clampi(y0 - 3 + iy, 0, H - 1);
+        const int gz = clampi(z0 - 3 + iz, 0, D - 1);
+        A[i] = img[((size_t)gz * H + gy) * W + gx];
+    }
+    __syncthreads();
+    // x: B[iz][iy][bx] = sum_t w_t A[iz][iy][clamp(X + t)], X = clamp(x0 - 1 + bx)
+    for (int i = tid; i < S3B; i += 256) {
+        const int bx = i % B3X, r = i / B3X;   // r = iz * I3Y + iy
+        const int X = clampi(x0 - 1 + bx, 0, W - 1);
+        const unsigned *row = A + r * I3X - (x0 - 3);
+        B[i] = row[clampi(X - 2, 0, W - 1)] + 4u * row[clampi(X - 1, 0, W - 1)] + 6u * row[X] +
+               4u * row[clampi(X + 1, 0, W - 1)] + row[clampi(X + 2, 0, W - 1)];
+    }
+    __syncthreads();
+    // y: A[iz][by][bx] = sum_t w_t B[iz][clamp(Y + t)][bx], Y = clamp(y0 - 1 + by)
+    for (int i = tid; i < I3Z * B3Y * B3X; i += 256) {
+        const int bx = i % B3X, by = (i / B3X) % B3Y, iz = i / (B3X * B3Y);
+        const int Y = clampi(y0 - 1 + by, 0, H - 1);
+        const unsigned *col = B + iz * I3Y * B3X - (y0 - 3) * B3X + bx;
+        A[i] = col[clampi(Y - 2, 0, H - 1) * B3X] + 4u * col[clampi(Y - 1, 0, H - 1) * B3X] + 6u * col[Y * B3X] +
+               4u * col[clampi(Y + 1, 0, H - 1) * B3X] + col[clampi(Y + 2, 0, H - 1) * B3X];
+    }
+    __syncthreads();
+    // z: B[bz][by][bx] = (sum_t w_t A[clamp(Z + t)][by][bx] + 2048) >> 12, Z = clamp(z0 - 1 + bz)
+    for (int i = tid; i < B3Z * B3Y * B3X; i += 256) {
+        const int bxy = i % (B3Y * B3X), bz = i / (B3Y * B3X);
+        const int Z = clampi(z0 - 1 + bz, 0, D - 1);
+        const unsigned *col = A - (z0 - 3) * (B3Y * B3X) + bxy;
+        constexpr int P = B3Y * B3X;
+        const unsigned sum = col[clampi(Z - 2, 0, D - 1) * P] + 4u * col[clampi(Z - 1, 0, D - 1) * P] +
+                             6u * col[Z * P] + 4u * col[clampi(Z + 1, 0, D - 1) * P] + col[clampi(Z + 2, 0, D - 1) * P];
+        B[i] = (sum + 2048u) >> 12;
+    }
+    __syncthreads();
+    // Sobel on the blurred window (positions beyond the border hold the border's blur)
+    const int lx = tid & 31, ly = tid >> 5;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x >= W || y >= H) return;
+    for (int lz = 0; lz < G3Z; lz++) {
+        const int z = z0 + lz;
+        if (z >= D) break;
+        int gxs = 0, gys = 0, gzs = 0;
+#pragma unroll
+        for (int a = -1; a <= 1; a++)
+#pragma unroll
+            for (int b = -1; b <= 1; b++) {
+                const int wt = (2 - (a < 0 ? -a : a)) * (2 - (b < 0 ? -b : b));
+#define BL(dz, dy, dx) ((int)B[((lz + 1 + (dz)) * B3Y + ly + 1 + (dy)) * B3X + lx + 1 + (dx)])
+                gxs += wt * (BL(a, b, 1) - BL(a, b, -1));
+                gys += wt * (BL(a, 1, b) - BL(a, -1, b));
+                gzs += wt * (BL(1, a, b) - BL(-1, a, b));
+#undef BL
+            }
+        const unsigned long long s2 = (unsigned long long)((long long)gxs * gxs) +
+                                      (unsigned long long)((long long)gys * gys) +
+                                      (unsigned long long)((long long)gzs * gzs);
+        unsigned m = isqrt64_exact(s2) >> shift;
+        out[((size_t)z * H + y) * W + x] = (uint16_t)(m > 65535u ? 65535u : m);
+    }
+}
+
 __global__ void k_max_label(const int32_t *__restrict__ L, int N, int32_t *kcount)
 {
     int m = 0;
@@ -93,6 +191,25 @@ ws_status launch_gradient(ws_context *c, const uint8_t *img, int W, int H, int s
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "gradient launch");
+}
+
+ws_status launch_gradient3d(ws_context *c, const void *vol, int bps, int W, int H, int D, int shift,
+                            uint16_t *grad, cudaStream_t s)
+{
+    dim3 grid((W + G3X - 1) / G3X, (H + G3Y - 1) / G3Y, (D + G3Z - 1) / G3Z);
+    cudaError_t e = bps == 1 ? cudaFuncSetAttribute(k_gradient3d<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    G3_SMEM)
+                             : cudaFuncSetAttribute(k_gradient3d<uint16_t>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, G3_SMEM);
+    if (e != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
+    PhaseScope ps(c, PH_GRADIENT, s);
+    if (bps == 1)
+        k_gradient3d<uint8_t><<<grid, 256, G3_SMEM, s>>>((const uint8_t *)vol, W, H, D, shift, grad);
+    else
+        k_gradient3d<uint16_t><<<grid, 256, G3_SMEM, s>>>((const uint16_t *)vol, W, H, D, shift, grad);
+    c->launches += 1;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "gradient3d launch");
 }
 
 ws_status launch_count_labels(ws_context *c, const int32_t *labels, int N, cudaStream_t s)

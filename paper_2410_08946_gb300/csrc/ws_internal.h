@@ -218,5 +218,7 @@ ws_status region_graph_read(ws_context *c, int64_t *row_ptr, int32_t *col, uint3
 // Gradient (ws_gradient.cu).
 ws_status launch_gradient(ws_context *c, const uint8_t *img, int W, int H, int shift, uint8_t *grad,
                           cudaStream_t s);
+ws_status launch_gradient3d(ws_context *c, const void *vol, int bps, int W, int H, int D, int shift,
+                            uint16_t *grad, cudaStream_t s);
 
 }  // namespace ws
