@@ -82,10 +82,12 @@ __global__ void __launch_bounds__(256) k_gradient(const uint8_t *__restrict__ im
 //      staged in shared memory;
 //   2. the 5x5x5 binomial blur is taken as three exact integer passes (x, y,
 //      z; sums below 2^29, rounded once: (sum + 2048) >> 12) at the 34 x 10 x
-//      10 positions the Sobel stencil reads; a position outside the volume
-//      takes the blur of the nearest border voxel, like the 2D kernel;
-//   3. 3x3x3 Sobel, exact floor square root of gx^2 + gy^2 + gz^2 (float
-//      estimate corrected by 64-bit integer comparisons), >> shift, clip.
+//      10 positions the Sobel stencil reads, each a 5-tap window sliding in
+//      registers; a position outside the volume takes the blur of the nearest
+//      border voxel, like the 2D kernel;
+//   3. 3x3x3 Sobel from per-plane 3x3 sums sliding along z, exact floor square
+//      root of gx^2 + gy^2 + gz^2 (float estimate corrected by 64-bit integer
+//      comparisons), >> shift, clip.
 constexpr int G3X = 32, G3Y = 8, G3Z = 8;
 constexpr int I3X = G3X + 6, I3Y = G3Y + 6, I3Z = G3Z + 6;   // input window
 constexpr int B3X = G3X + 2, B3Y = G3Y + 2, B3Z = G3Z + 2;   // blur window
@@ -99,6 +101,36 @@ __device__ __forceinline__ unsigned isqrt64_exact(unsigned long long v)
     while (r * r > v) r--;
     while ((r + 1) * (r + 1) <= v) r++;
     return (unsigned)r;
+}
+
+// One line of a blur pass: out[k * os] = the 5-tap binomial sum of `line` at
+// position P0 + k clamped to [0, L - 1] (so positions beyond the border repeat
+// the border's sum), for k < n; line[u * is] is the input at coordinate u
+// (only coordinates clamped into [0, L - 1] are read).  In the interior the
+// window slides: one new load per output.  ROUND: (sum + 2048) >> 12.
+template <bool ROUND>
+__device__ __forceinline__ void blur_line(const unsigned *line, int is, unsigned *out, int os, int P0, int n, int L)
+{
+    auto at = [&](int u) { return line[clampi(u, 0, L - 1) * is]; };
+    auto put = [&](int k, unsigned sum) { out[k * os] = ROUND ? (sum + 2048u) >> 12 : sum; };
+    int k = 0;
+    for (; k < n && P0 + k < 0; k++) put(k, at(-2) + 4u * at(-1) + 6u * at(0) + 4u * at(1) + at(2));   // = position 0
+    if (k < n && P0 + k < L) {
+        int X = P0 + k;
+        unsigned w0 = at(X - 2), w1 = at(X - 1), w2 = at(X), w3 = at(X + 1);
+        for (; k < n && X < L; k++, X++) {
+            const unsigned w4 = at(X + 2);
+            put(k, w0 + 4u * w1 + 6u * w2 + 4u * w3 + w4);
+            w0 = w1;
+            w1 = w2;
+            w2 = w3;
+            w3 = w4;
+        }
+    }
+    if (k < n) {   // beyond the far border: the sum at L - 1
+        const unsigned e = at(L - 3) + 4u * at(L - 2) + 6u * at(L - 1) + 4u * at(L) + at(L + 1);
+        for (; k < n; k++) put(k, e);
+    }
 }
 
 template <typename V>
@@ -116,59 +148,55 @@ __global__ void __launch_bounds__(256) k_gradient3d(const V *__restrict__ img, i
         A[i] = img[((size_t)gz * H + gy) * W + gx];
     }
     __syncthreads();
+    // Each pass slides a 5-tap window along its axis in registers: one thread
+    // per row / column / pillar reads every input once.
     // x: B[iz][iy][bx] = sum_t w_t A[iz][iy][clamp(X + t)], X = clamp(x0 - 1 + bx)
-    for (int i = tid; i < S3B; i += 256) {
-        const int bx = i % B3X, r = i / B3X;   // r = iz * I3Y + iy
-        const int X = clampi(x0 - 1 + bx, 0, W - 1);
-        const unsigned *row = A + r * I3X - (x0 - 3);
-        B[i] = row[clampi(X - 2, 0, W - 1)] + 4u * row[clampi(X - 1, 0, W - 1)] + 6u * row[X] +
-               4u * row[clampi(X + 1, 0, W - 1)] + row[clampi(X + 2, 0, W - 1)];
-    }
+    for (int r = tid; r < I3Z * I3Y; r += 256)
+        blur_line<false>(A + r * I3X - (x0 - 3), 1, B + r * B3X, 1, x0 - 1, B3X, W);
     __syncthreads();
     // y: A[iz][by][bx] = sum_t w_t B[iz][clamp(Y + t)][bx], Y = clamp(y0 - 1 + by)
-    for (int i = tid; i < I3Z * B3Y * B3X; i += 256) {
-        const int bx = i % B3X, by = (i / B3X) % B3Y, iz = i / (B3X * B3Y);
-        const int Y = clampi(y0 - 1 + by, 0, H - 1);
-        const unsigned *col = B + iz * I3Y * B3X - (y0 - 3) * B3X + bx;
-        A[i] = col[clampi(Y - 2, 0, H - 1) * B3X] + 4u * col[clampi(Y - 1, 0, H - 1) * B3X] + 6u * col[Y * B3X] +
-               4u * col[clampi(Y + 1, 0, H - 1) * B3X] + col[clampi(Y + 2, 0, H - 1) * B3X];
+    for (int c = tid; c < I3Z * B3X; c += 256) {
+        const int bx = c % B3X, iz = c / B3X;
+        blur_line<false>(B + iz * I3Y * B3X - (y0 - 3) * B3X + bx, B3X, A + iz * B3Y * B3X + bx, B3X, y0 - 1, B3Y,
+                         H);
     }
     __syncthreads();
     // z: B[bz][by][bx] = (sum_t w_t A[clamp(Z + t)][by][bx] + 2048) >> 12, Z = clamp(z0 - 1 + bz)
-    for (int i = tid; i < B3Z * B3Y * B3X; i += 256) {
-        const int bxy = i % (B3Y * B3X), bz = i / (B3Y * B3X);
-        const int Z = clampi(z0 - 1 + bz, 0, D - 1);
-        const unsigned *col = A - (z0 - 3) * (B3Y * B3X) + bxy;
-        constexpr int P = B3Y * B3X;
-        const unsigned sum = col[clampi(Z - 2, 0, D - 1) * P] + 4u * col[clampi(Z - 1, 0, D - 1) * P] +
-                             6u * col[Z * P] + 4u * col[clampi(Z + 1, 0, D - 1) * P] + col[clampi(Z + 2, 0, D - 1) * P];
-        B[i] = (sum + 2048u) >> 12;
-    }
+    for (int c = tid; c < B3Y * B3X; c += 256)
+        blur_line<true>(A - (z0 - 3) * (B3Y * B3X) + c, B3Y * B3X, B + c, B3Y * B3X, z0 - 1, B3Z, D);
     __syncthreads();
-    // Sobel on the blurred window (positions beyond the border hold the border's blur)
+    // Sobel (positions beyond the border hold the border's blur).  Per blurred
+    // plane the thread's 3x3 (y, x) neighbourhood gives dx = [1 2 1]_y of the
+    // x difference, dy = [1 2 1]_x of the y difference and sm = [1 2 1]^2 of
+    // the values; then gx = [1 2 1]_z of dx, gy = [1 2 1]_z of dy and
+    // gz = sm(z + 1) - sm(z - 1).
     const int lx = tid & 31, ly = tid >> 5;
     const int x = x0 + lx, y = y0 + ly;
     if (x >= W || y >= H) return;
-    for (int lz = 0; lz < G3Z; lz++) {
-        const int z = z0 + lz;
-        if (z >= D) break;
-        int gxs = 0, gys = 0, gzs = 0;
+    int dxm = 0, dym = 0, smm = 0, dx0 = 0, dy0 = 0, sm0 = 0;
+    for (int bz = 0; bz < B3Z; bz++) {
+        const unsigned *pl = B + (bz * B3Y + ly) * B3X + lx;   // (y - 1, x - 1) of this plane
+        int v[3][3];
 #pragma unroll
-        for (int a = -1; a <= 1; a++)
+        for (int j = 0; j < 3; j++)
 #pragma unroll
-            for (int b = -1; b <= 1; b++) {
-                const int wt = (2 - (a < 0 ? -a : a)) * (2 - (b < 0 ? -b : b));
-#define BL(dz, dy, dx) ((int)B[((lz + 1 + (dz)) * B3Y + ly + 1 + (dy)) * B3X + lx + 1 + (dx)])
-                gxs += wt * (BL(a, b, 1) - BL(a, b, -1));
-                gys += wt * (BL(a, 1, b) - BL(a, -1, b));
-                gzs += wt * (BL(1, a, b) - BL(-1, a, b));
-#undef BL
-            }
-        const unsigned long long s2 = (unsigned long long)((long long)gxs * gxs) +
-                                      (unsigned long long)((long long)gys * gys) +
-                                      (unsigned long long)((long long)gzs * gzs);
-        unsigned m = isqrt64_exact(s2) >> shift;
-        out[((size_t)z * H + y) * W + x] = (uint16_t)(m > 65535u ? 65535u : m);
+            for (int i = 0; i < 3; i++) v[j][i] = (int)pl[j * B3X + i];
+        const int dx = (v[0][2] - v[0][0]) + 2 * (v[1][2] - v[1][0]) + (v[2][2] - v[2][0]);
+        const int dy = (v[2][0] - v[0][0]) + 2 * (v[2][1] - v[0][1]) + (v[2][2] - v[0][2]);
+        const int sm = (v[0][0] + 2 * v[0][1] + v[0][2]) + 2 * (v[1][0] + 2 * v[1][1] + v[1][2]) +
+                       (v[2][0] + 2 * v[2][1] + v[2][2]);
+        if (bz >= 2) {   // output plane z = z0 + bz - 2 (its blurred planes are bz - 2 .. bz)
+            const int z = z0 + bz - 2;
+            if (z >= D) break;
+            const int gxs = dxm + 2 * dx0 + dx, gys = dym + 2 * dy0 + dy, gzs = sm - smm;
+            const unsigned long long s2 = (unsigned long long)((long long)gxs * gxs) +
+                                          (unsigned long long)((long long)gys * gys) +
+                                          (unsigned long long)((long long)gzs * gzs);
+            const unsigned m = isqrt64_exact(s2) >> shift;
+            out[((size_t)z * H + y) * W + x] = (uint16_t)(m > 65535u ? 65535u : m);
+        }
+        dxm = dx0; dym = dy0; smm = sm0;
+        dx0 = dx; dy0 = dy; sm0 = sm;
     }
 }
 
