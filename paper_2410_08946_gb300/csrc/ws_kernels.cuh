@@ -278,33 +278,56 @@ static __device__ __forceinline__ unsigned long long mix64(unsigned long long k)
     return k;
 }
 
-static __device__ __forceinline__ void edge_insert(unsigned long long key, unsigned h, unsigned long long *keys,
-                                            uint32_t *vals, int32_t *slots, int32_t *ecount,
-                                            unsigned long long mask, DevStatus *status)
+// Inserts (key, h) into the region table (open addressing, min of h per key).
+// Returns the slot when this call created the key -- the caller then lists
+// it in `slots` -- and -1 otherwise (or when the table is full: error 6).
+static __device__ __forceinline__ int edge_insert_slot(unsigned long long key, unsigned h, unsigned long long *keys,
+                                                      uint32_t *vals, unsigned long long mask, DevStatus *status)
 {
     unsigned long long s = mix64(key) & mask;
     for (int probe = 0; probe < 4096; probe++) {
         unsigned long long k = *(volatile unsigned long long *)(keys + s);
         if (k == key) {
             atomicMin(vals + s, h);
-            return;
+            return -1;
         }
         if (k == EMPTY_KEY) {
             unsigned long long old = atomicCAS(keys + s, EMPTY_KEY, key);
             if (old == EMPTY_KEY) {
-                int idx = atomicAdd(ecount, 1);
-                slots[idx] = (int32_t)s;
                 atomicMin(vals + s, h);
-                return;
+                return (int)s;
             }
             if (old == key) {
                 atomicMin(vals + s, h);
-                return;
+                return -1;
             }
         }
         s = (s + 1) & mask;
     }
     record_error(status, DEV_EDGE_TABLE_FULL, 6);
+    return -1;
+}
+
+// One lane's insert, listing a new key at once.
+static __device__ __forceinline__ void edge_insert(unsigned long long key, unsigned h, unsigned long long *keys,
+                                                   uint32_t *vals, int32_t *slots, int32_t *ecount,
+                                                   unsigned long long mask, DevStatus *status)
+{
+    const int s = edge_insert_slot(key, h, keys, vals, mask, status);
+    if (s >= 0) slots[atomicAdd(ecount, 1)] = s;
+}
+
+// Called by all 32 lanes of a warp: lists the lanes' new slots (s >= 0) with
+// one atomic on the slot counter for the whole warp.
+static __device__ __forceinline__ void append_slots(int s, int32_t *slots, int32_t *ecount)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, s >= 0);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(ecount, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (s >= 0) slots[base + __popc(m & ((1u << lane) - 1u))] = s;
 }
 
 template <typename T, int CONN>
@@ -341,11 +364,15 @@ static __global__ void __launch_bounds__(NTHR) k_rag(const T *__restrict__ g, Ge
                     h = gp > gq ? gp : gq;
                 }
             }
-            unsigned m = __ballot_sync(0xffffffffu, has);
-            if (!has) continue;
-            unsigned grp = __match_any_sync(m, key);
-            unsigned hmin = __reduce_min_sync(grp, h);
-            if (lane == __ffs(grp) - 1) edge_insert(key, hmin, keys, vals, slots, ecount, mask, status);
+            const unsigned m = __ballot_sync(0xffffffffu, has);
+            if (!m) continue;   // warp-uniform
+            int sl = -1;
+            if (has) {
+                const unsigned grp = __match_any_sync(m, key);
+                const unsigned hmin = __reduce_min_sync(grp, h);
+                if (lane == __ffs(grp) - 1) sl = edge_insert_slot(key, hmin, keys, vals, mask, status);
+            }
+            append_slots(sl, slots, ecount);
         }
     }
 }
@@ -576,10 +603,15 @@ static __global__ void __launch_bounds__(NTHR) k_levels(Edge *e0, Edge *e1, int3
         }
         if (blockIdx.x == 0 && tid == 0 && counts) counts[k + 1] = all;
         if (!grid_barrier(status, timeout_ns)) return;
-        // F: compose the level-0 -> level-(k+1) map; contract the edge list
+        // F: every level-k region's level-(k+1) id, once (newmin is dead after
+        // C and holds it); then compose the level-0 -> level-(k+1) map and
+        // contract the edge list with one lookup per id
+        int32_t *lab = reinterpret_cast<int32_t *>(newmin);
+        for (int a = blockIdx.x * NTHR + tid; a < Kk; a += gsz) lab[a] = __ldcg(rank + uf_find(uf, a));
+        if (!grid_barrier(status, timeout_ns)) return;
         for (int c = blockIdx.x * NTHR + tid; c < K0; c += gsz) {
             const int A = gm ? __ldcg(gm + c) : c;
-            gout[c] = __ldcg(rank + uf_find(uf, A));
+            gout[c] = __ldcg(lab + A);
         }
         if (k + 2 < NL) {
             for (int e0i = blockIdx.x * NTHR; e0i < E; e0i += gsz) {
@@ -589,7 +621,7 @@ static __global__ void __launch_bounds__(NTHR) k_levels(Edge *e0, Edge *e1, int3
                 if (e < E) {
                     const Edge ed = ld_edge(cur + e);
                     if (ed.a != ed.b) {
-                        const int A = __ldcg(rank + uf_find(uf, ed.a)), B = __ldcg(rank + uf_find(uf, ed.b));
+                        const int A = __ldcg(lab + ed.a), B = __ldcg(lab + ed.b);
                         if (A != B) {
                             keep = true;
                             ne.a = A < B ? A : B;

@@ -1298,8 +1298,12 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
     }
     if (!do_rag) return;
     __syncthreads();
-    for (int i = tid; i < C::HASH; i += C::NT)
-        if (hk[i] != EMPTY_KEY) edge_insert(hk[i], hv[i], keys, vals, slots, ecount, gmask, status);
+    static_assert(C::HASH % C::NT == 0, "warp-uniform flush");
+    for (int i0 = 0; i0 < C::HASH; i0 += C::NT) {
+        const int i = i0 + tid;
+        const int sl = hk[i] != EMPTY_KEY ? edge_insert_slot(hk[i], hv[i], keys, vals, gmask, status) : -1;
+        append_slots(sl, slots, ecount);
+    }
 }
 
 // ---------------------------------------------------------------------------
