@@ -523,6 +523,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-image batch measurement")
+    ap.add_argument("--no-small", action="store_true", help="skip the smaller configurations and the NEXT-row "
+                    "measurements (2D configs, 512^3 volume, gradient, region graph, literal waterfall)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--ingest-ncu", metavar="CSV", help="write profiles/traffic.json from an ncu DRAM capture "
@@ -651,11 +653,13 @@ def main():
         # the copies alone at the measured link speed: the end-to-end ceiling
         copy_s = N * 2 / (link["h2d"] * 1e9) + NL * N * 4 / (link["d2h"] * 1e9)
         line["e2e"]["copy_bound_gvox_s"] = N / copy_s / 1e9
-    if world == 1 and not args.no_batch:
+    if world == 1 and not (args.no_small and args.no_batch):
         del levels_d
         torch.cuda.empty_cache()
-        line["small_configs"] = run_small_configs(ctx, torch)
-        line["batch"] = run_batch(ctx, binding, torch)
+        if not args.no_small:
+            line["small_configs"] = run_small_configs(ctx, torch)
+        if not args.no_batch:
+            line["batch"] = run_batch(ctx, binding, torch)
     if world == 1 and not args.no_serve:
         line["serve"] = run_serve(ctx, binding, torch, seconds=args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
