@@ -194,7 +194,8 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
     if ((e = reset_barrier(c, s)) != cudaSuccess) return set_cuda_error(c, e, "memset");
     {
         PhaseScope ps(c, PH_JUMP, s);
-        const int grid = coop_grid(c, k_jump2<CONN>, NTHR, 0, c->num_sms * 8);
+        // one CTA per tile at most (only plateau tiles have work)
+        const int grid = coop_grid(c, k_jump2<CONN>, NTHR, 0, b.ntiles < c->num_sms * 8 ? b.ntiles : c->num_sms * 8);
         e = launch_coop(k_jump2<CONN>, grid, NTHR, 0, s, b, w.par, (const int32_t *)w.dist, (const int32_t *)w.tlist,
                         w.counters, w.roots, tune_rr(c), c->status, tune_jump_cap(c), tune_timeout_ns(c));
         c->launches += 1;
