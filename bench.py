@@ -12,7 +12,8 @@ no cache flush is needed between steps.
 Prints ONE JSON line (rank 0).  Keys:
   value / unit        Gvoxels processed per second, device-resident input
   e2e                 the same through ws_segment_host (pinned host buffers,
-                      host<->device copies inside the timed region)
+                      host<->device copies inside the timed region; median
+                      of the per-step times, each step listed)
   roofline            the dominant kernel phase: algorithmic bytes per launch
                       / its CUDA-event time, against the measured HBM peak
   path_roofline       the whole step: (2 + 4 NL) bytes per voxel / step time
@@ -20,6 +21,10 @@ Prints ONE JSON line (rank 0).  Keys:
   phases_ms           per-phase device time per step (CUDA events)
   gpu_launches        kernels libws enqueued per timed step
   clocks              nvidia-smi samples taken during the timed region
+  small_configs       the other configurations (2D 256^2 and 4096^2, a 512^3
+                      volume in 6- and 26-connectivity) and the NEXT-row
+                      measurements (3D gradient, region-graph export, the
+                      paper-literal waterfall); batch, serve: configs 3 and 4
 --impl reference times the CPU oracle itself (the reference arm).
 Multi-GPU (torchrun): replicas, one volume per rank, no collective on the
 data path ("weak" scaling); value = voxels of all ranks / max rank time.
@@ -637,15 +642,18 @@ def main():
         ctx.segment_host(grad_h, CONN, NL, levels_h, counts_h)       # warm the staging buffers
         if dist:
             dist.barrier()
-        t0 = time.perf_counter()
+        e2e_steps = []
         for _ in range(args.e2e_steps):
-            ctx.segment_host(grad_h, CONN, NL, levels_h, counts_h)
-        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+            t0 = time.perf_counter()
+            ctx.segment_host(grad_h, CONN, NL, levels_h, counts_h)   # synchronises: copies in and out included
+            e2e_steps.append(time.perf_counter() - t0)
+        e2e_s = statistics.median(e2e_steps)
         if dist:
             t = torch.tensor([e2e_s], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
         line["e2e"] = {"value": N * world / e2e_s / 1e9, "unit": "Gvox/s", "ms_per_step": e2e_s * 1e3,
+                       "step_ms": [round(t * 1e3, 2) for t in e2e_steps],
                        "h2d_bytes_per_step": int(N * 2), "d2h_bytes_per_step": int(NL * N * 4 + NL * 4)}
         del grad_h, levels_h
         link = host_link_gbs(torch)
