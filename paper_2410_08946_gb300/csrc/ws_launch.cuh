@@ -263,10 +263,13 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
         k_rank_mark<<<rg, NTHR, 0, s>>>(b.npix, w.roots, w.counters, w.aux, w.rootm, w.bitmap, c->status);
         k_rank_groups<<<(ng + NTHR / 32 - 1) / (NTHR / 32), NTHR, 0, s>>>(w.bitmap, nw, w.gcnt, ng);
         k_scan_chunks<<<nch, NTHR, 0, s>>>(w.gcnt, ng, w.csum);
-        k_scan<<<1, 1024, 0, s>>>(w.csum, nch, nullptr);
-        k_scan_add<<<nch, NTHR, 0, s>>>(w.gcnt, ng, w.csum);
+        if (nch > 1) {   // one chunk is already scanned
+            k_scan<<<1, 1024, 0, s>>>(w.csum, nch, nullptr);
+            k_scan_add<<<nch, NTHR, 0, s>>>(w.gcnt, ng, w.csum);
+            c->launches += 2;
+        }
         k_rank_assign<<<rg, NTHR, 0, s>>>(w.roots, w.counters, w.rootm, w.bitmap, w.gcnt, w.aux);
-        c->launches += 6;
+        c->launches += 4;
         if (b.d) {
             k_rank_bases<<<(b.n + NTHR) / NTHR, NTHR, 0, s>>>(b, w.bitmap, w.gcnt, w.counters, w.rbase);
             c->launches += 1;

@@ -381,11 +381,14 @@ ws_status region_graph_build(ws_context *c, const int32_t *L, const void *grad, 
             for (int shift = 0; shift < 2 * sh; shift += 8) {
                 k_radix_hist<<<ntl, NTHR, 0, s>>>(r.key[cur], (int)n, shift, ntl, r.hist);
                 k_scan_chunks<<<nch, NTHR, 0, s>>>(r.hist, m, r.hsum);
-                k_scan<<<1, 1024, 0, s>>>(r.hsum, nch, nullptr);
-                k_scan_add<<<nch, NTHR, 0, s>>>(r.hist, m, r.hsum);
+                if (nch > 1) {   // one chunk is already scanned
+                    k_scan<<<1, 1024, 0, s>>>(r.hsum, nch, nullptr);
+                    k_scan_add<<<nch, NTHR, 0, s>>>(r.hist, m, r.hsum);
+                    c->launches += 2;
+                }
                 k_radix_scatter<<<ntl, NTHR, 0, s>>>(r.key[cur], r.val[cur], (int)n, shift, ntl, r.hist,
                                                      r.key[cur ^ 1], r.val[cur ^ 1]);
-                c->launches += 5;
+                c->launches += 3;
                 cur ^= 1;
             }
         }

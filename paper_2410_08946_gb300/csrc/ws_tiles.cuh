@@ -301,8 +301,10 @@ __device__ __forceinline__ int init_step1(const T *gs, int *nx, int (&st)[TC<CON
     return plateau;
 }
 
+// 26-connectivity: at most 64 registers, so that two CTAs share an SM
 template <typename T, int CONN, bool TMA>
-__global__ void __launch_bounds__(TT<CONN>::NT) k_init(const __grid_constant__ CUtensorMap tm, const Batch b,
+__global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
+    k_init(const __grid_constant__ CUtensorMap tm, const Batch b,
                                                        int32_t *__restrict__ par, int32_t *__restrict__ mi,
                                                        int32_t *__restrict__ dist, uint8_t *__restrict__ plat,
                                                        uint8_t *__restrict__ act, int32_t *__restrict__ tlist,
@@ -1284,6 +1286,10 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
         if (in && (lane == 0 || rprev != r)) atomicMin(mi + r, p);
         if (!do_rag || !in) continue;
         const unsigned gp = gb[bg];
+        // neighbours in the same other basin follow each other: merge each run
+        // of equal roots in registers (lowest height) and insert once per run
+        int rl = -1;
+        unsigned hl = 0;
 #pragma unroll
         for (int n = Half<CONN>::first; n < Nb<CONN>::n; n++) {
             const int dn = Nb<CONN>::dz(n) * C::BY + Nb<CONN>::dy(n);
@@ -1292,9 +1298,20 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
             const int rq = pb[bp + dn * B::RWP + Nb<CONN>::dx(n)];
             if (rq == r) continue;
             const unsigned gq = gb[bg + dn * B::RWG + Nb<CONN>::dx(n)];
-            const unsigned lo = (unsigned)(r < rq ? r : rq), hi = (unsigned)(r < rq ? rq : r);
-            smem_edge_insert(lo, hi, gp > gq ? gp : gq, hk, hv, C::HASH, keys, vals, slots, ecount, gmask, status);
+            const unsigned h = gp > gq ? gp : gq;
+            if (rq == rl) {
+                hl = h < hl ? h : hl;
+                continue;
+            }
+            if (rl >= 0)
+                smem_edge_insert((unsigned)(r < rl ? r : rl), (unsigned)(r < rl ? rl : r), hl, hk, hv, C::HASH, keys,
+                                 vals, slots, ecount, gmask, status);
+            rl = rq;
+            hl = h;
         }
+        if (rl >= 0)
+            smem_edge_insert((unsigned)(r < rl ? r : rl), (unsigned)(r < rl ? rl : r), hl, hk, hv, C::HASH, keys, vals,
+                             slots, ecount, gmask, status);
     }
     if (!do_rag) return;
     __syncthreads();
