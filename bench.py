@@ -17,6 +17,8 @@ Prints ONE JSON line (rank 0).  Keys:
   roofline            the dominant kernel phase: algorithmic bytes per launch
                       / its CUDA-event time, against the measured HBM peak
   path_roofline       the whole step: (2 + 4 NL) bytes per voxel / step time
+  path_dram           the whole step's measured DRAM bytes (ncu record of its
+                      main kernels, while their source matches) / step time
   cpu_baseline        the CPU oracle (1 thread) on a bounded sample volume
   phases_ms           per-phase device time per step (CUDA events)
   gpu_launches        kernels libws enqueued per timed step
@@ -152,6 +154,20 @@ def traffic_for(kernel, voxels):
     if not ent or ent.get("source_sha") != _source_sha(kernel):
         return None
     return ent["bytes_per_voxel"] * voxels
+
+
+def path_dram(voxels, ms, peak):
+    """Measured DRAM bytes of a whole step (read + write of the kernels that
+    move nearly all of them, from the committed ncu record) over the step time;
+    None unless every record matches the current source."""
+    kerns = ("k_init6", "k_chase", "k_rag6", "k_write6")
+    tr = {k: traffic_for(k, voxels) for k in kerns}
+    if any(v is None for v in tr.values()):
+        return None
+    tot = sum(tr.values())
+    ach = tot / (ms / 1e3) / 1e9
+    return {"bytes_per_voxel": tot / voxels, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "kernels": list(kerns)}
 
 
 def ingest_ncu(csv_path, voxels):
@@ -632,6 +648,7 @@ def main():
             "roofline": roofline,
             "path_roofline": {"bytes_per_voxel": 2 + 4 * NL, "achieved": path_achieved, "peak": peak,
                               "unit": "GB/s", "frac": path_achieved / peak},
+            "path_dram": path_dram(N, ms, peak),
             "phases_ms": {k: round(v, 4) for k, v in per_step.items()},
             "gpu_launches": launches, "clocks": clocks}
 
