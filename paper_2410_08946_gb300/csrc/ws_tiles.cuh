@@ -382,9 +382,12 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
 
         // step III inside the tile: pointer doubling through shared memory
         // (in place: every value read is the pointer of a pixel further down
-        // the same path, or the path's end), until no pointer stays in the tile
+        // the same path, or the path's end), until no pointer stays in the tile.
+        // No round waits for the others: each thread doubles until its own
+        // pointers have left the tile (an unfinished pointer moves at least one
+        // step per round down a path of fewer than NPIX steps).
         volatile int *vnx = nx;
-        for (int round = 0; round < 32; round++) {
+        for (int round = 0; round < C::NPIX; round++) {
             int more = 0;
 #pragma unroll
             for (int k = 0; k < C::PER; k++) {
@@ -396,8 +399,9 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
                     more |= c2 >= 0;
                 }
             }
-            if (!__syncthreads_or(more)) break;
+            if (!more) break;
         }
+        __syncthreads();
 
 #pragma unroll
         for (int k = 0; k < C::PER; k++) {
@@ -406,7 +410,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
             const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
             const int p = base + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
             const int e = vnx[i];
-            par[p] = e < 0 ? dec_final(e) : p;  // e >= 0 cannot survive 32 doubling rounds
+            par[p] = e < 0 ? dec_final(e) : p;  // e >= 0 does not survive the doubling
             if (st[k] != ST0) mi[p] = 0x7fffffff;
         }
         // list the strict minima (roots known now)
@@ -674,12 +678,15 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
 
         // step III inside the tile: pointer doubling.  A value read while its
         // owner is updating it is the old or the new pointer of a pixel further
-        // down the same path, or the path's end.
+        // down the same path, or the path's end; so no round needs the others
+        // to be done: each thread doubles until its own pixels point at their
+        // ends (every round moves an unfinished pointer at least one step down
+        // a path of fewer than NPIX steps, so NPIX rounds always suffice).
         int cur[C::TZ];
 #pragma unroll
         for (int k = 0; k < C::TZ; k++) cur[k] = nx[tid + k * C::NT];
         volatile int *vnx = nx;
-        for (int round = 0; round < 32; round++) {
+        for (int round = 0; round < C::NPIX; round++) {
             int more = 0;
 #pragma unroll
             for (int h = 0; h < C::TZ; h += 8) {  // eight entries in flight
@@ -693,19 +700,19 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
                     cur[h + k] = nxt[k];
                 }
             }
-            if (!__syncthreads_or(more)) break;   // (also publishes slotof)
+            if (!more) break;
         }
         if (tid == 0) {
             s_first = first;
             tends[t] = make_int2(first, nend);
         }
-        __syncthreads();
+        __syncthreads();   // every pointer at its end; slotof published
         {
             const int fst = s_first;
 #pragma unroll
             for (int k = 0; k < C::TZ; k++) {
                 if (((stb >> (2 * k)) & 3u) == (unsigned)STOUT) continue;
-                code[p0 + k * HW] = slotof[cur[k]];   // cur[k]: the end (32 rounds always suffice)
+                code[p0 + k * HW] = slotof[cur[k]];   // cur[k]: the end
             }
             for (unsigned m = endb; m; m &= m - 1) {
                 const int k = __ffs(m) - 1;
