@@ -234,10 +234,32 @@ def cpu_baseline(side=320):
                       f"{os.cpu_count()} host cores ({os.uname().machine})"}
 
 
+def rank_env():
+    """(world size, rank, local rank) of a torchrun launch; (1, 0, 0) otherwise."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (x itself without a process group).  The
+    timed region of every rank ends at the same barrier, so the slowest rank's
+    time is the whole job's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units of all ranks (replicas: each rank does the same work) per second, in billions."""
+    return units_per_rank * world / seconds / 1e9
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle on the host cores, bounded sample per step."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if rank_env()[1] != 0:   # under torchrun, rank 0 alone times the oracle
         return 0
     import oracle
     from paper_2410_08946_gb300 import synth
@@ -561,9 +583,7 @@ def main():
 
     import torch
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -617,12 +637,9 @@ def main():
     phases = ctx.phase_times()
     ctx.set_profiling(False)
     clocks = sampler.stop()
-    if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dist, "cuda")
     ms = ms_total / args.steps
-    value = N * world / (ms / 1e3) / 1e9
+    value = whole_job_rate(N, world, ms / 1e3)
     counts = counts_d.cpu().tolist()
 
     peak, peak_src = hbm_peak()
@@ -664,12 +681,8 @@ def main():
             t0 = time.perf_counter()
             ctx.segment_host(grad_h, CONN, NL, levels_h, counts_h)   # synchronises: copies in and out included
             e2e_steps.append(time.perf_counter() - t0)
-        e2e_s = statistics.median(e2e_steps)
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        line["e2e"] = {"value": N * world / e2e_s / 1e9, "unit": "Gvox/s", "ms_per_step": e2e_s * 1e3,
+        e2e_s = max_over_ranks(statistics.median(e2e_steps), dist, "cuda")
+        line["e2e"] = {"value": whole_job_rate(N, world, e2e_s), "unit": "Gvox/s", "ms_per_step": e2e_s * 1e3,
                        "step_ms": [round(t * 1e3, 2) for t in e2e_steps],
                        "h2d_bytes_per_step": int(N * 2), "d2h_bytes_per_step": int(NL * N * 4 + NL * 4)}
         del grad_h, levels_h
