@@ -1,38 +1,32 @@
-// ws_kernels.cuh -- the watershed (steps I-IV) and waterfall kernels of
-// libws, templated on the gradient sample type T (uint8_t / uint16_t) and the
-// connectivity CONN (4, 8 in 2D; 6 in 3D).  Included by one translation
-// unit per sample type, which instantiates the launchers.
+// ws_kernels.cuh -- the kernels and device helpers of libws that are not
+// tiled: step I alone, the union-find, the scans, the region table and the
+// graph-form waterfall, and Alg. 5's image reconstruction; templated on the
+// gradient sample type T (uint8_t / uint16_t) and the connectivity CONN (4, 8
+// in 2D; 6, 26 in 3D) where they touch pixels.  The tiled watershed pipeline
+// (steps I-IV, canonical ids, adjacency, level planes) is in ws_tiles.cuh.
 //
-// Pipeline of ws_watershed (all on one stream, no host synchronisation):
-//   k_step1          Eq. 1 arrows and states (Alg. 1 step I); initial step II
-//                    distances (0 on state-0 pixels); flags tiles holding
-//                    plateau pixels
-//   k_plateau        step II: exact geodesic distance of every non-minimal
-//                    plateau pixel to its plateau's lower border, by
-//                    in-tile relaxation in shared memory with frozen halos
-//                    and device-wide rounds over active tiles (the
-//                    block-asynchronous balanced scheme of Sec. 3.4, Alg. 3,
-//                    run to its fixpoint); cooperative launch
-//   k_resolve_union  step II pointer choice on non-minimal plateaux, and
-//                    step IV Union of adjacent minimal-plateau pixels
-//                    (atomicCAS links towards the smaller root)
-//   k_jump           step III pointer jumping, RR hops per pixel per round,
-//                    rounds until nothing changes (Sec. 3.1, Fig. 4), then the
-//                    smallest pixel index of every basin; cooperative launch
-//   k_flags / k_scan / k_assign / k_label
-//                    canonical compaction: ids 0..K-1 by smallest pixel index
-// ws_waterfall:
-//   k_rag            Alg. 5 step V on pixel pairs: pass(A,B) = min over
-//                    adjacent pixels of max(G(p), G(q)), warp-deduplicated
-//                    into a hash table of region pairs
+//   k_step1          Eq. 1 arrows and states (Alg. 1 step I) of every pixel,
+//                    for the ws_step1 entry point
+//   uf_find/uf_union global union-find (path halving; atomicCAS links the
+//                    larger root under the smaller)
+//   k_scan_chunks / k_scan / k_scan_add
+//                    device-wide exclusive scan in chunks of 2048
+//   edge_insert_slot / edge_insert / append_slots
+//                    the region table: open addressing on (a << 32 | b) with
+//                    the min pass per pair, new slots listed (one counter
+//                    atomic per warp where the caller is warp-uniform)
+//   k_rag            Alg. 5 step V on pixel pairs of a caller's labelling:
+//                    pass(A,B) = min over adjacent pixels of max(G(p), G(q)),
+//                    warp-deduplicated into the region table
+//   k_edges_compact  region table -> dense edge list in canonical level-0 ids
+//                    (and the table emptied)
 //   k_levels         NL-1 rounds of lowest-pass merging on the region graph
-//                    (newmin, Union over kept edges, canonical ids);
-//                    cooperative launch
+//                    (newmin, Union over kept edges, canonical ids, the next
+//                    level's id per region, contracted edges); cooperative
 //   k_level_write    levels[k][p] = map_k[L0[p]] for all k in one pass
-//   k_edges_compact  region table -> dense edge list (and the table emptied)
-// ws_waterfall_reconstruct (the paper-literal hierarchy of Alg. 4):
 //   k_fill_newmin, k_newmin, k_raise
-//                    Alg. 5 steps V and VI between two watersheds
+//                    ws_waterfall_reconstruct: Alg. 5 steps V and VI between
+//                    two watersheds of the paper-literal hierarchy (Alg. 4)
 #pragma once
 
 #include <cooperative_groups.h>
