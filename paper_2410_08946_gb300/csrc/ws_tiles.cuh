@@ -19,10 +19,12 @@
 //               the minimal-plateau roots
 //   k_label     per tile: final root of every pixel (chasing the few
 //               tile-to-tile hops left), smallest pixel index per basin, and
-//               Alg. 5 step V on pixel pairs (pass values, deduplicated in a
-//               shared-memory hash before the global region table)
+//               Alg. 5 step V on pixel pairs (runs of equal neighbour roots
+//               merged in registers, then a shared-memory hash, then the
+//               global region table)
+// These serve 2D (4-, 8-connectivity) and 3D 26-connectivity.
 //
-// 3D volumes (6-connectivity) take a variant of this pipeline with one z
+// 3D volumes with 6-connectivity take a variant of this pipeline with one z
 // column of the tile per thread:
 //   k_init6     as k_init, and numbers the tile's in-tile path ends (slots):
 //               per pixel the 16-bit slot of its end, per tile the list of
@@ -33,8 +35,12 @@
 //               and Alg. 5 step V from per-warp lists of boundary pixels
 //   k_rank_*    canonical ids: rank of every basin's smallest pixel index
 //               among all of them, by a bitmap over pixel indices
-//   k_write     per pixel: canonical id of its root and its id on every
-//               waterfall level, one pass writing all NL planes
+//   k_write6    per tile (3D, 6-connectivity): the canonical and waterfall
+//               ids of the tile's slots in a shared table, then every voxel's
+//               row of it by its slot code, all NL planes in one pass
+//   k_write_vec / k_write_batch
+//               per pixel (the other paths): canonical id of its root and its
+//               id on every waterfall level, one pass writing all NL planes
 #pragma once
 
 #include <type_traits>
