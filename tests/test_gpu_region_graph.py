@@ -147,3 +147,25 @@ def test_invalid_labels(ctx):
         assert st == binding.WS_ERR_INVALID
     finally:
         fresh.close()
+
+
+@pytest.mark.parametrize("shape,conn,dt", [((37, 128), 4, np.uint8), ((41, 64), 4, np.uint16),
+                                           ((9, 13, 64), 6, np.uint8), ((7, 11, 36), 6, np.uint16)])
+def test_aligned_widths_and_offset_view(ctx, shape, conn, dt):
+    """Widths that are multiples of 4 (u8 and u16 heights, 2D and 3D), and the
+    same labelling starting 4 bytes past an aligned address (a contiguous view
+    the library must not assume to be 16-byte aligned).  Both against the
+    oracle."""
+    rng = np.random.default_rng(sum(shape))
+    g = rng.integers(0, 200 if dt == np.uint8 else 50000, size=shape).astype(dt)
+    L, _ = oracle.watershed(g, conn)
+    compare(ctx, L, g, conn, g)
+    buf = torch.empty(L.size + 1, dtype=torch.int32, device="cuda")
+    buf[1:] = torch.from_numpy(L.ravel()).cuda()
+    Lm = buf[1:].view(shape)                      # contiguous, 4 bytes off a 16-byte boundary
+    got = ctx.region_graph(Lm, torch.from_numpy(g).cuda(), conn)
+    ctx.check()
+    ref = oracle.region_graph(L, g, conn)
+    assert np.array_equal(got["col"].cpu().numpy(), ref["col"])
+    assert np.array_equal(got["pass"].cpu().numpy().astype(np.uint32), ref["pass"])
+    assert got["row_ptr"].cpu().numpy().tolist() == ref["row_ptr"].tolist()
