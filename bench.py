@@ -140,11 +140,19 @@ def _source_sha(kernel):
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
-def traffic_for(kernel, voxels):
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def kernel_short_name(full):
+    """'void ws::<unnamed>::k_x<T, 1>(args)' -> 'k_x'."""
+    n = full.replace("(anonymous namespace)::", "").replace("<unnamed>::", "").replace("void ", "")
+    return n.split("<")[0].split("(")[0].strip().split("::")[-1]
+
+
+def traffic_for(kernel, voxels, path=TRAFFIC_PATH):
     """DRAM bytes (read + write) per launch of `kernel` on `voxels` voxels,
     from the committed ncu record (bytes per voxel of a captured launch), if
     the kernel's source has not changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
@@ -156,12 +164,12 @@ def traffic_for(kernel, voxels):
     return ent["bytes_per_voxel"] * voxels
 
 
-def path_dram(voxels, ms, peak):
+def path_dram(voxels, ms, peak, path=TRAFFIC_PATH):
     """Measured DRAM bytes of a whole step (read + write of the kernels that
     move nearly all of them, from the committed ncu record) over the step time;
     None unless every record matches the current source."""
     kerns = ("k_init6", "k_chase", "k_rag6", "k_write6")
-    tr = {k: traffic_for(k, voxels) for k in kerns}
+    tr = {k: traffic_for(k, voxels, path) for k in kerns}
     if any(v is None for v in tr.values()):
         return None
     tot = sum(tr.values())
@@ -170,7 +178,7 @@ def path_dram(voxels, ms, peak):
             "kernels": list(kerns)}
 
 
-def ingest_ncu(csv_path, voxels):
+def ingest_ncu(csv_path, voxels, out_path=TRAFFIC_PATH):
     """Writes profiles/traffic.json from an ncu --csv capture with the
     dram__bytes_read.sum / dram__bytes_write.sum metrics (one or more
     launches per kernel on a volume of `voxels` voxels)."""
@@ -181,7 +189,7 @@ def ingest_ncu(csv_path, voxels):
     hdr = rows[0]
     for r in rows[1:]:
         d = dict(zip(hdr, r))
-        name = d["Kernel Name"].split("<")[0].split("(")[0].replace("void ", "").strip().split("::")[-1]
+        name = kernel_short_name(d["Kernel Name"])
         if d["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
             v = float(d["Metric Value"].replace(",", ""))
             scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(d.get("Metric Unit", "byte"), 1)
@@ -195,10 +203,10 @@ def ingest_ncu(csv_path, voxels):
         if name in KERNEL_SOURCE:
             out[name] = {"bytes_per_voxel": statistics.median(vs) / voxels, "launches": len(vs),
                          "captured_voxels": voxels, "source_sha": _source_sha(name)}
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    with open(path, "w") as f:
+    with open(out_path, "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)
     print(json.dumps(out))
+    return out
 
 
 def host_link_gbs(torch, nbytes=4 << 30):
