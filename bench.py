@@ -421,7 +421,8 @@ def run_small_configs(ctx, torch, reps=20):
 
 def run_batch(ctx, binding, torch, n=512, NL=6, conn=4, reps=3):
     """Config 3: n 2D uint8 images, sides log-uniform in [64, 2048], as one
-    CUDA-graph replay of the batched pipeline vs n per-image ws_segment calls."""
+    CUDA-graph replay of the batched pipeline vs n per-image ws_segment calls,
+    with the runtime parameters autotuned on the batch first."""
     from paper_2410_08946_gb300 import synth
     img = torch.from_numpy(_pool_2d(SEED + 1)).cuda()
     pool = ctx.gradient(img)
@@ -430,6 +431,15 @@ def run_batch(ctx, binding, torch, n=512, NL=6, conn=4, reps=3):
     grads = [pool[int(offs[2 * i]):int(offs[2 * i]) + h, int(offs[2 * i + 1]):int(offs[2 * i + 1]) + w].contiguous()
              for i, (h, w) in enumerate(shapes)]
     npx = sum(g.numel() for g in grads)
+    outs = [(torch.empty((NL,) + tuple(g.shape), dtype=torch.int32, device="cuda"),
+             torch.empty(NL, dtype=torch.int32, device="cuda")) for g in grads]
+    # the runtime parameters (jumps per round, CTAs per SM of the level kernel)
+    # picked by measurement on this batch, before the graph captures them
+    from paper_2410_08946_gb300 import autotune
+    tuned = autotune.autotune(ctx, lambda: ctx.segment_batch(grads, conn, NL, [o[0] for o in outs],
+                                                             [o[1] for o in outs]),
+                              key=f"batch2d|u8|conn{conn}|NL{NL}|{autotune.size_bucket(npx)}", reps=3)
+    default_ms = next((ms for prm, ms in tuned["table"] if prm == autotune.DEFAULTS), None)
     graph = ctx.graph(grads, conn, NL)
     ctx.check()
     stream = torch.cuda.current_stream()
@@ -443,8 +453,6 @@ def run_batch(ctx, binding, torch, n=512, NL=6, conn=4, reps=3):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_graph = e0.elapsed_time(e1) / reps
-    outs = [(torch.empty((NL,) + tuple(g.shape), dtype=torch.int32, device="cuda"),
-             torch.empty(NL, dtype=torch.int32, device="cuda")) for g in grads]
     for g, (lv, c) in zip(grads, outs):
         ctx.segment(g, conn, NL, lv, c)
     torch.cuda.synchronize()
@@ -464,11 +472,14 @@ def run_batch(ctx, binding, torch, n=512, NL=6, conn=4, reps=3):
     ctx.check()
     phases = {k: round(v[0], 4) for k, v in ctx.phase_times().items() if v[1]}
     ctx.set_profiling(False)
+    ctx.set_tuning()
     return {"workload": f"{n} 2D uint8 crops of a 4096^2 blob gradient, sides log-uniform [64, 2048], "
                         f"{npx} px, 4-connectivity, NL={NL}",
             "batched_graph_ms": ms_graph, "batched_gvox_s": npx / ms_graph / 1e6,
             "per_image_ms": ms_single, "per_image_gvox_s": npx / ms_single / 1e6,
-            "speedup": ms_single / ms_graph, "identical": bool(same), "phases_ms_eager": phases}
+            "speedup": ms_single / ms_graph, "identical": bool(same), "phases_ms_eager": phases,
+            "autotune": {"params": tuned["params"], "eager_ms": tuned["ms"], "eager_ms_defaults": default_ms,
+                         "candidates": len(tuned["table"])}}
 
 
 def run_serve(ctx, binding, torch, seconds=10.0, rate=200.0, NL=4, budget=40 << 30, lanes=4):

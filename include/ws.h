@@ -83,6 +83,8 @@ typedef struct {
     int32_t jumps_per_round;     /* pointer hops per pixel per round (the paper's RR, Sec. 3.1) */
     int32_t barrier_timeout_ms;  /* device-wide barrier wait limit */
     int64_t edge_capacity;       /* slots of the region-adjacency hash table */
+    int32_t levels_ctas_per_sm;  /* CTAs per SM of the cooperative waterfall-level kernel (1..32) */
+    int32_t pad_;                /* reserved, 0 */
 } ws_tuning;
 
 /* ------------------------------------------------------------------------ */

@@ -16,6 +16,7 @@ namespace ws {
 int tune_plateau_cap(const ws_context *c) { return c->tun.plateau_round_cap > 0 ? c->tun.plateau_round_cap : (1 << 24); }
 int tune_jump_cap(const ws_context *c) { return c->tun.jump_round_cap > 0 ? c->tun.jump_round_cap : 4096; }
 int tune_rr(const ws_context *c) { return c->tun.jumps_per_round > 0 ? c->tun.jumps_per_round : 6; }
+int tune_levels_ctas(const ws_context *c) { return c->tun.levels_ctas_per_sm > 0 ? c->tun.levels_ctas_per_sm : 4; }
 unsigned long long tune_timeout_ns(const ws_context *c)
 {
     long long ms = c->tun.barrier_timeout_ms > 0 ? c->tun.barrier_timeout_ms : 4000;
@@ -546,8 +547,9 @@ ws_status ws_context_set_tuning(ws_context *c, const ws_tuning *t)
 {
     if (!c || !t) return WS_ERR_INVALID;
     if (t->plateau_round_cap < 0 || t->jump_round_cap < 0 || t->jumps_per_round < 0 || t->barrier_timeout_ms < 0 ||
-        t->edge_capacity < 0)
+        t->edge_capacity < 0 || t->levels_ctas_per_sm < 0)
         return set_error(c, WS_ERR_INVALID, "tuning values must be >= 0");
+    if (t->levels_ctas_per_sm > 32) return set_error(c, WS_ERR_INVALID, "levels_ctas_per_sm must be <= 32");
     c->tun = *t;
     return WS_OK;
 }

@@ -164,6 +164,7 @@ constexpr size_t kDescBytes = 128;
 int tune_plateau_cap(const ws_context *c);
 int tune_jump_cap(const ws_context *c);
 int tune_rr(const ws_context *c);
+int tune_levels_ctas(const ws_context *c);
 unsigned long long tune_timeout_ns(const ws_context *c);
 
 // Workspace management (ws_api.cu).

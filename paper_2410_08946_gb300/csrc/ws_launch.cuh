@@ -350,7 +350,7 @@ static inline ws_status run_levels(ws_context *c, int NL, const int32_t *idmap, 
         c->launches += 2;
     }
     PhaseScope ps(c, PH_LEVELS, s);
-    int grid = coop_grid(c, k_levels, NTHR, 0, c->num_sms * 4);
+    int grid = coop_grid(c, k_levels, NTHR, 0, c->num_sms * tune_levels_ctas(c));
     if (grid > 4096) grid = 4096;
     e = launch_coop(k_levels, grid, NTHR, 0, s, (Edge *)w.ea, (Edge *)w.eb, w.ecnt, k0_ptr, NL, w.gmap, w.kmax,
                     w.newmin, w.uf, w.rank, w.bsum, counts, c->status, tune_timeout_ns(c));

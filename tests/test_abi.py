@@ -42,7 +42,7 @@ def test_shape_marshalling():
     s = binding._shape_of((3, 5, 7))
     assert (s.ndim, s.dims[0], s.dims[1], s.dims[2]) == (3, 7, 5, 3)
     assert ctypes.sizeof(binding.ws_shape) == 32
-    assert ctypes.sizeof(binding.ws_tuning) == 24
+    assert ctypes.sizeof(binding.ws_tuning) == 32   # 4 x int32, int64, 2 x int32 (include/ws.h)
 
 
 def test_no_oracle_import_in_product():

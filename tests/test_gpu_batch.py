@@ -114,3 +114,39 @@ def test_batch_invalid(ctx):
         ctx.segment_batch([a, b], 4, 2)
     with pytest.raises((binding.WsError, TypeError)):
         ctx.segment_batch([a, torch.zeros((8, 8), dtype=torch.uint16, device="cuda")], 4, 2)
+
+
+def test_autotune_batch(ctx, tmp_path):
+    """The autotuner times the batch under each candidate, leaves the fastest
+    set on the context, caches it, and no parameter changes a label: the tuned
+    batch equals the batch under the defaults and the oracle."""
+    from paper_2410_08946_gb300 import autotune
+    rng = np.random.default_rng(11)
+    shapes = [tuple(int(v) for v in rng.integers(40, 400, size=2)) for _ in range(12)]
+    grads = _blob_grads(shapes, 500, shift=2)
+    ctx.set_tuning()
+    ref_levels, ref_counts = ctx.segment_batch(grads, 4, 4)
+    ctx.check()
+    lv = [torch.empty_like(x) for x in ref_levels]
+    ct = [torch.empty_like(x) for x in ref_counts]
+    space = {"jumps_per_round": [1, 3, 6], "levels_ctas_per_sm": [1, 4]}
+    cache = str(tmp_path / "tune.json")
+    res = autotune.autotune(ctx, lambda: ctx.segment_batch(grads, 4, 4, lv, ct), key="test", reps=2,
+                            space=space, cache_path=cache)
+    assert not res["cached"] and len(res["table"]) == 5
+    assert res["params"]["jumps_per_round"] in (1, 3, 6) and res["params"]["levels_ctas_per_sm"] in (1, 4)
+    for a, b in zip(lv, ref_levels):
+        assert torch.equal(a, b)
+    for a, b in zip(ct, ref_counts):
+        assert torch.equal(a, b)
+    # every candidate gives the same labels (jumps_per_round 1 and one CTA per SM included)
+    for p in ({"jumps_per_round": 1, "levels_ctas_per_sm": 1}, {"jumps_per_round": 16, "levels_ctas_per_sm": 8}):
+        ctx.set_tuning(**p)
+        levels, counts = ctx.segment_batch(grads, 4, 4)
+        ctx.check()
+        assert all(torch.equal(a, b) for a, b in zip(levels, ref_levels))
+    again = autotune.autotune(ctx, lambda: None, key="test", cache_path=cache)
+    assert again["cached"] and again["params"] == res["params"]
+    ref, _ = oracle.segment(grads[3].cpu().numpy(), 4, 4)
+    assert np.array_equal(ref_levels[3].cpu().numpy(), ref)
+    ctx.set_tuning()
