@@ -295,13 +295,6 @@ def run_reference(args):
     return 0
 
 
-def _pool_2d(seed):
-    """4096^2 uint8 blob gradient (32 blobs per 256^2, the small-image density):
-    the images of the batch and of the request stream are crops of it."""
-    from paper_2410_08946_gb300 import synth
-    return synth.blob_image(4096, 4096, 8192, seed)
-
-
 def run_small_configs(ctx, torch, reps=20):
     """Configs 0 and 1 (the 2D cases): 256^2 blob image, gradient + watershed +
     NL=3 (latency, us); 4096^2 blob gradient quantised to 16 levels, 4- and
@@ -424,12 +417,9 @@ def run_batch(ctx, binding, torch, n=512, NL=6, conn=4, reps=3):
     CUDA-graph replay of the batched pipeline vs n per-image ws_segment calls,
     with the runtime parameters autotuned on the batch first."""
     from paper_2410_08946_gb300 import synth
-    img = torch.from_numpy(_pool_2d(SEED + 1)).cuda()
+    img = torch.from_numpy(synth.crop_pool_image(synth.BATCH_POOL_SEED)).cuda()
     pool = ctx.gradient(img)
-    shapes = synth.batch_shapes(n, 64, 2048, seed=SEED + 3)
-    offs = synth.integers(SEED + 3, 41, 2 * n, 0, 4096 - 2048)
-    grads = [pool[int(offs[2 * i]):int(offs[2 * i]) + h, int(offs[2 * i + 1]):int(offs[2 * i + 1]) + w].contiguous()
-             for i, (h, w) in enumerate(shapes)]
+    grads = [pool[y:y + h, x:x + w].contiguous() for y, x, h, w in synth.batch_windows(n)]
     npx = sum(g.numel() for g in grads)
     outs = [(torch.empty((NL,) + tuple(g.shape), dtype=torch.int32, device="cuda"),
              torch.empty(NL, dtype=torch.int32, device="cuda")) for g in grads]
@@ -489,15 +479,16 @@ def run_serve(ctx, binding, torch, seconds=10.0, rate=200.0, NL=4, budget=40 << 
     request on one stream.  Latency = arrival -> labels complete on the device."""
     import numpy as np
     from paper_2410_08946_gb300 import synth
-    img = torch.from_numpy(_pool_2d(SEED + 4)).cuda()
+    img = torch.from_numpy(synth.crop_pool_image(synth.SERVE_SEED)).cuda()
     pool2 = ctx.gradient(img)
-    pool3 = torch.from_numpy(synth.distance_volume(256, 256, 256, sample_seeds(256), seed=SEED + 4)).cuda()
-    reqs = synth.request_stream(rate, seconds, seed=SEED + 4)
+    vs = synth.SERVE_VOLUME_SIDE
+    pool3 = torch.from_numpy(synth.distance_volume(vs, vs, vs, synth.SERVE_VOLUME_SEEDS, seed=synth.SERVE_SEED)).cuda()
+    reqs = synth.request_stream(rate, seconds, seed=synth.SERVE_SEED)
     inputs = []
     for i, r in enumerate(reqs):
         if r["kind"] == "2d":
             h, w = r["shape"]
-            y, x = (i * 7919) % (4097 - h), (i * 104729) % (4097 - w)
+            y, x = synth.request_window_2d(i, h, w)
             inputs.append((pool2[y:y + h, x:x + w].contiguous(), 4))
         else:
             d, h, w = r["shape"]
@@ -514,6 +505,7 @@ def run_serve(ctx, binding, torch, seconds=10.0, rate=200.0, NL=4, budget=40 << 
         srv.poll(srv.submit(g, conn, NL), 120_000_000)
     torch.cuda.synchronize()
     lat, pending = [], []
+    failed = 0
     t0 = time.perf_counter()
     i = 0
     while i < len(inputs) or pending:
@@ -526,8 +518,10 @@ def run_serve(ctx, binding, torch, seconds=10.0, rate=200.0, NL=4, budget=40 << 
             st, lv, c = srv.poll(tk, 0)
             if st == binding.WS_ERR_NOT_READY:
                 still.append((tk, ta))
-            else:
+            elif st == binding.WS_OK:
                 lat.append(time.perf_counter() - t0 - ta)
+            else:
+                failed += 1
         pending = still
         if i < len(inputs) and not pending:
             time.sleep(max(0.0, min(0.001, times[i] - (time.perf_counter() - t0))))
@@ -538,7 +532,8 @@ def run_serve(ctx, binding, torch, seconds=10.0, rate=200.0, NL=4, budget=40 << 
     t1 = time.perf_counter()
     tks = [srv.submit(g, conn, NL) for g, conn in inputs[:n_sat]]
     for tk in tks:
-        srv.poll(tk, 600_000_000)
+        if srv.poll(tk, 600_000_000)[0] != binding.WS_OK:
+            failed += 1
     sat_served = time.perf_counter() - t1
     srv.close()
     # per-image: one ws_segment per request, in arrival order, one stream
@@ -570,7 +565,7 @@ def run_serve(ctx, binding, torch, seconds=10.0, rate=200.0, NL=4, budget=40 << 
             "per_image_p50_ms": pct(lat1, 50), "per_image_p99_ms": pct(lat1, 99),
             "served_gvox_s_saturated": sat_px / sat_served / 1e9,
             "per_image_gvox_s_saturated": sat_px / sat_single / 1e9, "saturation_requests": n_sat,
-            "offered_gvox_s": npx / seconds / 1e9, "served_wall_s": wall_served}
+            "offered_gvox_s": npx / seconds / 1e9, "served_wall_s": wall_served, "failed_requests": failed}
 
 
 def main():

@@ -84,7 +84,12 @@ typedef struct {
     int32_t barrier_timeout_ms;  /* device-wide barrier wait limit */
     int64_t edge_capacity;       /* slots of the region-adjacency hash table */
     int32_t levels_ctas_per_sm;  /* CTAs per SM of the cooperative waterfall-level kernel (1..32) */
-    int32_t pad_;                /* reserved, 0 */
+    int32_t barrier_withhold;    /* failure-detection tests only: 1 arms a one-shot hold, 0 = off.  In
+                                    the next cooperative kernel the context launches, block 0 does not
+                                    arrive at its first device-wide barrier, so the other blocks' waits
+                                    run out after barrier_timeout_ms; the call then reports
+                                    WS_ERR_TIMEOUT through ws_context_check.  Nothing faults or hangs,
+                                    and the hold is disarmed once it has been handed to a launch. */
 } ws_tuning;
 
 /* ------------------------------------------------------------------------ */
@@ -394,6 +399,10 @@ ws_status ws_plateau_distance(ws_context *ctx, const void *grad_d, ws_dtype dtyp
 /* Largest image, in pixels, that ws_watershed_static accepts. */
 #define WS_STATIC_MAX_PIXELS 524288
 
+/* Size of the device array that holds all scratch of ws_watershed_static
+ * (about 14.2 MB; the library checks this figure against its layout). */
+#define WS_STATIC_SCRATCH_BYTES 14193408
+
 /*
  * The result of ws_watershed (the same labels and the same count) for callers
  * that cannot allocate device memory: hosts that reserve all of the GPU's
@@ -402,8 +411,8 @@ ws_status ws_plateau_distance(ws_context *ctx, const void *grad_d, ws_dtype dtyp
  * paper has no counterpart: this is a deployment variant of the watershed.
  *
  * It needs no ws_context and allocates nothing.  All of its scratch lives in
- * one fixed device array inside the library (about 8.3 MB), which every GPU
- * that loads the library holds until the process exits.
+ * one fixed device array inside the library (WS_STATIC_SCRATCH_BYTES), which
+ * every GPU that loads the library holds until the process exits.
  *   - Images of at most WS_STATIC_MAX_PIXELS pixels; a larger image returns
  *     WS_ERR_INVALID and enqueues nothing (use ws_watershed instead).
  *   - grad_d, dtype, shape, connectivity, labels_d as in ws_watershed.
@@ -415,7 +424,12 @@ ws_status ws_plateau_distance(ws_context *ctx, const void *grad_d, ws_dtype dtyp
  *   - Every call uses the same array: calls whose work overlaps on the GPU
  *     (on different streams, or from different host threads) race and
  *     corrupt each other's results.  Issue them one after another on one
- *     stream, or synchronise between them.
+ *     stream, or synchronise between them.  Host threads may call it at the
+ *     same time without harm to the library's host state (each call works on
+ *     its own copy of it), but the results of GPU work that overlaps are
+ *     undefined.
+ *   - Each call starts by clearing the error state a failed earlier call may
+ *     have left, so one call's device error never leaks into the next.
  */
 ws_status ws_watershed_static(const void *grad_d, ws_dtype dtype, const ws_shape *shape, int connectivity,
                               int32_t *labels_d, int32_t *count_d, ws_stream_t stream);

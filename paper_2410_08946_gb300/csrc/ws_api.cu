@@ -17,10 +17,15 @@ int tune_plateau_cap(const ws_context *c) { return c->tun.plateau_round_cap > 0 
 int tune_jump_cap(const ws_context *c) { return c->tun.jump_round_cap > 0 ? c->tun.jump_round_cap : 4096; }
 int tune_rr(const ws_context *c) { return c->tun.jumps_per_round > 0 ? c->tun.jumps_per_round : 6; }
 int tune_levels_ctas(const ws_context *c) { return c->tun.levels_ctas_per_sm > 0 ? c->tun.levels_ctas_per_sm : 4; }
-unsigned long long tune_timeout_ns(const ws_context *c)
+unsigned long long tune_timeout_ns(ws_context *c)
 {
     long long ms = c->tun.barrier_timeout_ms > 0 ? c->tun.barrier_timeout_ms : 4000;
-    return (unsigned long long)ms * 1000000ull;
+    unsigned long long ns = (unsigned long long)ms * 1000000ull;
+    if (c->hold_armed) {   // the one-shot hold of ws_tuning.barrier_withhold goes to this launch
+        c->hold_armed = 0;
+        ns |= kHold;
+    }
+    return ns;
 }
 
 ws_status set_cuda_error(ws_context *c, cudaError_t e, const char *what)
@@ -69,14 +74,18 @@ template <typename P> static void dfree(ws_context *c, P **p, size_t bytes)
     }
 }
 
-// Capacity to allocate when a workspace array must grow from `have` to at
-// least `need`: 1.5x the old capacity (so that a stream of growing requests
-// reallocates rarely; cudaFree synchronises the device), or exactly `need`.
-static size_t grown(size_t need, size_t have, bool exact)
+// Capacity to allocate when a workspace array of `unit` bytes per element must
+// grow from `have` to at least `need` elements: 1.5x the old capacity (so that
+// a stream of growing requests reallocates rarely; cudaFree synchronises the
+// device), or exactly `need` when asked to or when the larger capacity would
+// not fit the context's budget.
+static size_t grown(const ws_context *c, size_t need, size_t have, bool exact, size_t unit)
 {
     if (exact || have == 0) return need;
     const size_t g = have + have / 2;
-    return g > need ? g : need;
+    if (g <= need) return need;
+    if (c->budget && c->held - have * unit + g * unit > c->budget) return need;
+    return g;
 }
 
 static ws_status alloc_pixels(ws_context *c, size_t N)
@@ -120,7 +129,7 @@ ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles)
     if (N > w.N) {
         const size_t have = w.N;
         free_pixels(c);
-        if ((st = alloc_pixels(c, grown(N, have, false))) != WS_OK) {
+        if ((st = alloc_pixels(c, grown(c, N, have, false, 17))) != WS_OK) {
             free_pixels(c);
             if ((st = alloc_pixels(c, N)) != WS_OK) return st;
         }
@@ -132,7 +141,7 @@ ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles)
             dfree(c, &w.act, w.ntiles * 2);
             dfree(c, &w.tlist, w.ntiles * 4);
             w.ntiles = 0;
-            const size_t n = grown(ntiles, have, exact);
+            const size_t n = grown(c, ntiles, have, exact, 7);
             if ((st = dalloc(c, &w.plat, n)) || (st = dalloc(c, &w.act, n * 2)) || (st = dalloc(c, &w.tlist, n * 4))) {
                 w.ntiles = n;  // so that the frees above release what was allocated
                 continue;
@@ -149,11 +158,13 @@ ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles)
     return WS_OK;
 }
 
-ws_status ensure_edges(ws_context *c, size_t cap)
+// Grows the region table to cap slots.  The old arrays are released by
+// cudaFree (which waits for the work that may still use them); the new ones
+// are initialised on `s`, ahead of the calls that use them.
+ws_status ensure_edges(ws_context *c, size_t cap, cudaStream_t s)
 {
     Workspace &w = c->w;
     if (cap <= w.edge_cap) return WS_OK;
-    cudaDeviceSynchronize();
     dfree(c, &w.keys, w.edge_cap * 8);
     dfree(c, &w.vals, w.edge_cap * 4);
     dfree(c, &w.slots, w.edge_cap * 4);
@@ -165,9 +176,9 @@ ws_status ensure_edges(ws_context *c, size_t cap)
         (st = dalloc(c, &w.slots, cap * 4)) || (st = dalloc(c, (uint8_t **)&w.ea, cap * 12)) ||
         (st = dalloc(c, (uint8_t **)&w.eb, cap * 12)))
         return st;
-    cudaError_t e = cudaMemset(w.keys, 0xff, cap * 8);
-    if (e == cudaSuccess) e = cudaMemset(w.vals, 0xff, cap * 4);
-    if (e == cudaSuccess) e = cudaMemset(w.ecount, 0, 4);
+    cudaError_t e = cudaMemsetAsync(w.keys, 0xff, cap * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.vals, 0xff, cap * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.ecount, 0, 4, s);
     if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
     w.edge_cap = cap;
     return WS_OK;
@@ -240,11 +251,11 @@ ws_status ensure_ends(ws_context *c, size_t N, size_t ntiles)
     if (N > w.ncode) {
         const size_t have = w.ncode;
         dfree(c, &w.code, w.ncode * 2);
-        dfree(c, &w.ends, w.ncode * 4);
-        w.ncode = grown(N, have, false);
-        if ((st = dalloc(c, &w.code, w.ncode * 2)) || (st = dalloc(c, &w.ends, w.ncode * 4))) {
+        dfree(c, &w.ends, w.ncode * 8);
+        w.ncode = grown(c, N, have, false, 10);
+        if ((st = dalloc(c, &w.code, w.ncode * 2)) || (st = dalloc(c, &w.ends, w.ncode * 8))) {
             dfree(c, &w.code, w.ncode * 2);
-            dfree(c, &w.ends, w.ncode * 4);
+            dfree(c, &w.ends, w.ncode * 8);
             w.ncode = 0;
             return st;
         }
@@ -252,7 +263,7 @@ ws_status ensure_ends(ws_context *c, size_t N, size_t ntiles)
     if (ntiles > w.ntends) {
         const size_t have = w.ntends;
         dfree(c, &w.tends, w.ntends * 8);
-        w.ntends = grown(ntiles, have, false);
+        w.ntends = grown(c, ntiles, have, false, 8);
         if ((st = dalloc(c, &w.tends, w.ntends * 8))) {
             w.ntends = 0;
             return st;
@@ -273,7 +284,7 @@ ws_status ensure_rgraph(ws_context *c, size_t K, size_t sums, size_t entries)
         const size_t have = r.kcap;
         dfree(c, &r.size, r.kcap * 8);
         dfree(c, &r.row, (r.kcap + 1) * 4);
-        r.kcap = grown(K, have, false);
+        r.kcap = grown(c, K, have, false, 12);
         if ((st = dalloc(c, &r.size, r.kcap * 8)) || (st = dalloc(c, &r.row, (r.kcap + 1) * 4))) {
             dfree(c, &r.size, r.kcap * 8);
             r.kcap = 0;
@@ -283,7 +294,7 @@ ws_status ensure_rgraph(ws_context *c, size_t K, size_t sums, size_t entries)
     if (sums > r.scap) {
         const size_t have = r.scap;
         dfree(c, &r.sum, r.scap * 8);
-        r.scap = grown(sums, have, false);
+        r.scap = grown(c, sums, have, false, 8);
         if ((st = dalloc(c, &r.sum, r.scap * 8))) {
             r.scap = 0;
             return st;
@@ -297,7 +308,7 @@ ws_status ensure_rgraph(ws_context *c, size_t K, size_t sums, size_t entries)
         }
         dfree(c, &r.hist, r.hcap * 4);
         dfree(c, &r.hsum, (r.hcap / 2048 + 2) * 4);
-        r.ecap = grown(entries, have, false);
+        r.ecap = grown(c, entries, have, false, 24);
         r.hcap = 256 * ((r.ecap + 4095) / 4096);
         for (int i = 0; i < 2; i++)
             if ((st = dalloc(c, &r.key[i], r.ecap * 8)) || (st = dalloc(c, &r.val[i], r.ecap * 4))) break;
@@ -322,10 +333,69 @@ ws_status ensure_rec(ws_context *c, size_t bytes)
     if (bytes <= w.rec_n) return WS_OK;
     const size_t have = w.rec_n;
     dfree(c, (uint8_t **)&w.rec, w.rec_n);
-    w.rec_n = grown(bytes, have, false);
+    w.rec_n = grown(c, bytes, have, false, 1);
     ws_status st = dalloc(c, (uint8_t **)&w.rec, w.rec_n);
     if (st) w.rec_n = 0;
     return st;
+}
+
+// Edge-table slots of a call over npix pixels (the sizing in run_core).
+size_t edge_slots(size_t npix, int conn, const ws_context *c)
+{
+    const int halfn = conn == 26 ? 13 : conn / 2;
+    size_t want = npix * (size_t)halfn / 2;
+    if (c && c->tun.edge_capacity > 0) want = (size_t)c->tun.edge_capacity;
+    size_t cap = 1 << 16;
+    while (cap < want && cap < ((size_t)1 << 28)) cap <<= 1;
+    return cap;
+}
+
+size_t workspace_bound(size_t npix, size_t ntiles, size_t nimg, int conn, int NL, bool additive)
+{
+    size_t b = npix * 17 + ntiles * 7 + 4096;                      // per-pixel and per-tile arrays
+    if (conn == 6) b += npix * 10 + ntiles * 8;                    // 3D slot codes, path ends, slot spans
+    if (nimg > 1) b += nimg * (kDescBytes + 4);                    // batch descriptors
+    if (NL > 1) {
+        const size_t kmax = npix / 2 + nimg + 2;
+        b += kmax * (4 * (size_t)(NL - 1) + 12);                   // region graph arrays
+        // region table and edge lists; additive: a bound that holds for any
+        // batch summing such requests (twice the wanted slots covers the
+        // power-of-two rounding of the sum)
+        const int halfn = conn == 26 ? 13 : conn / 2;
+        b += (additive ? npix * (size_t)halfn + ((size_t)1 << 16) : edge_slots(npix, conn, nullptr)) * 40;
+    }
+    return b;
+}
+
+void release_workspace(ws_context *c)
+{
+    Workspace &w = c->w;
+    cudaDeviceSynchronize();
+    free_pixels(c);
+    dfree(c, &w.plat, w.ntiles);
+    dfree(c, &w.act, w.ntiles * 2);
+    dfree(c, &w.tlist, w.ntiles * 4);
+    w.ntiles = 0;
+    dfree(c, &w.code, w.ncode * 2);
+    dfree(c, &w.ends, w.ncode * 8);
+    w.ncode = 0;
+    dfree(c, &w.tends, w.ntends * 8);
+    w.ntends = 0;
+    dfree(c, &w.keys, w.edge_cap * 8);
+    dfree(c, &w.vals, w.edge_cap * 4);
+    dfree(c, &w.slots, w.edge_cap * 4);
+    dfree(c, (uint8_t **)&w.ea, w.edge_cap * 12);
+    dfree(c, (uint8_t **)&w.eb, w.edge_cap * 12);
+    w.edge_cap = 0;
+    dfree(c, &w.gmap, w.kmax * 4 * (size_t)w.levels_cap);
+    dfree(c, &w.newmin, w.kmax * 4);
+    dfree(c, &w.uf, w.kmax * 4);
+    dfree(c, &w.rank, w.kmax * 4);
+    w.kmax = 0;
+    w.levels_cap = 0;
+    dfree(c, &w.descs, w.nbatch * kDescBytes);
+    dfree(c, &w.rbase, (w.nbatch + 1) * 4);
+    w.nbatch = 0;
 }
 
 ws_status ensure_batch(ws_context *c, size_t n)
@@ -550,7 +620,11 @@ ws_status ws_context_set_tuning(ws_context *c, const ws_tuning *t)
         t->edge_capacity < 0 || t->levels_ctas_per_sm < 0)
         return set_error(c, WS_ERR_INVALID, "tuning values must be >= 0");
     if (t->levels_ctas_per_sm > 32) return set_error(c, WS_ERR_INVALID, "levels_ctas_per_sm must be <= 32");
+    if (t->barrier_withhold != 0 && t->barrier_withhold != 1)
+        return set_error(c, WS_ERR_INVALID, "barrier_withhold must be 0 or 1");
     c->tun = *t;
+    c->hold_armed = t->barrier_withhold;
+    c->tun.barrier_withhold = 0;
     return WS_OK;
 }
 

@@ -50,11 +50,17 @@ __device__ __forceinline__ unsigned long long global_ns()
 // Device-wide barrier for a cooperative launch (all blocks co-resident).
 // Bounded: a block that waits longer than timeout_ns records DEV_TIMEOUT and
 // every waiting block returns false (the caller then leaves the kernel).
-// bar_count must be 0 when the kernel starts.
+// bar_count must be 0 when the kernel starts.  Bit 63 of timeout_ns (kHold,
+// set only by failure-detection tests) makes block 0 return false without
+// arriving, so that the other blocks' waits run out.
+constexpr unsigned long long kHold = 1ull << 63;
+
 __device__ __forceinline__ bool grid_barrier(DevStatus *s, unsigned long long timeout_ns)
 {
     __shared__ int ok_s;
     __syncthreads();
+    if ((timeout_ns & kHold) && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) return false;
+    timeout_ns &= ~kHold;
     if (threadIdx.x == 0) {
         int ok = 1;
         volatile unsigned *vgen = &s->bar_gen;

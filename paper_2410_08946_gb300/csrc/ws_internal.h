@@ -26,7 +26,8 @@ struct TileGeo {
 // seen so far and stays resident between calls.
 struct Workspace {
     size_t N = 0;           // pixels the per-pixel arrays can hold
-    int32_t *par = nullptr; // in-tile path ends, then roots                 [N]
+    int32_t *par = nullptr; // in-tile path ends, then roots (3D 6-connectivity:
+                            // the arrows of plateau tiles only)              [N]
     int32_t *aux = nullptr; // smallest index per root, then canonical id    [N]
     int32_t *dist = nullptr;// step II distances (plateau tiles only)        [N]
     size_t ntiles = 0;
@@ -38,10 +39,11 @@ struct Workspace {
     int32_t *rootm = nullptr; // smallest pixel index of each listed root    [rmax]
     int32_t *counters = nullptr;  // plateau tiles, roots, path ends, ...    [4]
     // 3D path ends: per pixel the slot of its in-tile path end, per tile the
-    // span of its slots in `ends` (the end pixel, then its root)
+    // span of its slots in `ends` ((end pixel, next pixel of its path), then
+    // (root, root))
     size_t ncode = 0, ntends = 0;
     uint16_t *code = nullptr;     // [ncode]
-    int32_t *ends = nullptr;      // [ncode]
+    int2 *ends = nullptr;         // [ncode]
     int2 *tends = nullptr;        // (first slot, slot count) per tile  [ntends]
     size_t nwords = 0, ngroups = 0, nchunks = 0;
     uint32_t *bitmap = nullptr;   // one bit per pixel index (kept zero)     [nwords]
@@ -139,6 +141,7 @@ struct ws_context {
     int num_sms = 0;
     unsigned long long launches = 0;  // kernels enqueued by this context
     unsigned long long generation = 0; // bumped whenever workspace is reallocated
+    int hold_armed = 0;                // ws_tuning.barrier_withhold, not yet handed to a launch
     ws::Prof prof;
 };
 
@@ -165,16 +168,26 @@ int tune_plateau_cap(const ws_context *c);
 int tune_jump_cap(const ws_context *c);
 int tune_rr(const ws_context *c);
 int tune_levels_ctas(const ws_context *c);
-unsigned long long tune_timeout_ns(const ws_context *c);
+// The barrier time limit of the next cooperative launch (it also hands over
+// an armed ws_tuning.barrier_withhold, once).
+unsigned long long tune_timeout_ns(ws_context *c);
 
 // Workspace management (ws_api.cu).
 ws_status ensure_pixels(ws_context *c, size_t N, size_t ntiles);
-ws_status ensure_edges(ws_context *c, size_t cap);
+ws_status ensure_edges(ws_context *c, size_t cap, cudaStream_t s);
 ws_status ensure_regions(ws_context *c, size_t kmax, int levels);
 ws_status ensure_batch(ws_context *c, size_t n);
 ws_status ensure_ends(ws_context *c, size_t N, size_t ntiles);
 ws_status ensure_rgraph(ws_context *c, size_t K, size_t sums, size_t entries);
 ws_status ensure_rec(ws_context *c, size_t bytes);
+// Region-table slots of a call over npix pixels (c: the context's tuning, or nullptr).
+size_t edge_slots(size_t npix, int conn, const ws_context *c);
+// Upper bound of the workspace bytes a call (a batch of nimg images, npix
+// pixels and ntiles tiles in all) needs; additive: a per-request bound whose
+// sum over a batch bounds the batch.
+size_t workspace_bound(size_t npix, size_t ntiles, size_t nimg, int conn, int NL, bool additive);
+// Frees every workspace array of the context (after a device synchronisation).
+void release_workspace(ws_context *c);
 ws_status set_error_msg(ws_context *c, ws_status st, const char *msg);
 ws_status set_cuda_error(ws_context *c, cudaError_t e, const char *what);
 

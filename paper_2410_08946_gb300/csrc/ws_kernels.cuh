@@ -1,12 +1,10 @@
 // ws_kernels.cuh -- the kernels and device helpers of libws that are not
-// tiled: step I alone, the union-find, the scans, the region table and the
+// tiled: the union-find, the scans, the region table and the
 // graph-form waterfall, and Alg. 5's image reconstruction; templated on the
 // gradient sample type T (uint8_t / uint16_t) and the connectivity CONN (4, 8
 // in 2D; 6, 26 in 3D) where they touch pixels.  The tiled watershed pipeline
 // (steps I-IV, canonical ids, adjacency, level planes) is in ws_tiles.cuh.
 //
-//   k_step1          Eq. 1 arrows and states (Alg. 1 step I) of every pixel,
-//                    for the ws_step1 entry point
 //   uf_find/uf_union global union-find (path halving; atomicCAS links the
 //                    larger root under the smaller)
 //   k_scan_chunks / k_scan / k_scan_add
@@ -80,56 +78,6 @@ static __device__ __forceinline__ bool nb_at(const Geo &g, int x, int y, int z, 
     if (xx < 0 || xx >= g.W || yy < 0 || yy >= g.H || zz < 0 || zz >= g.D) return false;
     q = (zz * g.H + yy) * g.W + xx;
     return true;
-}
-
-// ---------------------------------------------------------------------------
-// step I (Eq. 1)
-// ---------------------------------------------------------------------------
-
-template <typename T, int CONN>
-static __global__ void __launch_bounds__(NTHR) k_step1(const T *__restrict__ g, Geo geo, int32_t *__restrict__ par,
-                                                uint8_t *__restrict__ st, int32_t *__restrict__ dist,
-                                                uint8_t *__restrict__ act, TileGeo tg)
-{
-    for (int p = blockIdx.x * NTHR + threadIdx.x; p < geo.N; p += gridDim.x * NTHR) {
-        int x, y, z;
-        coords(geo, p, x, y, z);
-        const unsigned gp = g[p];
-        unsigned m = 0xffffffffu;
-        int q = -1;
-#pragma unroll
-        for (int i = 0; i < Nb<CONN>::n; i++) {
-            int r;
-            if (!nb_at<CONN>(geo, x, y, z, i, r)) continue;
-            unsigned v = g[r];
-            if (v < m || (v == m && r > q)) {
-                m = v;
-                q = r;
-            }
-        }
-        uint8_t s;
-        int32_t l;
-        if (q < 0 || m > gp) {
-            s = 1;
-            l = p;
-        } else if (m < gp) {
-            s = 0;
-            l = q;
-        } else if (q > p) {
-            s = 2;
-            l = q;
-        } else {
-            s = 3;
-            l = p;
-        }
-        par[p] = l;
-        st[p] = s;
-        if (dist) dist[p] = s == 0 ? 0 : INF_D;
-        if (act && s >= 2) {
-            int t = ((z / tg.TZ) * tg.nty + y / tg.TY) * tg.ntx + x / tg.TX;
-            act[t] = 1;
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------

@@ -54,22 +54,6 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes)
 static inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 // ---------------------------------------------------------------------------
-// step I alone (debug entry point)
-// ---------------------------------------------------------------------------
-
-template <typename T, int CONN> static ws_status run_step1(ws_context *c, const void *grad, const Geo &geo,
-                                                           uint8_t *states, int32_t *arrows, cudaStream_t s)
-{
-    TileGeo tg = make_tilegeo<CONN>(geo);
-    PhaseScope ps(c, PH_STEP1, s);
-    k_step1<T, CONN><<<pixel_grid(c, geo.N), NTHR, 0, s>>>((const T *)grad, geo, arrows, states, nullptr,
-                                                           nullptr, tg);
-    c->launches += 1;
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "step1 launch");
-}
-
-// ---------------------------------------------------------------------------
 // the tiled watershed core (one image, or a batch of images)
 // ---------------------------------------------------------------------------
 
@@ -107,9 +91,15 @@ template <int CONN> static Batch single_batch(const Geo &g, const void *grad, in
     return b;
 }
 
-// Steps I and II: leaves in-tile path ends in w.par, step II distances of
-// the plateau tiles in w.dist, the plateau tiles in w.tlist.
-template <typename T, int CONN> static ws_status run_front(ws_context *c, const Batch &b, cudaStream_t s)
+// Steps I and II: leaves in-tile path ends in w.par (3D 6-connectivity: the
+// slot codes and path ends, and the arrows of plateau tiles), step II
+// distances of the plateau tiles in w.dist, the plateau tiles in w.tlist.
+// full: the arrow of every pixel in w.par (3D 6-connectivity; the other
+// paths always write every pixel), the states and arrows of Eq. 1 into ex
+// when ex.s is set, and no step II when step1_only.
+template <typename T, int CONN> static ws_status run_front(ws_context *c, const Batch &b, cudaStream_t s,
+                                                           bool full = false, StepExport ex = StepExport{},
+                                                           bool step1_only = false)
 {
     using C = TC<CONN>;
     Workspace &w = c->w;
@@ -126,38 +116,33 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
         CUtensorMap tm;
         const bool tma = !b.d && make_tmap_3d(&tm, b.one.grad, sizeof(T), b.one.W, b.one.H, b.one.D, B::RW, C::HY,
                                               C::HZ);
+        if (!tma) memset(&tm, 0, sizeof tm);
         if constexpr (CONN == 6) {
             // k_init6 is the 3D specialisation (it also numbers the path ends)
             using B6 = Init6Box<T>;
-            if (tma) {
-                if ((e = allow_smem(k_init6<T, true>, B6::SMEM_TMA)) != cudaSuccess)
-                    return set_cuda_error(c, e, "smem attribute");
-                const int grid = coop_grid(c, k_init6<T, true>, C::NT, B6::SMEM_TMA, b.ntiles);
-                k_init6<T, true><<<grid, C::NT, B6::SMEM_TMA, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act,
-                                                                   w.tlist, w.roots, w.code, w.ends, w.tends,
-                                                                   w.counters, c->status);
-            } else {
-                memset(&tm, 0, sizeof tm);
-                if ((e = allow_smem(k_init6<T, false>, B6::SMEM_PLAIN)) != cudaSuccess)
-                    return set_cuda_error(c, e, "smem attribute");
-                k_init6<T, false><<<b.ntiles, C::NT, B6::SMEM_PLAIN, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act,
-                                                                          w.tlist, w.roots, w.code, w.ends, w.tends,
-                                                                          w.counters, c->status);
-            }
-        } else if (tma) {
-            if ((e = allow_smem(k_init<T, CONN, true>, B::SMEM_TMA)) != cudaSuccess)
-                return set_cuda_error(c, e, "smem attribute");
-            const int grid = coop_grid(c, k_init<T, CONN, true>, C::NT, B::SMEM_TMA, b.ntiles);
-            k_init<T, CONN, true><<<grid, C::NT, B::SMEM_TMA, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act,
-                                                                   w.tlist, w.roots, w.counters, c->status);
+            auto kern = tma ? (full ? k_init6<T, true, true> : k_init6<T, true, false>)
+                            : (full ? k_init6<T, false, true> : k_init6<T, false, false>);
+            const size_t smem = tma ? B6::SMEM_TMA : B6::SMEM_PLAIN;
+            if ((e = allow_smem(kern, smem)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
+            // TMA: persistent CTAs, two tiles in flight each; plain loads: one CTA per tile
+            const int grid = tma ? coop_grid(c, kern, C::NT, smem, b.ntiles) : b.ntiles;
+            kern<<<grid, C::NT, smem, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act, w.tlist, w.roots, w.code,
+                                           w.ends, w.tends, w.counters, c->status, ex);
         } else {
-            memset(&tm, 0, sizeof tm);
-            if ((e = allow_smem(k_init<T, CONN, false>, B::SMEM_PLAIN)) != cudaSuccess)
-                return set_cuda_error(c, e, "smem attribute");
-            k_init<T, CONN, false><<<b.ntiles, C::NT, B::SMEM_PLAIN, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act,
-                                                                         w.tlist, w.roots, w.counters, c->status);
+            const bool exp = ex.s != nullptr;
+            auto kern = tma ? (exp ? k_init<T, CONN, true, true> : k_init<T, CONN, true, false>)
+                            : (exp ? k_init<T, CONN, false, true> : k_init<T, CONN, false, false>);
+            const size_t smem = tma ? B::SMEM_TMA : B::SMEM_PLAIN;
+            if ((e = allow_smem(kern, smem)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
+            const int grid = tma ? coop_grid(c, kern, C::NT, smem, b.ntiles) : b.ntiles;
+            kern<<<grid, C::NT, smem, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act, w.tlist, w.roots, w.counters,
+                                           c->status, ex);
         }
         c->launches += 1;
+    }
+    if (step1_only) {
+        e = cudaGetLastError();
+        return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "step1 launch");
     }
     {
         PhaseScope ps(c, PH_PLATEAU, s);
@@ -197,23 +182,19 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
         // one CTA per tile at most (only plateau tiles have work)
         const int grid = coop_grid(c, k_jump2<CONN>, NTHR, 0, b.ntiles < c->num_sms * 8 ? b.ntiles : c->num_sms * 8);
         e = launch_coop(k_jump2<CONN>, grid, NTHR, 0, s, b, w.par, (const int32_t *)w.dist, (const int32_t *)w.tlist,
-                        w.counters, w.roots, tune_rr(c), c->status, tune_jump_cap(c), tune_timeout_ns(c));
+                        w.counters, w.roots, tune_rr(c), c->status, tune_jump_cap(c), tune_timeout_ns(c),
+                        (const uint8_t *)w.plat, w.ends, (const int2 *)w.tends);
         c->launches += 1;
         if (e != cudaSuccess) return set_cuda_error(c, e, "jump launch");
     }
     if (do_rag) {
         // distinct adjacent basin pairs: about 3 K0 <= 1.5 N for a fragmented 2D
         // image; slots for a load factor <= 1/2 (capped at 2^28 slots)
-        const int halfn = Nb<CONN>::n / 2;
-        size_t want = (size_t)b.npix * halfn / 2;
-        if (c->tun.edge_capacity > 0) want = (size_t)c->tun.edge_capacity;
-        size_t cap = 1 << 16;
-        while (cap < want && cap < ((size_t)1 << 28)) cap <<= 1;
-        if ((st = ensure_edges(c, cap)) != WS_OK) return st;
+        if ((st = ensure_edges(c, edge_slots((size_t)b.npix, CONN, c), s)) != WS_OK) return st;
     }
     if constexpr (CONN == 6) {  // 3D: roots of the tiles' path ends
         PhaseScope pc(c, PH_CHASE, s);
-        k_chase<<<c->num_sms * 8, NTHR, 0, s>>>(b, w.ends, w.tends, w.code, w.counters, w.par, c->status);
+        k_chase<<<c->num_sms * 8, NTHR, 0, s>>>(b, w.ends, w.tends, w.code, w.counters, c->status);
         c->launches += 1;
     }
     {
@@ -237,7 +218,7 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
             }
             auto kern = tma6 ? k_rag6<T, true> : k_rag6<T, false>;
             if ((e = allow_smem(kern, B6::SMEM)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
-            kern<<<b.ntiles, C::NT, B6::SMEM, s>>>(tmc, tmg, b, w.code, w.ends, w.tends, w.par, w.aux, do_rag ? 1 : 0,
+            kern<<<b.ntiles, C::NT, B6::SMEM, s>>>(tmc, tmg, b, w.code, w.ends, w.tends, w.aux, do_rag ? 1 : 0,
                                                    w.keys, w.vals, w.slots, w.ecount, gmask, c->status);
         } else if (tma) {
             if ((e = allow_smem(k_label<T, CONN, true>, B::SMEM)) != cudaSuccess)
@@ -447,13 +428,25 @@ template <typename T, int CONN> static ws_status run_plateau_distance(ws_context
                                                                       cudaStream_t s)
 {
     const Batch b = single_batch<CONN>(geo, grad, nullptr, nullptr);
-    ws_status st = run_front<T, CONN>(c, b, s);
+    ws_status st = run_front<T, CONN>(c, b, s, true);   // every pixel's arrow (k_dist_out2 reads them)
     if (st != WS_OK) return st;
     k_dist_out2<<<pixel_grid(c, geo.N), NTHR, 0, s>>>(geo, tiles_for<CONN>(geo), c->w.par, c->w.dist, c->w.plat,
                                                       dist);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "plateau distance");
+}
+
+// Step I alone (ws_step1): the states and arrows of Eq. 1 as the tiled step I
+// kernels of the segmentation path compute them.
+template <typename T, int CONN> static ws_status run_step1(ws_context *c, const void *grad, const Geo &geo,
+                                                           uint8_t *states, int32_t *arrows, cudaStream_t s)
+{
+    const Batch b = single_batch<CONN>(geo, grad, nullptr, nullptr);
+    StepExport ex;
+    ex.s = states;
+    ex.l = arrows;
+    return run_front<T, CONN>(c, b, s, true, ex, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -475,12 +468,7 @@ template <typename T, int CONN> static ws_status run_waterfall(ws_context *c, co
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "waterfall launch");
     }
-    const int halfn = Nb<CONN>::n / 2;
-    size_t want = (size_t)geo.N * halfn / 2;
-    if (c->tun.edge_capacity > 0) want = (size_t)c->tun.edge_capacity;
-    size_t cap = 1 << 16;
-    while (cap < want && cap < ((size_t)1 << 28)) cap <<= 1;
-    ws_status st = ensure_edges(c, cap);
+    ws_status st = ensure_edges(c, edge_slots((size_t)geo.N, CONN, c), s);
     if (st != WS_OK) return st;
     st = ensure_regions(c, kmax, NL - 1);
     if (st != WS_OK) return st;

@@ -326,14 +326,7 @@ ws_status region_graph_build(ws_context *c, const int32_t *L, const void *grad, 
     const long long K = (long long)h[0] + 1;
     if (K > N) return set_error_msg(c, WS_ERR_INVALID, "label ids must be below the pixel count");
     // region table: the same sizing as the waterfall's (load factor <= 1/2)
-    {
-        const int halfn = conn == 4 ? 2 : conn == 8 ? 4 : conn == 6 ? 3 : 13;
-        size_t want = (size_t)N * halfn / 2;
-        if (c->tun.edge_capacity > 0) want = (size_t)c->tun.edge_capacity;
-        size_t cap = 1 << 16;
-        while (cap < want && cap < ((size_t)1 << 28)) cap <<= 1;
-        if ((st = ensure_edges(c, cap)) != WS_OK) return st;
-    }
+    if ((st = ensure_edges(c, edge_slots((size_t)N, conn, c), s)) != WS_OK) return st;
     if ((st = ensure_rgraph(c, (size_t)K, (size_t)K * C, 1)) != WS_OK) return st;
     {
         PhaseScope ps(c, PH_EXPORT, s);

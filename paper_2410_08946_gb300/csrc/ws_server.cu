@@ -53,12 +53,17 @@ size_t pixels_of(const ws_shape &s)
     return n > 0 ? (size_t)n : 0;
 }
 
-// Device bytes a request occupies in a lane: workspace (per-pixel arrays,
-// region table and graph) plus staging of host inputs and outputs.
+// Device bytes a request occupies in a lane, an upper bound whose sum over a
+// batch bounds the batch: workspace (per-pixel and per-tile arrays, region
+// table and graph, as the context sizes them) plus staging of host inputs and
+// outputs (with their growth margin).
 size_t estimate(const ws_request &r, size_t N)
 {
-    size_t b = N * 24 + N * (size_t)(r.NL > 1 ? 8 + 2 * (r.NL - 1) : 0) + (1 << 20);
-    if (r.on_host) b += N * (r.dtype == WS_U8 ? 1 : 2) + N * 4 * (size_t)r.NL + 256;
+    const int64_t W = r.shape.dims[0], H = r.shape.dims[1], D = r.shape.ndim == 3 ? r.shape.dims[2] : 1;
+    // tiles: at least 32 x 16 (x 16) pixels each, so this counts them from above
+    const size_t tiles = (size_t)((W + 31) / 32) * (size_t)((H + 15) / 16) * (size_t)((D + 15) / 16);
+    size_t b = ws::workspace_bound(N, tiles, 2, r.connectivity, r.NL, true);
+    if (r.on_host) b += (N * (r.dtype == WS_U8 ? 1 : 2) + 256 + N * 4 * (size_t)r.NL) * 3 / 2;
     return b;
 }
 
@@ -152,6 +157,15 @@ ws_status launch_batch(ws_server *s, int li, std::vector<Req *> &batch)
     }
     ws_status st = ws_segment_batch(L.ctx, (int)batch.size(), items.data(), h.dtype, h.connectivity, h.NL,
                                     (ws_stream_t)L.stream);
+    if (st == WS_ERR_OOM) {
+        // the batch fits the lane's share (admission), but arrays kept from
+        // earlier batches may not leave room for it: start from an empty
+        // workspace once
+        cudaStreamSynchronize(L.stream);
+        ws::release_workspace(L.ctx);
+        st = ws_segment_batch(L.ctx, (int)batch.size(), items.data(), h.dtype, h.connectivity, h.NL,
+                              (ws_stream_t)L.stream);
+    }
     if (st != WS_OK) return st;
     if (host) {
         for (size_t i = 0; i < batch.size(); i++) {

@@ -46,9 +46,10 @@ constexpr size_t OFF_COUNTERS = OFF_TLIST + a256(kMaxTiles * 4);
 constexpr size_t OFF_STATUS = OFF_COUNTERS + 256;
 constexpr size_t OFF_KCOUNT = OFF_STATUS + a256(sizeof(DevStatus));
 constexpr size_t OFF_CODE = OFF_KCOUNT + 256;                  // 3D path: slot code per pixel
-constexpr size_t OFF_ENDS = OFF_CODE + a256(kMaxPixels * 2);   // 3D path: path ends, then roots
-constexpr size_t OFF_TENDS = OFF_ENDS + a256(kMaxPixels * 4);  // 3D path: slot span per tile
+constexpr size_t OFF_ENDS = OFF_CODE + a256(kMaxPixels * 2);   // 3D path: (end, next), then (root, root)
+constexpr size_t OFF_TENDS = OFF_ENDS + a256(kMaxPixels * 8);  // 3D path: slot span per tile
 constexpr size_t kScratchBytes = OFF_TENDS + a256(kMaxTiles * 8);
+static_assert(kScratchBytes == (size_t)WS_STATIC_SCRATCH_BYTES, "WS_STATIC_SCRATCH_BYTES must match the layout");
 
 }  // namespace
 
@@ -59,7 +60,7 @@ static __device__ __align__(256) unsigned char ws_static_scratch[kScratchBytes];
 namespace {
 
 // Reports a device-side error of the call through the count output (-1) and
-// returns the status word to zero for the next call.
+// returns the status word to zero.
 __global__ void k_static_finish(int32_t *count)
 {
     DevStatus *s = reinterpret_cast<DevStatus *>(ws_static_scratch + OFF_STATUS);
@@ -73,7 +74,7 @@ __global__ void k_static_finish(int32_t *count)
 
 struct Slot {
     bool ready = false;
-    ws_context ctx;  // never owns memory: its workspace points into the scratch array
+    ws_context ctx;  // never owns memory: its workspace points into the scratch array (each call copies it)
 };
 constexpr int kMaxDevices = 64;
 Slot g_slots[kMaxDevices];
@@ -81,7 +82,9 @@ std::mutex g_mu;
 
 // Once per device, with that device current: the device address of the
 // scratch array, carved into the workspace of a context that never allocates.
-ws_status setup(int dev, ws_context **out)
+// *out receives a copy, so that host threads calling at the same time share
+// no host state.
+ws_status setup(int dev, ws_context *out)
 {
     std::lock_guard<std::mutex> lock(g_mu);
     Slot &sl = g_slots[dev];
@@ -120,12 +123,12 @@ ws_status setup(int dev, ws_context **out)
         w.kcount = reinterpret_cast<int32_t *>(base + OFF_KCOUNT);
         w.ncode = kMaxPixels;
         w.code = reinterpret_cast<uint16_t *>(base + OFF_CODE);
-        w.ends = reinterpret_cast<int32_t *>(base + OFF_ENDS);
+        w.ends = reinterpret_cast<int2 *>(base + OFF_ENDS);
         w.ntends = kMaxTiles;
         w.tends = reinterpret_cast<int2 *>(base + OFF_TENDS);
         sl.ready = true;
     }
-    *out = &sl.ctx;
+    *out = sl.ctx;
     return WS_OK;
 }
 
@@ -150,9 +153,10 @@ extern "C" ws_status ws_watershed_static(const void *grad_d, ws_dtype dtype, con
         cudaGetLastError();
         return WS_ERR_CUDA;
     }
-    ws_context *c = nullptr;
-    ws_status st = setup(dev, &c);
+    ws_context local;
+    ws_status st = setup(dev, &local);
     if (st != WS_OK) return st;
+    ws_context *c = &local;
     Geo g;
     g.W = (int)W;
     g.H = (int)H;
@@ -164,6 +168,12 @@ extern "C" ws_status ws_watershed_static(const void *grad_d, ws_dtype dtype, con
     const Launchers *L = launchers(dtype, connectivity);
     if (!L) return WS_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
+    // clear the error state an earlier call that failed on the host side may
+    // have left (its k_static_finish never ran)
+    if (cudaMemsetAsync(c->status, 0, offsetof(DevStatus, bar_count), s) != cudaSuccess) {
+        cudaGetLastError();
+        return WS_ERR_CUDA;
+    }
     st = L->watershed(c, grad_d, g, labels_d, count_d, s);
     if (st != WS_OK) return st;
     k_static_finish<<<1, 32, 0, s>>>(count_d);

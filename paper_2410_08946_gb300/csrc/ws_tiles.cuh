@@ -206,6 +206,16 @@ template <int CONN> __device__ __forceinline__ int tile_of_c(const TileGeo &tg, 
 // state codes kept in registers by k_init
 enum : int { ST0 = 0, ST1 = 1, STP = 2, STOUT = 3 };
 
+// Optional outputs of step I (ws_step1): the state of Eq. 1 (0: a lower
+// neighbour; 1: a strict minimum; 2 / 3: an equal lowest neighbour with a
+// larger / smaller index) and the arrow (the lowest neighbour for states 0 and
+// 2, the pixel itself for 1 and 3) of every pixel, as computed by the tiled
+// step I kernels of the segmentation path.
+struct StepExport {
+    uint8_t *s = nullptr;
+    int32_t *l = nullptr;
+};
+
 // ---------------------------------------------------------------------------
 // k_init: step I + in-tile path reduction
 // ---------------------------------------------------------------------------
@@ -240,9 +250,9 @@ __device__ __forceinline__ void init_issue(const CUtensorMap *tm, T *dst, uint64
 // The thread's pixels are slots k = 0..PER-1 of one column of the tile (the
 // z column in 3D, every NT/TX-th row in 2D); in 3D the column and its four
 // side columns are read once into registers and the z neighbours reused.
-template <typename T, int CONN, bool CHECK>
+template <typename T, int CONN, bool CHECK, bool EXP>
 __device__ __forceinline__ int init_step1(const T *gs, int *nx, int (&st)[TC<CONN>::PER], int tid, int x0, int y0,
-                                          int z0, const Geo &geo, int base)
+                                          int z0, const Geo &geo, int base, const StepExport &ex)
 {
     using C = TC<CONN>;
     using B = InitBox<T, CONN>;
@@ -288,33 +298,47 @@ __device__ __forceinline__ int init_step1(const T *gs, int *nx, int (&st)[TC<CON
                 qn = n;
             }
         }
+        // the lowest neighbour (global index), when there is one
+        const int q = qn < 0 ? p : p + (Nb<CONN>::dz(qn) * geo.H + Nb<CONN>::dy(qn)) * geo.W + Nb<CONN>::dx(qn);
         if (qn < 0 || m > gp) {
             st[k] = ST1;
             nx[i] = enc_final(p);
+            if (EXP) {
+                ex.s[p] = 1;
+                ex.l[p] = p;
+            }
         } else if (m < gp) {
             st[k] = ST0;
             const int lxx = lx + Nb<CONN>::dx(qn), lyy = ly + Nb<CONN>::dy(qn), lzz = lz + Nb<CONN>::dz(qn);
             if (lxx >= 0 && lxx < C::TX && lyy >= 0 && lyy < C::TY && lzz >= 0 && lzz < C::TZ)
                 nx[i] = (lzz * C::TY + lyy) * C::TX + lxx;
             else
-                nx[i] = enc_final(p + (Nb<CONN>::dz(qn) * geo.H + Nb<CONN>::dy(qn)) * geo.W + Nb<CONN>::dx(qn));
+                nx[i] = enc_final(q);
+            if (EXP) {
+                ex.s[p] = 0;
+                ex.l[p] = q;
+            }
         } else {
             st[k] = STP;  // plateau pixel: resolved by step II / step IV
             nx[i] = enc_final(p);
             plateau = 1;
+            if (EXP) {   // state 2 when the equal lowest neighbour comes later in index order
+                ex.s[p] = (uint8_t)(q > p ? 2 : 3);
+                ex.l[p] = q > p ? q : p;
+            }
         }
     }
     return plateau;
 }
 
 // 26-connectivity: at most 64 registers, so that two CTAs share an SM
-template <typename T, int CONN, bool TMA>
+// EXP: also writes the states and arrows of Eq. 1 into ex (ws_step1).
+template <typename T, int CONN, bool TMA, bool EXP>
 __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
-    k_init(const __grid_constant__ CUtensorMap tm, const Batch b,
-                                                       int32_t *__restrict__ par, int32_t *__restrict__ mi,
-                                                       int32_t *__restrict__ dist, uint8_t *__restrict__ plat,
-                                                       uint8_t *__restrict__ act, int32_t *__restrict__ tlist,
-                                                       int32_t *__restrict__ roots, int32_t *counters, DevStatus *status)
+    k_init(const __grid_constant__ CUtensorMap tm, const Batch b, int32_t *__restrict__ par,
+           int32_t *__restrict__ mi, int32_t *__restrict__ dist, uint8_t *__restrict__ plat,
+           uint8_t *__restrict__ act, int32_t *__restrict__ tlist, int32_t *__restrict__ roots, int32_t *counters,
+           DevStatus *status, const StepExport ex)
 {
     using C = TC<CONN>;
     using B = InitBox<T, CONN>;
@@ -379,9 +403,9 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
         const bool interior = x0 >= 1 && x0 + C::TX < geo.W && y0 >= 1 && y0 + C::TY < geo.H &&
                               (!C::D3 || (z0 >= 1 && z0 + C::TZ < geo.D));
         if (interior)
-            plateau = init_step1<T, CONN, false>(gs, nx, st, tid, x0, y0, z0, geo, base);
+            plateau = init_step1<T, CONN, false, EXP>(gs, nx, st, tid, x0, y0, z0, geo, base, ex);
         else
-            plateau = init_step1<T, CONN, true>(gs, nx, st, tid, x0, y0, z0, geo, base);
+            plateau = init_step1<T, CONN, true, EXP>(gs, nx, st, tid, x0, y0, z0, geo, base, ex);
         __syncthreads();  // the gradient box of stage s is no longer read
         if (TMA && tid == 0 && t + 2 * G < b.ntiles)
             init_issue<T, CONN, TMA>(&tm, gs, &bars[s], b, t + 2 * G);
@@ -467,14 +491,20 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
 //
 // Step I (Eq. 1) and step III inside the tile, for the 3D path (k_init6,
 // k_chase, k_rag6):
-//   - par[p] is the arrow of Eq. 1 (the lowest neighbour), or p itself for a
-//     strict minimum or a plateau pixel (resolved later by step II / IV);
 //   - a pixel whose arrow leaves the tile, a minimum and a plateau pixel end
 //     their in-tile paths; the ends of tile t get slots 0..n-1, ends[first +
-//     slot] is the end pixel and tends[t] = (first, n);
+//     slot] = (end pixel, next pixel of its path: the neighbour its arrow
+//     leads to, or itself for a minimum or a plateau pixel) and tends[t] =
+//     (first, n);
 //   - pointer doubling (ends point at themselves; a thread's column of
 //     pointers in registers, every load of a round issued before any store)
-//     takes every pixel to its end: code[p] is the slot of p's end.
+//     takes every pixel to its end: the low 13 bits of code[p] are the slot
+//     of p's end (the top three, its end's lowest neighbour, are masked off
+//     by every reader);
+//   - only on plateau tiles, par[p] is the arrow of Eq. 1 (the lowest
+//     neighbour), or p itself for a strict minimum or a plateau pixel
+//     (resolved later by step II / IV); no other kernel of the path reads an
+//     arrow, so the other tiles write none.
 // Step I picks the lowest neighbour with one integer minimum over packed
 // keys (value << 3 | 7 - n, so that ties go to the later neighbour n in
 // ascending index order) and has no divergent branches.
@@ -488,16 +518,24 @@ template <typename T> struct Init6Box {
     static constexpr int SMEM_PLAIN = B::STAGE + NPIX * 4 + NPIX * 2;
 };
 
+// Global offset of neighbour n (ascending index order: -z, -y, -x, +x, +y, +z).
+__device__ __forceinline__ int go6(int n, const Geo &geo)
+{
+    const int a = n == 0 || n == 5 ? geo.HW : (n == 1 || n == 4 ? geo.W : 1);
+    return n < 3 ? -a : a;
+}
+
 // Step I on the thread's column (z = 0..TZ-1): in-tile pointers into nx
-// (ends point at themselves), the arrow into par, states into stb (two bits
-// per pixel), ends into endb, strict minima into minb; mi = INT_MAX for every
-// pixel that can be a root.  CHECK = false for a tile whose halo lies inside
-// the image.
-template <typename T, bool CHECK>
-__device__ __forceinline__ void init6_step1(const T *gs, int *nx, int32_t *par, int32_t *mi, const int *lo_tab,
-                                            const int *go_tab, int tid, int lx, int ly, int h0, int p0, int x, int y,
+// (ends point at themselves), the lowest neighbour n of every pixel into the
+// top three bits of its slotof entry (n << 13), states into stb (two bits per
+// pixel), ends into endb, strict minima into minb.  CHECK = false for a tile
+// whose halo lies inside the image.  FULL also writes every pixel's arrow into
+// par; when ex.s is set, the states and arrows of Eq. 1 go into ex.
+template <typename T, bool CHECK, bool FULL>
+__device__ __forceinline__ void init6_step1(const T *gs, int *nx, uint16_t *slotof, int32_t *par,
+                                            const int *lo_tab, int tid, int lx, int ly, int h0, int p0, int x, int y,
                                             int z0, const Geo &geo, unsigned &stb, unsigned &endb, unsigned &minb,
-                                            int &plateau)
+                                            int &plateau, const StepExport &ex)
 {
     using C = TC<6>;
     using B = InitBox<T, 6>;
@@ -537,8 +575,17 @@ __device__ __forceinline__ void init6_step1(const T *gs, int *nx, int32_t *par, 
         const bool follow = in && st0 && (tin & 1u);   // the arrow stays in the tile
         const int nn = has ? n : 0;
         nx[i] = follow ? i + lo_tab[nn] : i;
-        if (in) par[p] = st0 ? p + go_tab[nn] : p;
-        if (in && !st0) mi[p] = 0x7fffffff;   // a root candidate: its smallest index is taken later
+        if (FULL && in) par[p] = st0 ? p + go6(nn, geo) : p;
+        // Only ws_step1 sets ex.s.  The uniform branch costs one instruction
+        // per pixel and also keeps the compiler from interleaving all sixteen
+        // pixels of the column (which runs out of registers).
+        if (in && ex.s) {   // Eq. 1: state 2 when the equal lowest neighbour comes later, 3 when earlier
+            const bool later = nn >= 3;
+            const int q = p + go6(nn, geo);
+            ex.s[p] = (uint8_t)(st0 ? 0 : (st1 ? 1 : (later ? 2 : 3)));
+            ex.l[p] = st0 || (!st1 && later) ? q : p;
+        }
+        slotof[i] = (uint16_t)(nn << 13);
         plateau |= state == STP;
         stb |= (unsigned)state << (2 * k);
         endb |= (unsigned)(in && !follow) << k;
@@ -546,14 +593,19 @@ __device__ __forceinline__ void init6_step1(const T *gs, int *nx, int32_t *par, 
     }
 }
 
-template <typename T, bool TMA>
+// FULL: the variant of the step I entry points (ws_step1, ws_plateau_distance),
+// which also writes every pixel's arrow into par and optionally exports the
+// states and arrows.  The segmentation path writes par on plateau tiles only
+// (the step II / IV kernels and k_jump2 work there); elsewhere the arrow of a
+// path end travels with it in `ends`.
+template <typename T, bool TMA, bool FULL>
 __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ CUtensorMap tm, const Batch b,
                                                         int32_t *__restrict__ par, int32_t *__restrict__ mi,
                                                         int32_t *__restrict__ dist, uint8_t *__restrict__ plat,
                                                         uint8_t *__restrict__ act, int32_t *__restrict__ tlist,
                                                         int32_t *__restrict__ roots, uint16_t *__restrict__ code,
-                                                        int32_t *__restrict__ ends, int2 *__restrict__ tends,
-                                                        int32_t *counters, DevStatus *status)
+                                                        int2 *__restrict__ ends, int2 *__restrict__ tends,
+                                                        int32_t *counters, DevStatus *status, const StepExport ex)
 {
     using C = TC<6>;
     using B = InitBox<T, 6>;
@@ -563,7 +615,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
     __shared__ uint64_t bars[2];
     __shared__ int wbase[NW];
     __shared__ int s_first;
-    __shared__ int lo_tab[6], go_tab[6];
+    __shared__ int lo_tab[6];
     int *nx = (int *)(smem + (TMA ? 2 : 1) * B::STAGE);
     uint16_t *slotof = (uint16_t *)(nx + C::NPIX);
     const int tid = threadIdx.x, lane = tid & 31, lx = lane, ly = tid >> 5;
@@ -594,10 +646,6 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
         const TileCtx tc = tile_ctx<6>(b, t);
         const Geo &geo = tc.geo;
         const int x0 = tc.x0, y0 = tc.y0, z0 = tc.z0, base = tc.base;
-        if (tid < 6) {  // global offsets (the image may change from tile to tile in a batch)
-            const int gofs[6] = {-geo.HW, -geo.W, -1, 1, geo.W, geo.HW};
-            go_tab[tid] = gofs[tid];
-        }
         if (TMA) {
             const bool ok = mbar_wait(&bars[s], (unsigned)((j >> 1) & 1), status);
             if (__syncthreads_or(!ok)) return;
@@ -638,14 +686,17 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
         unsigned minb = 0;  // bit k: pixel k of the column is a strict minimum
         int plateau = 0;
         if (interior)
-            init6_step1<T, false>(gs, nx, par, mi, lo_tab, go_tab, tid, lx, ly, h0, p0, x, y, z0, geo, stb, endb,
-                                  minb, plateau);
+            init6_step1<T, false, FULL>(gs, nx, slotof, par, lo_tab, tid, lx, ly, h0, p0, x, y, z0, geo, stb, endb,
+                                        minb, plateau, ex);
         else
-            init6_step1<T, true>(gs, nx, par, mi, lo_tab, go_tab, tid, lx, ly, h0, p0, x, y, z0, geo, stb, endb,
-                                 minb, plateau);
-        // the strict minima are roots: list them
-        for (unsigned m = minb; m; m &= m - 1)
-            roots[atomicAdd(counters + CNT_ROOTS, 1)] = p0 + (__ffs(m) - 1) * HW;
+            init6_step1<T, true, FULL>(gs, nx, slotof, par, lo_tab, tid, lx, ly, h0, p0, x, y, z0, geo, stb, endb,
+                                       minb, plateau, ex);
+        // the strict minima are roots: list them (their smallest index is taken later)
+        for (unsigned m = minb; m; m &= m - 1) {
+            const int p = p0 + (__ffs(m) - 1) * HW;
+            roots[atomicAdd(counters + CNT_ROOTS, 1)] = p;
+            mi[p] = 0x7fffffff;
+        }
         // number the ends: the thread's ends get consecutive slots after those
         // of the lanes before it (warp scan) and of the warps before it
         int lpre;
@@ -677,9 +728,10 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
         }
         __syncthreads();
         const int slot0 = wbase[ly] + lpre;   // the slot of this thread's first end
-        for (unsigned m = endb; m; m &= m - 1) {
+        for (unsigned m = endb; m; m &= m - 1) {   // an end's entry: its slot, below its lowest neighbour
             const int k = __ffs(m) - 1;
-            slotof[tid + k * C::NT] = (uint16_t)(slot0 + __popc(endb & ((1u << k) - 1u)));
+            uint16_t *e = slotof + tid + k * C::NT;
+            *e = (uint16_t)(*e | (slot0 + __popc(endb & ((1u << k) - 1u))));
         }
 
         // step III inside the tile: pointer doubling.  A value read while its
@@ -718,19 +770,29 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
 #pragma unroll
             for (int k = 0; k < C::TZ; k++) {
                 if (((stb >> (2 * k)) & 3u) == (unsigned)STOUT) continue;
-                code[p0 + k * HW] = slotof[cur[k]];   // cur[k]: the end
+                code[p0 + k * HW] = slotof[cur[k]];   // cur[k]: the end (the top three bits ride along)
             }
+            // each end with the next pixel of its path: the neighbour its arrow
+            // leads to (out of the tile), or itself (a minimum or plateau pixel)
             for (unsigned m = endb; m; m &= m - 1) {
                 const int k = __ffs(m) - 1;
-                ends[fst + slot0 + __popc(endb & ((1u << k) - 1u))] = p0 + k * HW;
+                const int e = p0 + k * HW;
+                const int dn = slotof[tid + k * C::NT] >> 13;
+                const int nxt = ((stb >> (2 * k)) & 3u) == (unsigned)ST0 ? e + go6(dn, geo) : e;
+                ends[fst + slot0 + __popc(endb & ((1u << k) - 1u))] = make_int2(e, nxt);
             }
         }
         if (__syncthreads_or(plateau)) {
-#pragma unroll
+            // a plateau tile: step II starts from dist, and the step II / IV
+            // kernels and k_jump2 work on every pixel's arrow (rare: not unrolled)
+#pragma unroll 1
             for (int k = 0; k < C::TZ; k++) {
                 const unsigned sk = (stb >> (2 * k)) & 3u;
                 if (sk == (unsigned)STOUT) continue;
-                dist[p0 + k * HW] = sk == (unsigned)ST0 ? 0 : (sk == (unsigned)ST1 ? -2 : INF_D);
+                const int p = p0 + k * HW;
+                dist[p] = sk == (unsigned)ST0 ? 0 : (sk == (unsigned)ST1 ? -2 : INF_D);
+                if (!FULL) par[p] = sk == (unsigned)ST0 ? p + go6(slotof[tid + k * C::NT] >> 13, geo) : p;
+                if (sk == (unsigned)STP) mi[p] = 0x7fffffff;   // a root candidate
             }
             if (tid == 0) {
                 plat[t] = 1;
@@ -741,7 +803,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             plat[t] = 0;
         }
         // (the __syncthreads_or above also orders this tile's nx, slotof,
-        // wbase, s_first and go_tab reads before the next tile's writes)
+        // wbase and s_first reads before the next tile's writes)
     }
 }
 
@@ -1022,13 +1084,19 @@ __global__ void __launch_bounds__(NTHR) k_union2(const Batch b, int32_t *par, co
 // k_jump2: step III on plateau tiles (cooperative), lists minimal-plateau roots
 // ---------------------------------------------------------------------------
 
+// 3D 6-connectivity (SPARSE): par holds arrows on plateau tiles only, so a
+// jump stops at a pixel of another tile that is not a plateau tile (its path
+// goes on through the slot codes in k_chase); at the end, every path end of a
+// plateau tile takes its final pointer as the next pixel of its path in ends.
 template <int CONN>
 __global__ void __launch_bounds__(NTHR) k_jump2(const Batch b, int32_t *par, const int32_t *__restrict__ dist,
                                                 const int32_t *__restrict__ tlist, int32_t *counters,
                                                 int32_t *roots, int RR, DevStatus *status, int round_cap,
-                                                unsigned long long timeout_ns)
+                                                unsigned long long timeout_ns, const uint8_t *__restrict__ plat,
+                                                int2 *ends, const int2 *__restrict__ tends)
 {
     using C = TC<CONN>;
+    constexpr bool SPARSE = CONN == 6;
     const int tid = threadIdx.x, lane = tid & 31;
     const int ntl = counters[CNT_TILES];
     for (int r = 0;; r++) {
@@ -1048,6 +1116,11 @@ __global__ void __launch_bounds__(NTHR) k_jump2(const Batch b, int32_t *par, con
                 int l = l0;
                 for (int k = 0; k < RR; k++) {
                     if (!C::D3 && dist[l] <= 0) break;
+                    if (SPARSE) {   // l's arrow is known only on a plateau tile
+                        const int ql = l - tc.base;
+                        const int zl = ql / tc.geo.HW, rl = ql - zl * tc.geo.HW, yl = rl / tc.geo.W;
+                        if (!plat[tc.tile0 + tile_of_c<CONN>(tc.tg, rl - yl * tc.geo.W, yl, zl)]) break;
+                    }
                     const int l2 = __ldcg(par + l);
                     if (l2 == l) break;
                     l = l2;
@@ -1091,6 +1164,14 @@ __global__ void __launch_bounds__(NTHR) k_jump2(const Batch b, int32_t *par, con
             if (lane == 0) rb = atomicAdd(counters + CNT_ROOTS, __popc(bl));
             rb = __shfl_sync(0xffffffffu, rb, 0);
             if (isr) roots[rb + __popc(bl & ((1u << lane) - 1u))] = p;
+        }
+        if (SPARSE) {   // the path ends of the tile continue where their pointers now lead
+            const int2 te = tends[tlist[j]];
+            for (int i = tid; i < te.y; i += NTHR) {
+                int2 c = ends[te.x + i];
+                c.y = __ldcg(par + c.x);
+                ends[te.x + i] = c;
+            }
         }
     }
 }
@@ -1349,44 +1430,45 @@ __device__ __forceinline__ int tile_of_pixel(const Batch &b, int g)
     return d.tile0 + ((z / TT<6>::TZ) * d.nty + y / TT<6>::TY) * d.ntx + x / TT<6>::TX;
 }
 
-// Root of every listed in-tile path end, in place, and the end pixel's par
-// set to it.  From an end e, par[e] is the next pixel q of the path (in a
-// neighbouring tile, or given by step II / IV), and q's own in-tile end is
-// ends[first of q's tile + code[q]] (or, once chased, already its root);
-// repeat until a root (par[r] == r).
-static __global__ void __launch_bounds__(NTHR) k_chase(const Batch b, int32_t *ends, const int2 *__restrict__ tends,
+// Root of every listed in-tile path end, in place.  ends[j] = (e, q): e the
+// end pixel, q the next pixel of its path (in a neighbouring tile, or given
+// by step II / IV on a plateau tile), or q == e for a root.  q's own in-tile
+// end is the entry first-of-q's-tile + code[q]; repeat until a root, then
+// ends[j] = (root, root).  An entry read while another thread rewrites it
+// holds pixels of the same path in either field, so every walk ends at the
+// same root.
+static __global__ void __launch_bounds__(NTHR) k_chase(const Batch b, int2 *ends, const int2 *__restrict__ tends,
                                                        const uint16_t *__restrict__ code, const int32_t *counters,
-                                                       int32_t *par, DevStatus *status)
+                                                       DevStatus *status)
 {
     const int n = counters[CNT_ENDS];
     const int npix = b.npix;
     for (int j = blockIdx.x * NTHR + threadIdx.x; j < n; j += gridDim.x * NTHR) {
-        const int e0 = ends[j];
-        int e = e0;
-        bool ok = (unsigned)e0 < (unsigned)npix;
-        for (int hop = 0; ok; hop++) {
-            const int q = par[e];
-            if (q == e) break;
+        const int2 c0 = ends[j];
+        int e = c0.x, q = c0.y;
+        bool ok = (unsigned)e < (unsigned)npix;
+        for (int hop = 0; ok && q != e; hop++) {
             if ((unsigned)q >= (unsigned)npix || hop >= (1 << 22)) {
                 ok = false;
                 break;
             }
             const int2 te = __ldg(tends + tile_of_pixel(b, q));
-            const int s = __ldg(code + q);
+            const int s = __ldg(code + q) & (TC<6>::NPIX - 1);
             if (s >= te.y) {
                 ok = false;
                 break;
             }
-            e = ends[te.x + s];
+            const int2 c = ends[te.x + s];
+            e = c.x;
+            q = c.y;
             if ((unsigned)e >= (unsigned)npix) ok = false;
         }
         if (!ok) {  // only after an earlier device error
             record_error(status, DEV_NONCONVERGED, 12);
-            ends[j] = 0;
+            ends[j] = make_int2(0, 0);
             continue;
         }
-        ends[j] = e;
-        if (e != e0) par[e0] = e;
+        if (e != c0.x || q != c0.y) ends[j] = make_int2(e, e);
     }
 }
 
@@ -1430,14 +1512,14 @@ template <typename T> struct Rag6Box {
 
 // root of slot c of a neighbouring tile whose span of the end list is e,
 // -1 if invalid
-__device__ __forceinline__ int face_root(bool valid, int c, int2 e, const int32_t *ends, DevStatus *status)
+__device__ __forceinline__ int face_root(bool valid, int c, int2 e, const int2 *ends, DevStatus *status)
 {
     if (!valid) return -1;
     if (c >= e.y) {  // only after an earlier device error
         record_error(status, DEV_NONCONVERGED, 13);
         return -1;
     }
-    return __ldg(ends + e.x + c);
+    return __ldg(&ends[e.x + c].x);
 }
 
 // Per 3D tile, one z column per thread: the smallest pixel index per basin,
@@ -1461,8 +1543,8 @@ template <typename T, bool TMA>
 __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ CUtensorMap tmc,
                                                        const __grid_constant__ CUtensorMap tmg, const Batch b,
                                                        const uint16_t *__restrict__ code,
-                                                       const int32_t *__restrict__ ends,
-                                                       const int2 *__restrict__ tends, int32_t *par, int32_t *mi,
+                                                       const int2 *__restrict__ ends,
+                                                       const int2 *__restrict__ tends, int32_t *mi,
                                                        int do_rag, unsigned long long *keys, uint32_t *vals,
                                                        int32_t *slots, int32_t *ecount, unsigned long long gmask,
                                                        DevStatus *status)
@@ -1563,7 +1645,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
     // of it goes before the wait.  The thread's first slot root stays in a
     // register for the ids below.
     const bool hasx = x0 + C::TX < geo.W, hasy = y0 + C::TY < geo.H, hasz = z0 + C::TZ < geo.D;
-    const int rown = tid < te.y ? __ldg(ends + te.x + tid) : -1;
+    const int rown = tid < te.y ? __ldg(&ends[te.x + tid].x) : -1;
     int fzr = -1, fyr = -1, fxr = -1;   // roots of the face pixels (lane, ly, TZ), (lane, TY, ly), (TX, fy, fz)
     if (do_rag) {
         const int fy = tid % C::TY, fz = tid / C::TY;
@@ -1572,15 +1654,16 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
         const int2 tez = vz ? __ldg(tends + t + ntx * nty) : make_int2(0, 0);
         const int2 tey = vy ? __ldg(tends + t + ntx) : make_int2(0, 0);
         const int2 tex = vx ? __ldg(tends + t + 1) : make_int2(0, 0);
-        const int cz = vz ? __ldg(code + base + ((z0 + C::TZ) * geo.H + y) * geo.W + x) : 0;
-        const int cy = vy ? __ldg(code + base + ((z0 + ly) * geo.H + y0 + C::TY) * geo.W + x) : 0;
-        const int cx = vx ? __ldg(code + base + ((z0 + fz) * geo.H + y0 + fy) * geo.W + x0 + C::TX) : 0;
+        constexpr int CM = C::NPIX - 1;   // slot bits of a code
+        const int cz = vz ? __ldg(code + base + ((z0 + C::TZ) * geo.H + y) * geo.W + x) & CM : 0;
+        const int cy = vy ? __ldg(code + base + ((z0 + ly) * geo.H + y0 + C::TY) * geo.W + x) & CM : 0;
+        const int cx = vx ? __ldg(code + base + ((z0 + fz) * geo.H + y0 + fy) * geo.W + x0 + C::TX) & CM : 0;
         fzr = face_root(vz, cz, tez, ends, status);
         fyr = face_root(vy, cy, tey, ends, status);
         fxr = face_root(vx, cx, tex, ends, status);
     }
     rh_insert(rown);
-    for (int i = tid + C::NT; i < te.y; i += C::NT) rh_insert(__ldg(ends + te.x + i));
+    for (int i = tid + C::NT; i < te.y; i += C::NT) rh_insert(__ldg(&ends[te.x + i].x));
     rh_insert(fzr);
     rh_insert(fyr);
     rh_insert(fxr);
@@ -1628,7 +1711,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
     }
     if (mode < 2) {
         if (tid < te.y) ss[tid] = (uint8_t)rh_find(rown);
-        for (int i = tid + C::NT; i < te.y; i += C::NT) ss[i] = (uint8_t)rh_find(__ldg(ends + te.x + i));
+        for (int i = tid + C::NT; i < te.y; i += C::NT) ss[i] = (uint8_t)rh_find(__ldg(&ends[te.x + i].x));
         if (do_rag) {   // ids of the forward faces
             const int iz = rh_find(hzr[tid]);
             hzr[tid] = iz;
@@ -1760,7 +1843,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
         // more than RB basins in the tile: per-pixel loop over roots read from
         // the global end list
         auto root_at = [&](bool valid, int c) -> int {
-            return valid ? __ldg(ends + first + (c & (C::NPIX - 1))) : -1;
+            return valid ? __ldg(&ends[first + (c & (C::NPIX - 1))].x) : -1;
         };
         const bool vy = y + 1 < geo.H;
         int pid = -1;
@@ -1951,7 +2034,7 @@ static __global__ void __launch_bounds__(NTHR) k_write_batch(const Batch b, cons
 static constexpr int kWrite6Tab = 12288;   // level ids held in shared memory per tile
 
 static __global__ void __launch_bounds__(TT<6>::NT, 3) k_write6(const Batch b, const uint16_t *__restrict__ code,
-                                                             const int32_t *__restrict__ ends,
+                                                             const int2 *__restrict__ ends,
                                                              const int2 *__restrict__ tends,
                                                              const int32_t *__restrict__ idmap,
                                                              const int32_t *__restrict__ gmap, size_t kstride,
@@ -1997,7 +2080,7 @@ static __global__ void __launch_bounds__(TT<6>::NT, 3) k_write6(const Batch b, c
     const int n = te.y;
     const bool tab = n * NL <= kWrite6Tab;
     auto level_of = [&](int s, int k) -> int {   // level-k id of slot s's basin
-        const int c = safe_id(idmap, ends[te.x + s], K0);
+        const int c = safe_id(idmap, ends[te.x + s].x, K0);
         if (c < 0) return -1;
         if (k == 0) return c - rb;
         const int32_t *gm = gmap + (size_t)(k - 1) * kstride;
@@ -2005,7 +2088,7 @@ static __global__ void __launch_bounds__(TT<6>::NT, 3) k_write6(const Batch b, c
     };
     if (tab) {
         for (int s = tid; s < n; s += C::NT) {
-            const int c = safe_id(idmap, ends[te.x + s], K0);
+            const int c = safe_id(idmap, ends[te.x + s].x, K0);
             lv[s] = c >= 0 ? c - rb : -1;
             for (int k = 1; k < NL; k++) {
                 const int32_t *gm = gmap + (size_t)(k - 1) * kstride;

@@ -224,3 +224,36 @@ def request_stream(rate_hz: float, duration_s: float, seed: int, frac_3d: float 
             out.append(dict(t=float(t[i]), kind="2d", shape=(int(s2[1][i]), int(s2[0][i])),
                             seed=seed * 100003 + i))
     return out
+
+
+# --------------------------------------------------------------------------
+# the batch (config 3) and the request stream (config 4): crops of one large
+# 2D blob image and of one 3D distance volume
+# --------------------------------------------------------------------------
+
+CROP_SIDE = 4096                   # the 2D image the batch and the requests are cut from
+CROP_BLOBS = 8192                  # 32 blobs per 256^2, the small-image density
+BATCH_POOL_SEED = BASE_SEED + 3    # the batch's 4096^2 image
+BATCH_SHAPE_SEED = BASE_SEED + 5   # the batch's crop sides and offsets
+SERVE_SEED = BASE_SEED + 6         # the request stream, its 2D image and its 3D volume
+SERVE_VOLUME_SIDE = 256
+SERVE_VOLUME_SEEDS = 1050          # 50,000 seeds scaled by volume from 928^3 to 256^3
+
+
+def crop_pool_image(seed: int) -> np.ndarray:
+    """The CROP_SIDE^2 uint8 blob image that 2D batch images and requests are
+    cut from (its gradient, rather: callers crop the gradient)."""
+    return blob_image(CROP_SIDE, CROP_SIDE, CROP_BLOBS, seed)
+
+
+def batch_windows(n: int, seed: int = BATCH_SHAPE_SEED, lo: int = 64, hi: int = 2048):
+    """n crop windows (y, x, h, w) of the CROP_SIDE^2 image: sides
+    independently log-uniform in [lo, hi], offsets uniform in [0, CROP_SIDE - hi]."""
+    shapes = batch_shapes(n, lo, hi, seed)
+    offs = integers(seed, 41, 2 * n, 0, CROP_SIDE - hi)
+    return [(int(offs[2 * i]), int(offs[2 * i + 1]), h, w) for i, (h, w) in enumerate(shapes)]
+
+
+def request_window_2d(i: int, h: int, w: int):
+    """Crop origin (y, x) of 2D request i (h x w) in the CROP_SIDE^2 image."""
+    return (i * 7919) % (CROP_SIDE + 1 - h), (i * 104729) % (CROP_SIDE + 1 - w)

@@ -2,10 +2,11 @@
 bounded; when a bound runs out the kernel records an error in the context's
 status word and returns, and ws_context_check reports it.  These tests make
 bounds run out on purpose through ws_tuning -- a step II round cap, a pointer
-jumping round cap, a region table too small for the image -- check the status
-the host reads, and then check that the same context computes the same input
-correctly once the tuning is back to its defaults (the context stays usable;
-nothing traps, faults or hangs)."""
+jumping round cap, a region table too small for the image, a device-wide
+barrier whose wait runs out because one block withholds its arrival -- check
+the status the host reads, and then check that the same context computes the
+same input correctly once the tuning is back to its defaults (the context
+stays usable; nothing traps, faults or hangs)."""
 import numpy as np
 import pytest
 
@@ -99,3 +100,65 @@ def test_region_table_full():
         _parity(fresh, g, 4, 3)
     finally:
         fresh.close()
+
+
+def _plateau_image():
+    g = np.full((40, 600), 9, dtype=np.uint8)
+    g[:, 0] = 3
+    g[:, 1:] = 7
+    g[5:35, 20:580] = 7
+    g[0, :] = 9
+    g[-1, :] = 9
+    return g
+
+
+@pytest.mark.parametrize("kind", ["segment2d", "segment3d", "waterfall"])
+def test_barrier_timeout(ctx, kind):
+    """A device-wide barrier wait that runs out.  With ws_tuning's one-shot
+    barrier_withhold armed, block 0 of the next cooperative kernel (the step II
+    relaxation of a segmentation; the level kernel of a waterfall over given
+    labels) does not arrive at its first barrier, so the other blocks' waits
+    run out after barrier_timeout_ms = 1: the call ends within a fraction of
+    the default 4 s limit, ws_context_check reports WS_ERR_TIMEOUT, and the
+    same context then computes the same input correctly."""
+    import time
+    from paper_2410_08946_gb300 import binding
+    if kind == "segment3d":
+        g, conn = synth.distance_volume(40, 48, 96, 30, seed=77), 6
+    else:
+        g, conn = _plateau_image(), 4
+    g_d = torch.from_numpy(g).cuda()
+    if kind == "waterfall":
+        l0 = torch.from_numpy(oracle.watershed(g, conn)[0]).cuda()
+        run = lambda: ctx.waterfall(l0, g_d, conn, 4)   # noqa: E731
+    else:
+        run = lambda: ctx.segment(g_d, conn, 3)          # noqa: E731
+    run()            # workspace allocated, nothing armed
+    ctx.check()
+    ctx.set_tuning(barrier_timeout_ms=1, barrier_withhold=1)
+    t0 = time.perf_counter()
+    _expect(ctx, binding.WS_ERR_TIMEOUT, run)
+    assert time.perf_counter() - t0 < 2.0, "a barrier wait did not end at its limit"
+    ctx.set_tuning()
+    if kind == "waterfall":
+        ref_l, ref_c = oracle.waterfall(l0.cpu().numpy(), g, conn, 4)
+        lv, c = ctx.waterfall(l0, g_d, conn, 4)
+        ctx.check()
+        assert c.cpu().tolist() == ref_c.tolist()
+        assert np.array_equal(lv.cpu().numpy(), ref_l)
+    else:
+        _parity(ctx, g, conn, 3)
+
+
+def test_barrier_withhold_is_one_shot(ctx):
+    """The hold goes to one launch only: the next call on the context, with
+    the same tuning left in place, completes without error."""
+    from paper_2410_08946_gb300 import binding
+    g = _plateau_image()
+    g_d = torch.from_numpy(g).cuda()
+    ctx.set_tuning(barrier_timeout_ms=50, barrier_withhold=1)
+    _expect(ctx, binding.WS_ERR_TIMEOUT, lambda: ctx.segment(g_d, 4, 3))
+    _parity(ctx, g, 4, 3)
+    with pytest.raises(binding.WsError):
+        ctx.set_tuning(barrier_withhold=2)
+    ctx.set_tuning()

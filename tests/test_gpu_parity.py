@@ -74,6 +74,47 @@ def test_step1_3d(ctx, shape, levels):
     assert np.array_equal(host(l_d), L)
 
 
+# Step I runs in the segmentation path's own tiled kernels (k_init for 2D and
+# 26-connectivity, k_init6 for 6-connectivity).  The shapes below give tiles
+# whose halo lies inside the image (the branch-free interior code) beside
+# border tiles, with rows that are 16-byte multiples (the gradient staged by
+# TMA) and rows that are not (plain loads).
+STEP1_TILES = [
+    ((200, 256), 4, np.uint8, 3),      # 2D TMA (256 B rows), interior tiles
+    ((200, 256), 8, np.uint16, 5),     # 2D TMA (512 B rows)
+    ((130, 203), 4, np.uint8, 3),      # 2D plain loads (203 B rows)
+    ((130, 203), 8, np.uint16, 256),
+    ((50, 50, 96), 6, np.uint16, 4),   # 3D TMA (192 B rows), interior tiles
+    ((50, 50, 96), 6, np.uint8, 2),    # 3D TMA (96 B rows)
+    ((40, 40, 97), 6, np.uint16, 3),   # 3D plain loads
+    ((40, 36, 96), 26, np.uint16, 3),  # 3D 26-connectivity, TMA
+    ((20, 19, 37), 26, np.uint8, 2),   # 3D 26-connectivity, plain loads
+]
+
+
+@pytest.mark.parametrize("shape,conn,dtype,levels", STEP1_TILES)
+def test_step1_tiled_kernels(ctx, shape, conn, dtype, levels):
+    rng = np.random.default_rng(sum(shape) * conn + levels)
+    img = rand_img(rng, shape, levels, dtype)
+    S, L = oracle.step1(img, conn)
+    s_d, l_d = ctx.step1(dev(img), conn)
+    ctx.check()
+    assert np.array_equal(host(s_d), S)
+    assert np.array_equal(host(l_d), L)
+
+
+def test_step1_distance_volume(ctx):
+    """Step I of a distance-field volume (the benchmark's kind of input) with
+    interior tiles on both staging paths."""
+    for shape in ((48, 64, 128), (33, 47, 99)):
+        vol = synth.distance_volume(*shape, 40, seed=sum(shape))
+        S, L = oracle.step1(vol, 6)
+        s_d, l_d = ctx.step1(dev(vol), 6)
+        ctx.check()
+        assert np.array_equal(host(s_d), S)
+        assert np.array_equal(host(l_d), L)
+
+
 # --------------------------------------------------------------------------
 # step II distances
 # --------------------------------------------------------------------------
