@@ -468,8 +468,59 @@ def run_batch(ctx, binding, torch, n=512, NL=6, conn=4, reps=3):
             "batched_graph_ms": ms_graph, "batched_gvox_s": npx / ms_graph / 1e6,
             "per_image_ms": ms_single, "per_image_gvox_s": npx / ms_single / 1e6,
             "speedup": ms_single / ms_graph, "identical": bool(same), "phases_ms_eager": phases,
-            "autotune": {"params": tuned["params"], "eager_ms": tuned["ms"], "eager_ms_defaults": default_ms,
+            "autotune": {"params": tuned["params"], "tile_shape": autotune.SHAPES[tuned["params"]["tile_shape"]],
+                         "eager_ms": tuned["ms"], "eager_ms_defaults": default_ms,
                          "candidates": len(tuned["table"])}}
+
+
+def run_batch_only(n=512, NL=6, conn=4, reps=5, cache_path=None):
+    """The batch alone: tuned, recorded as a CUDA graph, replayed `reps` times
+    between CUDA events, then replayed once more.  Prints the replay time and
+    the kernels one replay launches, so that a launch list of this command's
+    last replay (ncu) gives the kernels' own device time beside the replay's.
+    With cache_path the tuning is read from (or stored in) that JSON file, so
+    that a profiled run replays the configuration a plain run chose."""
+    import torch
+    from paper_2410_08946_gb300 import autotune, binding, synth
+    binding.load()
+    ctx = binding.Context(0)
+    img = torch.from_numpy(synth.crop_pool_image(synth.BATCH_POOL_SEED)).cuda()
+    pool = ctx.gradient(img)
+    grads = [pool[y:y + h, x:x + w].contiguous() for y, x, h, w in synth.batch_windows(n)]
+    npx = sum(g.numel() for g in grads)
+    outs = [(torch.empty((NL,) + tuple(g.shape), dtype=torch.int32, device="cuda"),
+             torch.empty(NL, dtype=torch.int32, device="cuda")) for g in grads]
+    tuned = autotune.autotune(ctx, lambda: ctx.segment_batch(grads, conn, NL, [o[0] for o in outs],
+                                                             [o[1] for o in outs]),
+                              key=f"batch2d|u8|conn{conn}|NL{NL}|{autotune.size_bucket(npx)}", reps=3,
+                              cache_path=cache_path)
+    graph = ctx.graph(grads, conn, NL)
+    ctx.check()
+    for _ in range(3):
+        graph.launch()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(reps):
+        e0.record(stream)
+        graph.launch()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    before = ctx.launches()
+    ctx.segment_batch(grads, conn, NL, [o[0] for o in outs], [o[1] for o in outs])
+    per_call = ctx.launches() - before
+    torch.cuda.synchronize()
+    graph.launch()   # the replay a launch list of this command ends with
+    torch.cuda.synchronize()
+    ctx.check()
+    graph.close()
+    print(json.dumps({"workload": f"{n} 2D uint8 crops, {npx} px, 4-connectivity, NL={NL}",
+                      "graph_replay_ms": statistics.median(ts), "graph_replay_ms_all": ts,
+                      "kernels_per_replay": per_call, "autotune": tuned["params"]}), flush=True)
+    ctx.close()
+    return 0
 
 
 def run_serve(ctx, binding, torch, seconds=10.0, rate=200.0, NL=4, budget=40 << 30, lanes=4):
@@ -586,12 +637,17 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--ingest-ncu", metavar="CSV", help="write profiles/traffic.json from an ncu DRAM capture "
                     "(dram__bytes_read.sum, dram__bytes_write.sum) of a --side S run, then exit")
+    ap.add_argument("--batch-only", action="store_true", help="only the 512-image batch as a CUDA-graph replay "
+                    "(tuned, then timed), ending with one more replay: for a launch list of one replay")
+    ap.add_argument("--tune-cache", metavar="JSON", help="with --batch-only: read or store the batch's tuning here")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.ingest_ncu:
         ingest_ncu(args.ingest_ncu, args.side ** 3)
         return 0
+    if args.batch_only:
+        return run_batch_only(cache_path=args.tune_cache)
     if args.impl == "reference":
         return run_reference(args)
 

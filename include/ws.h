@@ -90,6 +90,12 @@ typedef struct {
                                     run out after barrier_timeout_ms; the call then reports
                                     WS_ERR_TIMEOUT through ws_context_check.  Nothing faults or hangs,
                                     and the hold is disarmed once it has been handed to a launch. */
+    int32_t tile_shape;          /* 2D uint8 images: tile shape and threads per tile of the tiled kernels:
+                                    0 = 64 x 32 pixels / 256 threads (default), 1 = 32 x 32 / 256,
+                                    2 = 128 x 16 / 256, 3 = 64 x 32 / 512.  Other images use their
+                                    fixed shape (2D uint16: 64 x 32 / 256; 3D: 32 x 16 x 16 / 512).
+                                    No shape changes a result. */
+    int32_t pad_;                /* reserved, 0 */
 } ws_tuning;
 
 /* ------------------------------------------------------------------------ */

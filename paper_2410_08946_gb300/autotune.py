@@ -1,11 +1,12 @@
 """Autotuner of libws's runtime parameters for one workload.
 
 The paper fixes its launch parameters by a study on its own GPUs (Sec. 5:
-thread blocks of 16x16 / 8x8x8, RR = 6 jumps per round).  Here the tile shapes
-are compile-time constants of the kernels, and the parameters that remain free
-at run time -- none of which changes a result, only the time -- are picked per
-workload by measurement:
+thread blocks of 16x16 / 8x8x8, RR = 6 jumps per round).  Here they are picked
+per workload by measurement; none of them changes a result, only the time:
 
+  tile_shape           tile shape and threads per tile of the tiled kernels
+                       for 2D uint8 images (the library compiles four:
+                       SHAPES below; other images have one fixed shape)
   jumps_per_round      pointer hops per pixel per round of step III (RR)
   levels_ctas_per_sm   CTAs per SM of the cooperative waterfall-level kernel
 
@@ -21,8 +22,12 @@ from __future__ import annotations
 import json
 import os
 
-SPACE = {"jumps_per_round": [2, 4, 6, 8, 12, 16], "levels_ctas_per_sm": [2, 4, 8]}
-DEFAULTS = {"jumps_per_round": 6, "levels_ctas_per_sm": 4}
+SHAPES = {0: "64x32 px / 256 threads", 1: "32x32 px / 256 threads", 2: "128x16 px / 256 threads",
+          3: "64x32 px / 512 threads"}
+SPACE = {"tile_shape": [0, 1, 2, 3], "jumps_per_round": [2, 4, 6, 8, 12, 16], "levels_ctas_per_sm": [2, 4, 8]}
+DEFAULTS = {"tile_shape": 0, "jumps_per_round": 6, "levels_ctas_per_sm": 4}
+# the space for workloads without a choice of tile shape (3D, uint16)
+SPACE_FIXED_SHAPE = {k: v for k, v in SPACE.items() if k != "tile_shape"}
 
 
 def size_bucket(n_pixels: int) -> str:

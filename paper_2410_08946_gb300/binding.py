@@ -48,7 +48,7 @@ class ws_tuning(ctypes.Structure):
     _fields_ = [("plateau_round_cap", ctypes.c_int32), ("jump_round_cap", ctypes.c_int32),
                 ("jumps_per_round", ctypes.c_int32), ("barrier_timeout_ms", ctypes.c_int32),
                 ("edge_capacity", ctypes.c_int64), ("levels_ctas_per_sm", ctypes.c_int32),
-                ("barrier_withhold", ctypes.c_int32)]
+                ("barrier_withhold", ctypes.c_int32), ("tile_shape", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 _lib = None

@@ -418,6 +418,13 @@ const Launchers *launchers(int dtype, int conn)
     return nullptr;
 }
 
+const Launchers *launchers_for(const ws_context *c, int dtype, int conn)
+{
+    if (dtype == WS_U8 && (conn == 4 || conn == 8) && c->tun.tile_shape > 0)
+        return launchers_u8_shape(conn, c->tun.tile_shape);
+    return launchers(dtype, conn);
+}
+
 }  // namespace ws
 
 // ---------------------------------------------------------------------------
@@ -464,7 +471,7 @@ static ws_status prep(ws_context *c, const void *grad, int dtype, const ws_shape
         cudaError_t e = cudaSetDevice(c->device);
         if (e != cudaSuccess) return set_cuda_error(c, e, "cudaSetDevice");
     }
-    *L = launchers(dtype, conn);
+    *L = launchers_for(c, dtype, conn);
     if (!*L) return set_error(c, WS_ERR_UNSUPPORTED, "no pipeline for this dtype / connectivity");
     return WS_OK;
 }
@@ -622,6 +629,7 @@ ws_status ws_context_set_tuning(ws_context *c, const ws_tuning *t)
     if (t->levels_ctas_per_sm > 32) return set_error(c, WS_ERR_INVALID, "levels_ctas_per_sm must be <= 32");
     if (t->barrier_withhold != 0 && t->barrier_withhold != 1)
         return set_error(c, WS_ERR_INVALID, "barrier_withhold must be 0 or 1");
+    if (t->tile_shape < 0 || t->tile_shape > 3) return set_error(c, WS_ERR_INVALID, "tile_shape must be in 0..3");
     c->tun = *t;
     c->hold_armed = t->barrier_withhold;
     c->tun.barrier_withhold = 0;
@@ -834,7 +842,7 @@ static ws_status prep_batch(ws_context *c, int n, const ws_item *items, ws_dtype
     if (st) return st;
     if (dtype != WS_U8 && dtype != WS_U16) return set_error(c, WS_ERR_INVALID, "dtype must be WS_U8 or WS_U16");
     cudaSetDevice(c->device);
-    *L = launchers(dtype, conn);
+    *L = launchers_for(c, dtype, conn);
     if (!*L) return set_error(c, WS_ERR_UNSUPPORTED, "no pipeline for this dtype / connectivity");
     return WS_OK;
 }

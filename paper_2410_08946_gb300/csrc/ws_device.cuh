@@ -107,7 +107,10 @@ struct Geo {
 
 // Neighbour offsets in ascending linear-index order (dz, then dy, then dx),
 // which is the order Eq. 1's tie-break ("the largest index") refers to.
-template <int CONN> struct Nb;
+// A 2D pipeline may run on one of several tile shapes: the template value
+// CONN + 100 * shape names connectivity CONN on tile shape `shape`
+// (ws_tuning.tile_shape), with the neighbourhood of CONN % 100.
+template <int CONN> struct Nb : Nb<CONN % 100> {};
 
 template <> struct Nb<4> {
     static constexpr int n = 4;
@@ -146,7 +149,7 @@ template <> struct Nb<26> {
 };
 
 template <int CONN> struct Dim {
-    static constexpr int nd = (CONN == 4 || CONN == 8) ? 2 : 3;
+    static constexpr int nd = (CONN % 100 == 4 || CONN % 100 == 8) ? 2 : 3;
 };
 
 // Forward half of the neighbourhood: offsets whose linear index delta is

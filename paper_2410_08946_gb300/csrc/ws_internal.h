@@ -211,12 +211,16 @@ struct Launchers {
                              cudaStream_t);
 };
 
-// dtype: 0 = u8, 1 = u16; conn: 4, 8, 6.  Returns nullptr when unsupported.
+// dtype: 0 = u8, 1 = u16; conn: 4, 8, 6, 26.  Returns nullptr when unsupported.
 const Launchers *launchers(int dtype, int conn);
+// The same for a context: 2D uint8 images take the tile shape of its tuning.
+const Launchers *launchers_for(const ws_context *c, int dtype, int conn);
 
 // Instantiation entry points (one per translation unit).
 const Launchers *launchers_u8(int conn);
 const Launchers *launchers_u16(int conn);
+// 2D uint8 on tile shape 1..3 (ws_tuning.tile_shape); nullptr otherwise.
+const Launchers *launchers_u8_shape(int conn, int shape);
 
 // K0 = max(labels) + 1 into c->w.kcount (ws_gradient.cu).
 ws_status launch_count_labels(ws_context *c, const int32_t *labels, int N, cudaStream_t s);

@@ -16,8 +16,14 @@
 //   k_rag            Alg. 5 step V on pixel pairs of a caller's labelling:
 //                    pass(A,B) = min over adjacent pixels of max(G(p), G(q)),
 //                    warp-deduplicated into the region table
+//   EdgeSink, sink_put1 / sink_put_warp
+//                    where the segmentation path's adjacency kernels put
+//                    their pairs of basins: an appended list (2D) or the
+//                    region table (3D)
 //   k_edges_compact  region table -> dense edge list in canonical level-0 ids
 //                    (and the table emptied)
+//   k_edges_ids      the segmentation path's edge list -> canonical level-0
+//                    ids, in place
 //   k_levels         NL-1 rounds of lowest-pass merging on the region graph
 //                    (newmin, Union over kept edges, canonical ids, the next
 //                    level's id per region, contracted edges); cooperative
@@ -210,6 +216,34 @@ static __global__ void k_copy_int(const int32_t *src, int32_t *dst)
 // waterfall: region adjacency (Alg. 5 step V on pixel pairs)
 // ---------------------------------------------------------------------------
 
+// One edge of the region graph: regions a < b and their pass value.
+struct Edge {
+    int a, b;
+    unsigned h;
+};
+
+// Where the segmentation path's adjacency kernels put their pairs of basins
+// (a < b, root pixels) with the lowest pass each one saw:
+//   - a list (hashed == 0): records appended at e[*n], a pair found by several
+//     tiles once per tile.  The waterfall needs no more (its merge rule reads a
+//     pair's minimum over all its records), and appends cost far less than
+//     the table's atomics; 2D images, whose small basins rarely meet across
+//     tiles, take it.  A record past cap is dropped and reported as a full
+//     table.
+//   - the region table (hashed != 0): one record per pair; 3D volumes, whose
+//     large basins meet across many tiles, take it.
+struct EdgeSink {
+    Edge *e;
+    int32_t *n;
+    int cap;
+    unsigned long long *keys;
+    uint32_t *vals;
+    int32_t *slots;
+    int32_t *ecount;
+    unsigned long long gmask;
+    int hashed;
+};
+
 static __device__ __forceinline__ unsigned long long mix64(unsigned long long k)
 {
     k ^= k >> 33;
@@ -270,6 +304,49 @@ static __device__ __forceinline__ void append_slots(int s, int32_t *slots, int32
     if (lane == 0) base = atomicAdd(ecount, __popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (s >= 0) slots[base + __popc(m & ((1u << lane) - 1u))] = s;
+}
+
+static __device__ __forceinline__ void list_put(const EdgeSink &S, int i, unsigned a, unsigned b, unsigned h,
+                                                DevStatus *status)
+{
+    if (i >= S.cap) {
+        record_error(status, DEV_EDGE_TABLE_FULL, 14);
+        return;
+    }
+    int *q = reinterpret_cast<int *>(S.e + i);
+    q[0] = (int)a;
+    q[1] = (int)b;
+    q[2] = (int)h;
+}
+
+// One pair from any thread.
+static __device__ __forceinline__ void sink_put1(const EdgeSink &S, unsigned a, unsigned b, unsigned h,
+                                                 DevStatus *status)
+{
+    if (S.hashed)
+        edge_insert(((unsigned long long)a << 32) | b, h, S.keys, S.vals, S.slots, S.ecount, S.gmask, status);
+    else
+        list_put(S, atomicAdd(S.n, 1), a, b, h, status);
+}
+
+// The pairs of the lanes with have == true; every lane of the warp calls it
+// (one counter atomic per warp).
+static __device__ __forceinline__ void sink_put_warp(const EdgeSink &S, bool have, unsigned a, unsigned b,
+                                                     unsigned h, DevStatus *status)
+{
+    if (S.hashed) {
+        const int sl = have ? edge_insert_slot(((unsigned long long)a << 32) | b, h, S.keys, S.vals, S.gmask, status)
+                            : -1;
+        append_slots(sl, S.slots, S.ecount);
+        return;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, have);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(S.n, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (have) list_put(S, base + __popc(m & ((1u << lane) - 1u)), a, b, h, status);
 }
 
 template <typename T, int CONN>
@@ -388,12 +465,6 @@ static __device__ __forceinline__ int block_sum(int v, int *red)
     return s;
 }
 
-// One edge of the region graph: regions a < b and their pass value.
-struct Edge {
-    int a, b;
-    unsigned h;
-};
-
 // Edge lists are rewritten between levels by other CTAs: read them from L2.
 __device__ __forceinline__ Edge ld_edge(const Edge *p)
 {
@@ -439,6 +510,35 @@ static __global__ void __launch_bounds__(NTHR) k_edges_compact(unsigned long lon
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) status->edges = E;
     (void)lcnt;
+}
+
+// The segmentation path's edge list (lcnt[0] records, at most cap kept) ->
+// the level-0 edge list in canonical ids, in place; lcnt[0] clamped to cap
+// and lcnt[1..nl-1] cleared for k_levels.
+static __global__ void __launch_bounds__(NTHR) k_edges_ids(Edge *edges, int32_t *lcnt, int nl, int cap,
+                                                           const int32_t *__restrict__ idmap, int npix,
+                                                           const int32_t *__restrict__ k0_ptr, DevStatus *status)
+{
+    const int E = min(*(volatile int32_t *)lcnt, cap);
+    const int K0 = *k0_ptr;
+    for (int e = blockIdx.x * NTHR + threadIdx.x; e < E; e += gridDim.x * NTHR) {
+        int *q = reinterpret_cast<int *>(edges + e);
+        const int ra = q[0], rb = q[1];
+        const int a = (unsigned)ra < (unsigned)npix ? idmap[ra] : -1;
+        const int b = (unsigned)rb < (unsigned)npix ? idmap[rb] : -1;
+        if ((unsigned)a < (unsigned)K0 && (unsigned)b < (unsigned)K0) {
+            q[0] = a < b ? a : b;
+            q[1] = a < b ? b : a;
+        } else {  // only after an earlier device error: a self-loop is ignored
+            q[0] = q[1] = 0;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        for (int k = 1 + threadIdx.x; k < nl; k += 32) lcnt[k] = 0;
+        if (threadIdx.x == 0) status->edges = E;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0 && E < *(volatile int32_t *)lcnt) lcnt[0] = E;   // records dropped
 }
 
 static __global__ void k_edges_reset(int32_t *ecount, int32_t *lcnt, int nl)

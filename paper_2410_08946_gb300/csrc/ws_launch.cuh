@@ -191,7 +191,21 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
         // distinct adjacent basin pairs: about 3 K0 <= 1.5 N for a fragmented 2D
         // image; slots for a load factor <= 1/2 (capped at 2^28 slots)
         if ((st = ensure_edges(c, edge_slots((size_t)b.npix, CONN, c), s)) != WS_OK) return st;
+        if ((e = cudaMemsetAsync(w.ecnt, 0, 4, s)) != cudaSuccess) return set_cuda_error(c, e, "memset");
     }
+    // the adjacency kernels put their pairs of basins here: 2D images append
+    // them to a list (k_edges_ids turns it into the level-0 edge list), 3D
+    // volumes insert them into the region table (k_edges_compact)
+    EdgeSink elist{};
+    elist.e = (Edge *)w.ea;
+    elist.n = w.ecnt;
+    elist.cap = (int)w.edge_cap;
+    elist.keys = w.keys;
+    elist.vals = w.vals;
+    elist.slots = w.slots;
+    elist.ecount = w.ecount;
+    elist.gmask = w.edge_cap ? w.edge_cap - 1 : 0;
+    elist.hashed = TC<CONN>::D3 ? 1 : 0;
     if constexpr (CONN == 6) {  // 3D: roots of the tiles' path ends
         PhaseScope pc(c, PH_CHASE, s);
         k_chase<<<c->num_sms * 8, NTHR, 0, s>>>(b, w.ends, w.tends, w.code, w.counters, c->status);
@@ -203,7 +217,6 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
         CUtensorMap tmp, tmg;
         const bool tma = !b.d && make_tmap_3d(&tmp, w.par, 4, b.one.W, b.one.H, b.one.D, B::RWP, C::BY, C::BZ) &&
                          make_tmap_3d(&tmg, b.one.grad, sizeof(T), b.one.W, b.one.H, b.one.D, B::RWG, C::BY, C::BZ);
-        const unsigned long long gmask = w.edge_cap ? w.edge_cap - 1 : 0;
         if constexpr (CONN == 6) {
             // 3D: the per-pixel pass over slot codes (roots known from k_chase)
             using B6 = Rag6Box<T>;
@@ -218,20 +231,19 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
             }
             auto kern = tma6 ? k_rag6<T, true> : k_rag6<T, false>;
             if ((e = allow_smem(kern, B6::SMEM)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
-            kern<<<b.ntiles, C::NT, B6::SMEM, s>>>(tmc, tmg, b, w.code, w.ends, w.tends, w.aux, do_rag ? 1 : 0,
-                                                   w.keys, w.vals, w.slots, w.ecount, gmask, c->status);
+            kern<<<b.ntiles, C::NT, B6::SMEM, s>>>(tmc, tmg, b, w.code, w.ends, w.tends, w.aux, do_rag ? 1 : 0, elist,
+                                                   c->status);
         } else if (tma) {
             if ((e = allow_smem(k_label<T, CONN, true>, B::SMEM)) != cudaSuccess)
                 return set_cuda_error(c, e, "smem attribute");
-            k_label<T, CONN, true><<<b.ntiles, C::NT, B::SMEM, s>>>(tmp, tmg, b, w.par, w.aux, do_rag ? 1 : 0, w.keys,
-                                                                    w.vals, w.slots, w.ecount, gmask, c->status);
+            k_label<T, CONN, true><<<b.ntiles, C::NT, B::SMEM, s>>>(tmp, tmg, b, w.par, w.aux, do_rag ? 1 : 0, elist,
+                                                                    c->status);
         } else {
             memset(&tmp, 0, sizeof tmp);
             memset(&tmg, 0, sizeof tmg);
             if ((e = allow_smem(k_label<T, CONN, false>, B::SMEM)) != cudaSuccess)
                 return set_cuda_error(c, e, "smem attribute");
-            k_label<T, CONN, false><<<b.ntiles, C::NT, B::SMEM, s>>>(tmp, tmg, b, w.par, w.aux, do_rag ? 1 : 0,
-                                                                     w.keys, w.vals, w.slots, w.ecount, gmask,
+            k_label<T, CONN, false><<<b.ntiles, C::NT, B::SMEM, s>>>(tmp, tmg, b, w.par, w.aux, do_rag ? 1 : 0, elist,
                                                                      c->status);
         }
         c->launches += 1;
@@ -313,22 +325,31 @@ static inline ws_status run_write(ws_context *c, const Geo &geo, int NL, int32_t
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "write launch");
 }
 
-// Region-graph merging for levels 1..NL-1 over the filled region table:
-// the table becomes a dense edge list in canonical level-0 ids (idmap maps
-// its keys to ids; nullptr: the keys are ids), the table is emptied for the
-// next call, then the cooperative k_levels contracts the list level by level.
+// Region-graph merging for levels 1..NL-1: the cooperative k_levels
+// contracts the level-0 edge list level by level.  The level-0 list comes
+// from the edge list a 2D segmentation appended (list_npix > 0: its records,
+// keyed by root pixels below list_npix, mapped to canonical ids through idmap
+// in place) or from the filled region table (list_npix == 0: the table
+// becomes the list, idmap maps its keys to ids or is nullptr when the keys are
+// ids, and the table is emptied for the next call).
 static inline ws_status run_levels(ws_context *c, int NL, const int32_t *idmap, const int32_t *k0_ptr,
-                                   int32_t *counts, cudaStream_t s)
+                                   int32_t *counts, cudaStream_t s, int list_npix = 0)
 {
     Workspace &w = c->w;
     cudaError_t e = reset_barrier(c, s);
     if (e != cudaSuccess) return set_cuda_error(c, e, "memset");
     {
         PhaseScope ps(c, PH_CLEANUP, s);
-        k_edges_compact<<<c->num_sms * 8, NTHR, 0, s>>>(w.keys, w.vals, w.slots, w.ecount, idmap, k0_ptr,
-                                                        (Edge *)w.ea, w.ecnt, c->status);
-        k_edges_reset<<<1, 32, 0, s>>>(w.ecount, w.ecnt, NL);
-        c->launches += 2;
+        if (list_npix > 0) {
+            k_edges_ids<<<c->num_sms * 8, NTHR, 0, s>>>((Edge *)w.ea, w.ecnt, NL, (int)w.edge_cap, idmap, list_npix,
+                                                        k0_ptr, c->status);
+            c->launches += 1;
+        } else {
+            k_edges_compact<<<c->num_sms * 8, NTHR, 0, s>>>(w.keys, w.vals, w.slots, w.ecount, idmap, k0_ptr,
+                                                            (Edge *)w.ea, w.ecnt, c->status);
+            k_edges_reset<<<1, 32, 0, s>>>(w.ecount, w.ecnt, NL);
+            c->launches += 2;
+        }
     }
     PhaseScope ps(c, PH_LEVELS, s);
     int grid = coop_grid(c, k_levels, NTHR, 0, c->num_sms * tune_levels_ctas(c));
@@ -364,7 +385,8 @@ template <typename T, int CONN> static ws_status run_segment(ws_context *c, cons
     const Batch b = single_batch<CONN>(geo, grad, levels, counts);
     if ((st = run_core<T, CONN>(c, b, NL > 1, s)) != WS_OK) return st;
     if (NL > 1) {
-        if ((st = run_levels(c, NL, w.aux, w.counters + CNT_ROOTS, counts, s)) != WS_OK) return st;
+        if ((st = run_levels(c, NL, w.aux, w.counters + CNT_ROOTS, counts, s, TC<CONN>::D3 ? 0 : geo.N)) != WS_OK)
+            return st;
     } else if (counts) {
         k_copy_int<<<1, 32, 0, s>>>(w.counters + CNT_ROOTS, counts);
         c->launches += 1;
@@ -407,7 +429,9 @@ template <typename T, int CONN> static ws_status run_segment_batch(ws_context *c
     b.npix = (int)npix;
     if ((st = run_core<T, CONN>(c, b, NL > 1, s)) != WS_OK) return st;
     // w.lcount[k] = region count of level k over the whole batch
-    if (NL > 1 && (st = run_levels(c, NL, w.aux, w.counters + CNT_ROOTS, w.lcount, s)) != WS_OK) return st;
+    if (NL > 1 && (st = run_levels(c, NL, w.aux, w.counters + CNT_ROOTS, w.lcount, s, TC<CONN>::D3 ? 0 : b.npix)) !=
+                      WS_OK)
+        return st;
     {
         PhaseScope ps(c, PH_LEVEL_WRITE, s);
         if (CONN == 6)   // 3D: from the voxels' end slots, tile by tile
@@ -534,7 +558,7 @@ template <typename T, int CONN> struct Inst {
     static const Launchers *get()
     {
         static const Launchers L = {&run_watershed<T, CONN>, &run_step1<T, CONN>, &run_plateau_distance<T, CONN>,
-                                    &run_waterfall<T, CONN>, &run_segment<T, CONN>,
+                                    &run_waterfall<T, CONN % 100>, &run_segment<T, CONN>,
                                     &run_segment_batch<T, CONN>, sizeof(ImgDesc), &descs_host<CONN>,
                                     &run_reconstruct<T, CONN>};
         return &L;

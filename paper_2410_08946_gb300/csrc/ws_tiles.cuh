@@ -50,13 +50,28 @@
 
 namespace ws {
 
+// Tile shape and threads per tile.  2D images run on shape 0 (64 x 32
+// pixels, 256 threads) unless ws_tuning.tile_shape picks another (uint8
+// gradients): 1 = 32 x 32 / 256, 2 = 128 x 16 / 256, 3 = 64 x 32 / 512; the
+// template value is CONN + 100 * shape.  TX stays a multiple of 32 (warps
+// cover whole runs of one row).
 template <int CONN> struct TT;
 template <> struct TT<4> {
     static constexpr int TX = 64, TY = 32, TZ = 1, NT = 256;
 };
-template <> struct TT<8> {
-    static constexpr int TX = 64, TY = 32, TZ = 1, NT = 256;
+template <> struct TT<8> : TT<4> {};
+template <> struct TT<104> {
+    static constexpr int TX = 32, TY = 32, TZ = 1, NT = 256;
 };
+template <> struct TT<108> : TT<104> {};
+template <> struct TT<204> {
+    static constexpr int TX = 128, TY = 16, TZ = 1, NT = 256;
+};
+template <> struct TT<208> : TT<204> {};
+template <> struct TT<304> {
+    static constexpr int TX = 64, TY = 32, TZ = 1, NT = 512;
+};
+template <> struct TT<308> : TT<304> {};
 template <> struct TT<6> {
     static constexpr int TX = 32, TY = 16, TZ = 16, NT = 512;
 };
@@ -76,7 +91,7 @@ template <int CONN> struct TC {
     // forward box of k_label: +1 on every axis, and -1 in x / y where a
     // forward neighbour lies there
     // (forward neighbours reach x - 1 in 8- and 26-connectivity, y - 1 in 26)
-    static constexpr int BXL = (CONN == 8 || CONN == 26) ? 1 : 0;
+    static constexpr int BXL = (CONN % 100 == 8 || CONN == 26) ? 1 : 0;
     static constexpr int BYL = CONN == 26 ? 1 : 0;
     static constexpr int BX = TX + 1 + BXL, BY = TY + 1 + BYL, BZ = D3 ? TZ + 1 : 1;
     static constexpr int BS = BX * BY * BZ;
@@ -724,14 +739,30 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             }
             nend = __shfl_sync(0xffffffffu, inc, 31);
             if (lane < NW) wbase[lane] = inc - c;
-            if (lane == 0) first = atomicAdd(counters + CNT_ENDS, nend);
+            if (lane == 0) {
+                first = atomicAdd(counters + CNT_ENDS, nend);
+                s_first = first;
+                tends[t] = make_int2(first, nend);
+            }
         }
         __syncthreads();
         const int slot0 = wbase[ly] + lpre;   // the slot of this thread's first end
-        for (unsigned m = endb; m; m &= m - 1) {   // an end's entry: its slot, below its lowest neighbour
-            const int k = __ffs(m) - 1;
-            uint16_t *e = slotof + tid + k * C::NT;
-            *e = (uint16_t)(*e | (slot0 + __popc(endb & ((1u << k) - 1u))));
+        {
+            // each end: its slot goes below its lowest neighbour in its slotof
+            // entry, and its entry of ends is (the end, the next pixel of its
+            // path: the neighbour its arrow leads to out of the tile, or itself
+            // for a minimum or a plateau pixel)
+            const int fst = s_first;
+            for (unsigned m = endb; m; m &= m - 1) {
+                const int k = __ffs(m) - 1;
+                uint16_t *se = slotof + tid + k * C::NT;
+                const unsigned v = *se;
+                const int sl = slot0 + __popc(endb & ((1u << k) - 1u));
+                *se = (uint16_t)(v | (unsigned)sl);
+                const int e = p0 + k * HW;
+                const int nxt = ((stb >> (2 * k)) & 3u) == (unsigned)ST0 ? e + go6((int)(v >> 13), geo) : e;
+                ends[fst + sl] = make_int2(e, nxt);
+            }
         }
 
         // step III inside the tile: pointer doubling.  A value read while its
@@ -760,27 +791,11 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             }
             if (!more) break;
         }
-        if (tid == 0) {
-            s_first = first;
-            tends[t] = make_int2(first, nend);
-        }
         __syncthreads();   // every pointer at its end; slotof published
-        {
-            const int fst = s_first;
 #pragma unroll
-            for (int k = 0; k < C::TZ; k++) {
-                if (((stb >> (2 * k)) & 3u) == (unsigned)STOUT) continue;
-                code[p0 + k * HW] = slotof[cur[k]];   // cur[k]: the end (the top three bits ride along)
-            }
-            // each end with the next pixel of its path: the neighbour its arrow
-            // leads to (out of the tile), or itself (a minimum or plateau pixel)
-            for (unsigned m = endb; m; m &= m - 1) {
-                const int k = __ffs(m) - 1;
-                const int e = p0 + k * HW;
-                const int dn = slotof[tid + k * C::NT] >> 13;
-                const int nxt = ((stb >> (2 * k)) & 3u) == (unsigned)ST0 ? e + go6(dn, geo) : e;
-                ends[fst + slot0 + __popc(endb & ((1u << k) - 1u))] = make_int2(e, nxt);
-            }
+        for (int k = 0; k < C::TZ; k++) {
+            if (((stb >> (2 * k)) & 3u) == (unsigned)STOUT) continue;
+            code[p0 + k * HW] = slotof[cur[k]];   // cur[k]: the end (the top three bits ride along)
         }
         if (__syncthreads_or(plateau)) {
             // a plateau tile: step II starts from dist, and the step II / IV
@@ -1059,7 +1074,7 @@ __global__ void __launch_bounds__(NTHR) k_union2(const Batch b, int32_t *par, co
             const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
             // only pixels with a forward neighbour outside the tile
             const bool border = lx == C::TX - 1 || ly == C::TY - 1 || (C::D3 && lz == C::TZ - 1) ||
-                                ((CONN == 8 || CONN == 26) && lx == 0) || (CONN == 26 && ly == 0);
+                                ((CONN % 100 == 8 || CONN == 26) && lx == 0) || (CONN == 26 && ly == 0);
             if (!border) continue;
             const int x = tc.x0 + lx, y = tc.y0 + ly, z = tc.z0 + lz;
             if (x >= geo.W || y >= geo.H || z >= geo.D) continue;
@@ -1182,12 +1197,10 @@ __global__ void __launch_bounds__(NTHR) k_jump2(const Batch b, int32_t *par, con
 
 // Insert (key, h) into the CTA's edge hash (min of h per key).  The slot is
 // read before any atomic: lanes that find their key already present with a
-// pass value <= h issue no atomic at all.  A crowded CTA table falls back to
-// the global region table.
+// pass value <= h issue no atomic at all.  A crowded CTA table sends the pair
+// straight to the sink.
 static __device__ __noinline__ void smem_edge_insert(unsigned a, unsigned b, unsigned h, unsigned long long *hk,
-                                                     unsigned *hv, int nslots, unsigned long long *keys,
-                                                     uint32_t *vals, int32_t *slots, int32_t *ecount,
-                                                     unsigned long long gmask, DevStatus *status)
+                                                     unsigned *hv, int nslots, const EdgeSink &L, DevStatus *status)
 {
     const unsigned long long key = ((unsigned long long)a << 32) | b;
     unsigned s = (a * 0x9E3779B1u) ^ (b * 0x85EBCA77u);
@@ -1204,7 +1217,7 @@ static __device__ __noinline__ void smem_edge_insert(unsigned a, unsigned b, uns
         }
         s = (s + 1) & (unsigned)(nslots - 1);
     }
-    edge_insert(key, h, keys, vals, slots, ecount, gmask, status);
+    sink_put1(L, a, b, h, status);
 }
 
 // Shared-memory layout of k_label: the CTA's edge hash, then the path-end /
@@ -1247,9 +1260,8 @@ __device__ __forceinline__ int dedupe_slot(int *dk, int key, int nslots)
 template <typename T, int CONN, bool TMA>
 __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ CUtensorMap tmp,
                                                         const __grid_constant__ CUtensorMap tmg, const Batch b,
-                                                        int32_t *par, int32_t *mi, int do_rag,
-                                                        unsigned long long *keys, uint32_t *vals, int32_t *slots,
-                                                        int32_t *ecount, unsigned long long gmask, DevStatus *status)
+                                                        int32_t *par, int32_t *mi, int do_rag, const EdgeSink L,
+                                                        DevStatus *status)
 {
     using C = TC<CONN>;
     using B = LabelBox<T, CONN>;
@@ -1398,22 +1410,21 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
                 continue;
             }
             if (rl >= 0)
-                smem_edge_insert((unsigned)(r < rl ? r : rl), (unsigned)(r < rl ? rl : r), hl, hk, hv, C::HASH, keys,
-                                 vals, slots, ecount, gmask, status);
+                smem_edge_insert((unsigned)(r < rl ? r : rl), (unsigned)(r < rl ? rl : r), hl, hk, hv, C::HASH, L,
+                                 status);
             rl = rq;
             hl = h;
         }
         if (rl >= 0)
-            smem_edge_insert((unsigned)(r < rl ? r : rl), (unsigned)(r < rl ? rl : r), hl, hk, hv, C::HASH, keys, vals,
-                             slots, ecount, gmask, status);
+            smem_edge_insert((unsigned)(r < rl ? r : rl), (unsigned)(r < rl ? rl : r), hl, hk, hv, C::HASH, L, status);
     }
     if (!do_rag) return;
     __syncthreads();
     static_assert(C::HASH % C::NT == 0, "warp-uniform flush");
     for (int i0 = 0; i0 < C::HASH; i0 += C::NT) {
         const int i = i0 + tid;
-        const int sl = hk[i] != EMPTY_KEY ? edge_insert_slot(hk[i], hv[i], keys, vals, gmask, status) : -1;
-        append_slots(sl, slots, ecount);
+        const unsigned long long k = hk[i];
+        sink_put_warp(L, k != EMPTY_KEY, (unsigned)(k >> 32), (unsigned)k, hv[i], status);
     }
 }
 
@@ -1545,9 +1556,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
                                                        const uint16_t *__restrict__ code,
                                                        const int2 *__restrict__ ends,
                                                        const int2 *__restrict__ tends, int32_t *mi,
-                                                       int do_rag, unsigned long long *keys, uint32_t *vals,
-                                                       int32_t *slots, int32_t *ecount, unsigned long long gmask,
-                                                       DevStatus *status)
+                                                       int do_rag, const EdgeSink L, DevStatus *status)
 {
     using C = TC<6>;
     using B = Rag6Box<T>;
@@ -1697,8 +1706,8 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
             atomicMin(pm + a * B::RM + c2, h);
         } else {
             const int ra = mode < 2 ? rl[ida] : ida, rb = mode < 2 ? rl[idb] : idb;
-            smem_edge_insert((unsigned)(ra < rb ? ra : rb), (unsigned)(ra < rb ? rb : ra), h, hk, hv, B::EH, keys,
-                             vals, slots, ecount, gmask, status);
+            smem_edge_insert((unsigned)(ra < rb ? ra : rb), (unsigned)(ra < rb ? rb : ra), h, hk, hv, B::EH, L,
+                             status);
         }
     };
     const int p0 = base + (z0 * geo.H + y) * geo.W + x;   // global index of (lane, ly, z = 0)
@@ -1772,7 +1781,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
                     } else {
                         const int ra = rl[a], rb = rl[c2];
                         smem_edge_insert((unsigned)(ra < rb ? ra : rb), (unsigned)(ra < rb ? rb : ra), h, hk, hv,
-                                         B::EH, keys, vals, slots, ecount, gmask, status);
+                                         B::EH, L, status);
                     }
                 };
                 // 0x00 / 0xff bytes -> bits 0..3
@@ -1883,17 +1892,24 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
     __syncthreads();
     if (mode < 2 && tid < nr && tid < B::RB && rmin[tid] != 0x7fffffff) atomicMin(mi + rl[tid], rmin[tid]);
     if (!do_rag) return;
+    static_assert((B::RM * B::RM) % C::NT == 0 && B::EH % C::NT == 0, "warp-uniform flush");
     if (mode == 0) {
         for (int e = tid; e < B::RM * B::RM; e += C::NT) {
             const unsigned h = pm[e];
-            if (h == 0xffffffffu) continue;
-            const int ra = rl[e / B::RM], rb = rl[e % B::RM];
-            const unsigned lo = (unsigned)(ra < rb ? ra : rb), hi = (unsigned)(ra < rb ? rb : ra);
-            edge_insert(((unsigned long long)lo << 32) | hi, h, keys, vals, slots, ecount, gmask, status);
+            const bool have = h != 0xffffffffu;
+            unsigned lo = 0, hi = 0;
+            if (have) {   // the basin list is read for the few pairs present only
+                const int ra = rl[e / B::RM], rb = rl[e % B::RM];
+                lo = (unsigned)(ra < rb ? ra : rb);
+                hi = (unsigned)(ra < rb ? rb : ra);
+            }
+            sink_put_warp(L, have, lo, hi, h, status);
         }
     } else {
-        for (int i = tid; i < B::EH; i += C::NT)
-            if (hk[i] != EMPTY_KEY) edge_insert(hk[i], hv[i], keys, vals, slots, ecount, gmask, status);
+        for (int i = tid; i < B::EH; i += C::NT) {
+            const unsigned long long k = hk[i];
+            sink_put_warp(L, k != EMPTY_KEY, (unsigned)(k >> 32), (unsigned)k, hv[i], status);
+        }
     }
 }
 

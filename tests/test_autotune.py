@@ -12,13 +12,29 @@ def test_descend_finds_the_minimum_of_a_separable_cost():
         calls.append(dict(p))
         return (p["jumps_per_round"] - 8) ** 2 + 10 * (p["levels_ctas_per_sm"] - 2) ** 2 + 1.0
 
-    best, ms, table = autotune.descend(cost)
-    assert best == {"jumps_per_round": 8, "levels_ctas_per_sm": 2}
+    best, ms, table = autotune.descend(cost, space=autotune.SPACE_FIXED_SHAPE)
+    assert best == {"tile_shape": 0, "jumps_per_round": 8, "levels_ctas_per_sm": 2}
     assert ms == 1.0
     # one timing per candidate of each parameter, the second with the first fixed at its best
-    n = sum(len(v) for v in autotune.SPACE.values())
+    n = sum(len(v) for v in autotune.SPACE_FIXED_SHAPE.values())
     assert len(table) == len(calls) == n
     assert all(c["jumps_per_round"] == 8 for c in calls[len(autotune.SPACE["jumps_per_round"]):])
+
+
+def test_descend_over_tile_shapes():
+    """The tile shape is the first coordinate; the later ones are timed on the
+    shape chosen for it."""
+    calls = []
+
+    def cost(p):
+        calls.append(dict(p))
+        return {0: 5.0, 1: 4.0, 2: 3.0, 3: 6.0}[p["tile_shape"]] + abs(p["jumps_per_round"] - 12) * 0.1
+
+    best, ms, table = autotune.descend(cost)
+    assert best["tile_shape"] == 2 and best["jumps_per_round"] == 12
+    assert abs(ms - 3.0) < 1e-12
+    assert all(c["tile_shape"] == 2 for c in calls[len(autotune.SPACE["tile_shape"]):])
+    assert set(autotune.SHAPES) == set(autotune.SPACE["tile_shape"])
 
 
 def test_descend_ties_keep_the_first_candidate():

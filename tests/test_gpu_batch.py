@@ -129,18 +129,20 @@ def test_autotune_batch(ctx, tmp_path):
     ctx.check()
     lv = [torch.empty_like(x) for x in ref_levels]
     ct = [torch.empty_like(x) for x in ref_counts]
-    space = {"jumps_per_round": [1, 3, 6], "levels_ctas_per_sm": [1, 4]}
+    space = {"tile_shape": [0, 1, 2, 3], "jumps_per_round": [1, 3, 6], "levels_ctas_per_sm": [1, 4]}
     cache = str(tmp_path / "tune.json")
     res = autotune.autotune(ctx, lambda: ctx.segment_batch(grads, 4, 4, lv, ct), key="test", reps=2,
                             space=space, cache_path=cache)
-    assert not res["cached"] and len(res["table"]) == 5
+    assert not res["cached"] and len(res["table"]) == 9
     assert res["params"]["jumps_per_round"] in (1, 3, 6) and res["params"]["levels_ctas_per_sm"] in (1, 4)
+    assert res["params"]["tile_shape"] in (0, 1, 2, 3)
     for a, b in zip(lv, ref_levels):
         assert torch.equal(a, b)
     for a, b in zip(ct, ref_counts):
         assert torch.equal(a, b)
-    # every candidate gives the same labels (jumps_per_round 1 and one CTA per SM included)
-    for p in ({"jumps_per_round": 1, "levels_ctas_per_sm": 1}, {"jumps_per_round": 16, "levels_ctas_per_sm": 8}):
+    # every candidate gives the same labels (every tile shape, jumps_per_round 1 and one CTA per SM included)
+    for p in ({"jumps_per_round": 1, "levels_ctas_per_sm": 1}, {"jumps_per_round": 16, "levels_ctas_per_sm": 8},
+              {"tile_shape": 1}, {"tile_shape": 2}, {"tile_shape": 3, "jumps_per_round": 1}):
         ctx.set_tuning(**p)
         levels, counts = ctx.segment_batch(grads, 4, 4)
         ctx.check()
