@@ -406,8 +406,8 @@ ws_status ws_plateau_distance(ws_context *ctx, const void *grad_d, ws_dtype dtyp
 #define WS_STATIC_MAX_PIXELS 524288
 
 /* Size of the device array that holds all scratch of ws_watershed_static
- * (about 14.2 MB; the library checks this figure against its layout). */
-#define WS_STATIC_SCRATCH_BYTES 14193408
+ * (about 15.5 MB; the library checks this figure against its layout). */
+#define WS_STATIC_SCRATCH_BYTES 15504384
 
 /*
  * The result of ws_watershed (the same labels and the same count) for callers

@@ -76,24 +76,31 @@ __global__ void __launch_bounds__(256) k_gradient(const uint8_t *__restrict__ im
 }
 
 // ---------------------------------------------------------------------------
-// 3D: one CTA produces a 32 x 8 x 8 tile of the gradient of a volume
+// 3D: one CTA streams a 32 x 16 column of the volume along z
 // ---------------------------------------------------------------------------
-//   1. the 38 x 14 x 14 input window (3-voxel halo, replicated border) is
-//      staged in shared memory;
-//   2. the 5x5x5 binomial blur is taken as three exact integer passes (x, y,
-//      z; sums below 2^29, rounded once: (sum + 2048) >> 12) at the 34 x 10 x
-//      10 positions the Sobel stencil reads, each a 5-tap window sliding in
-//      registers; a position outside the volume takes the blur of the nearest
-//      border voxel, like the 2D kernel;
-//   3. 3x3x3 Sobel from per-plane 3x3 sums sliding along z, exact floor square
-//      root of gx^2 + gy^2 + gz^2 (float estimate corrected by 64-bit integer
-//      comparisons), >> shift, clip.
-constexpr int G3X = 32, G3Y = 8, G3Z = 8;
-constexpr int I3X = G3X + 6, I3Y = G3Y + 6, I3Z = G3Z + 6;   // input window
-constexpr int B3X = G3X + 2, B3Y = G3Y + 2, B3Z = G3Z + 2;   // blur window
-constexpr int S3A = I3Z * I3Y * I3X;   // input window, then the x-y sums  (>= I3Z * B3Y * B3X)
-constexpr int S3B = I3Z * I3Y * B3X;   // x sums, then the blur            (>= B3Z * B3Y * B3X)
-constexpr int G3_SMEM = (S3A + S3B) * 4;
+// A CTA owns the outputs (x0..x0+31, y0..y0+15, z0..z0+ZC-1), one thread per
+// (x, y), and walks the input planes in z order, so that every input voxel
+// of the column (with its 3-voxel x-y halo) is read once:
+//   1. the plane's 38 x 22 window (replicated border) goes to shared memory
+//      (the next plane's values are loaded into registers meanwhile);
+//   2. the 5-tap binomial x-pass, then y-pass, give the plane's x-y blurred
+//      sums at the 34 x 18 positions the Sobel reads, kept in a ring of the
+//      last five planes;
+//   3. once a plane has its two successors, the z-pass over the ring gives
+//      its 5x5x5 blur, rounded once: (sum + 2048) >> 12 (sums below 2^29);
+//   4. each thread turns its 3x3 neighbourhood of that plane into the
+//      plane's x difference dx and y difference dy (each smoothed [1 2 1]
+//      across) and its [1 2 1]^2 sum sm, and keeps them for three planes:
+//      gx = [1 2 1]_z of dx, gy = [1 2 1]_z of dy, gz = sm(z + 1) - sm(z - 1);
+//      exact floor square root of gx^2 + gy^2 + gz^2 (float estimate
+//      corrected by 64-bit integer comparisons), >> shift, clip.
+// A blur position outside the volume takes the blur of the nearest border
+// voxel, in x, y and z alike (the blurred volume's border is replicated).
+constexpr int ZX = 32, ZY = 16, ZT = ZX * ZY;                 // output tile, one thread per (x, y)
+constexpr int ZIX = ZX + 6, ZIY = ZY + 6, ZBX = ZX + 2, ZBY = ZY + 2;
+constexpr int ZIN = ZIX * ZIY, ZXS = ZBX * ZIY, ZBS = ZBX * ZBY;
+constexpr int ZC = 64;                                        // output planes per CTA
+static_assert(ZIN <= 2 * ZT, "two window loads per thread");
 
 __device__ __forceinline__ unsigned isqrt64_exact(unsigned long long v)
 {
@@ -103,100 +110,97 @@ __device__ __forceinline__ unsigned isqrt64_exact(unsigned long long v)
     return (unsigned)r;
 }
 
-// One line of a blur pass: out[k * os] = the 5-tap binomial sum of `line` at
-// position P0 + k clamped to [0, L - 1] (so positions beyond the border repeat
-// the border's sum), for k < n; line[u * is] is the input at coordinate u
-// (only coordinates clamped into [0, L - 1] are read).  In the interior the
-// window slides: one new load per output.  ROUND: (sum + 2048) >> 12.
-template <bool ROUND>
-__device__ __forceinline__ void blur_line(const unsigned *line, int is, unsigned *out, int os, int P0, int n, int L)
-{
-    auto at = [&](int u) { return line[clampi(u, 0, L - 1) * is]; };
-    auto put = [&](int k, unsigned sum) { out[k * os] = ROUND ? (sum + 2048u) >> 12 : sum; };
-    int k = 0;
-    for (; k < n && P0 + k < 0; k++) put(k, at(-2) + 4u * at(-1) + 6u * at(0) + 4u * at(1) + at(2));   // = position 0
-    if (k < n && P0 + k < L) {
-        int X = P0 + k;
-        unsigned w0 = at(X - 2), w1 = at(X - 1), w2 = at(X), w3 = at(X + 1);
-        for (; k < n && X < L; k++, X++) {
-            const unsigned w4 = at(X + 2);
-            put(k, w0 + 4u * w1 + 6u * w2 + 4u * w3 + w4);
-            w0 = w1;
-            w1 = w2;
-            w2 = w3;
-            w3 = w4;
-        }
-    }
-    if (k < n) {   // beyond the far border: the sum at L - 1
-        const unsigned e = at(L - 3) + 4u * at(L - 2) + 6u * at(L - 1) + 4u * at(L) + at(L + 1);
-        for (; k < n; k++) put(k, e);
-    }
-}
+struct Sob {   // one blurred plane's x and y differences and its 3x3 sum at a thread's (x, y)
+    int dx, dy, sm;
+};
 
 template <typename V>
-__global__ void __launch_bounds__(256) k_gradient3d(const V *__restrict__ img, int W, int H, int D, int shift,
-                                                    uint16_t *__restrict__ out)
+__global__ void __launch_bounds__(ZT) k_gradient3d(const V *__restrict__ img, int W, int H, int D, int shift,
+                                                   uint16_t *__restrict__ out)
 {
-    extern __shared__ unsigned g3s[];
-    unsigned *A = g3s, *B = g3s + S3A;
+    __shared__ unsigned inp[ZIN];       // the input plane's window
+    __shared__ unsigned xs[ZXS];        // its x-pass
+    __shared__ unsigned ring[5][ZBS];   // x-y blurred sums of the last five input planes (slot: plane mod 5)
+    __shared__ unsigned bz[ZBS];        // the blurred plane
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * G3X, y0 = blockIdx.y * G3Y, z0 = blockIdx.z * G3Z;
-    for (int i = tid; i < S3A; i += 256) {
-        const int ix = i % I3X, iy = (i / I3X) % I3Y, iz = i / (I3X * I3Y);
-        const int gx = clampi(x0 - 3 + ix, 0, W - 1), gy = clampi(y0 - 3 + iy, 0, H - 1);
-        const int gz = clampi(z0 - 3 + iz, 0, D - 1);
-        A[i] = img[((size_t)gz * H + gy) * W + gx];
-    }
-    __syncthreads();
-    // Each pass slides a 5-tap window along its axis in registers: one thread
-    // per row / column / pillar reads every input once.
-    // x: B[iz][iy][bx] = sum_t w_t A[iz][iy][clamp(X + t)], X = clamp(x0 - 1 + bx)
-    for (int r = tid; r < I3Z * I3Y; r += 256)
-        blur_line<false>(A + r * I3X - (x0 - 3), 1, B + r * B3X, 1, x0 - 1, B3X, W);
-    __syncthreads();
-    // y: A[iz][by][bx] = sum_t w_t B[iz][clamp(Y + t)][bx], Y = clamp(y0 - 1 + by)
-    for (int c = tid; c < I3Z * B3X; c += 256) {
-        const int bx = c % B3X, iz = c / B3X;
-        blur_line<false>(B + iz * I3Y * B3X - (y0 - 3) * B3X + bx, B3X, A + iz * B3Y * B3X + bx, B3X, y0 - 1, B3Y,
-                         H);
-    }
-    __syncthreads();
-    // z: B[bz][by][bx] = (sum_t w_t A[clamp(Z + t)][by][bx] + 2048) >> 12, Z = clamp(z0 - 1 + bz)
-    for (int c = tid; c < B3Y * B3X; c += 256)
-        blur_line<true>(A - (z0 - 3) * (B3Y * B3X) + c, B3Y * B3X, B + c, B3Y * B3X, z0 - 1, B3Z, D);
-    __syncthreads();
-    // Sobel (positions beyond the border hold the border's blur).  Per blurred
-    // plane the thread's 3x3 (y, x) neighbourhood gives dx = [1 2 1]_y of the
-    // x difference, dy = [1 2 1]_x of the y difference and sm = [1 2 1]^2 of
-    // the values; then gx = [1 2 1]_z of dx, gy = [1 2 1]_z of dy and
-    // gz = sm(z + 1) - sm(z - 1).
-    const int lx = tid & 31, ly = tid >> 5;
-    const int x = x0 + lx, y = y0 + ly;
-    if (x >= W || y >= H) return;
-    int dxm = 0, dym = 0, smm = 0, dx0 = 0, dy0 = 0, sm0 = 0;
-    for (int bz = 0; bz < B3Z; bz++) {
-        const unsigned *pl = B + (bz * B3Y + ly) * B3X + lx;   // (y - 1, x - 1) of this plane
+    const int x0 = blockIdx.x * ZX, y0 = blockIdx.y * ZY, z0 = blockIdx.z * ZC;
+    const int z1 = min(z0 + ZC, D);                             // outputs z0 .. z1 - 1
+    const int zlo = max(z0 - 1, 0), zhi = min(z1, D - 1);       // the blurred planes they read
+    const size_t HW = (size_t)H * W;
+    // this thread's two slots of the window, as offsets within a plane (clamped), or -1
+    auto slot = [&](int l) -> long long {
+        if (l >= ZIN) return -1;
+        const int ix = l % ZIX, iy = l / ZIX;
+        return (long long)clampi(y0 - 3 + iy, 0, H - 1) * W + clampi(x0 - 3 + ix, 0, W - 1);
+    };
+    const long long a0 = slot(tid), a1 = slot(tid + ZT);
+    auto fetch = [&](int zi, unsigned &v0, unsigned &v1) {
+        const size_t pz = (size_t)clampi(zi, 0, D - 1) * HW;
+        v0 = a0 >= 0 ? (unsigned)img[pz + a0] : 0u;
+        v1 = a1 >= 0 ? (unsigned)img[pz + a1] : 0u;
+    };
+    unsigned v0, v1;
+    fetch(zlo - 2, v0, v1);
+    const int ox = tid % ZX, oy = tid / ZX;
+    const int x = x0 + ox, y = y0 + oy;
+    const bool mine = x < W && y < H;
+    Sob A{0, 0, 0}, B{0, 0, 0};   // planes zb - 2, zb - 1
+    auto emit = [&](int z, const Sob &m, const Sob &c, const Sob &p) {
+        const long long gxs = m.dx + 2 * c.dx + p.dx, gys = m.dy + 2 * c.dy + p.dy, gzs = p.sm - m.sm;
+        const unsigned long long s2 =
+            (unsigned long long)(gxs * gxs) + (unsigned long long)(gys * gys) + (unsigned long long)(gzs * gzs);
+        const unsigned mg = isqrt64_exact(s2) >> shift;
+        out[(size_t)z * HW + (size_t)y * W + x] = (uint16_t)(mg > 65535u ? 65535u : mg);
+    };
+    for (int zi = zlo - 2; zi <= zhi + 2; zi++) {
+        if (a0 >= 0) inp[tid] = v0;
+        if (a1 >= 0) inp[tid + ZT] = v1;
+        __syncthreads();
+        if (zi < zhi + 2) fetch(zi + 1, v0, v1);   // in flight while this plane is blurred
+        // x-pass at X = clamp(x0 - 1 + bx)
+        for (int e = tid; e < ZXS; e += ZT) {
+            const int bx = e % ZBX, iy = e / ZBX;
+            const unsigned *r = inp + iy * ZIX + clampi(x0 - 1 + bx, 0, W - 1) - (x0 - 3);
+            xs[e] = r[-2] + 4u * r[-1] + 6u * r[0] + 4u * r[1] + r[2];
+        }
+        __syncthreads();
+        // y-pass at Y = clamp(y0 - 1 + by), into the ring
+        unsigned *rs = ring[(zi + 10) % 5];
+        for (int e = tid; e < ZBS; e += ZT) {
+            const int bx = e % ZBX, by = e / ZBX;
+            const unsigned *c = xs + (clampi(y0 - 1 + by, 0, H - 1) - (y0 - 3)) * ZBX + bx;
+            rs[e] = c[-2 * ZBX] + 4u * c[-ZBX] + 6u * c[0] + 4u * c[ZBX] + c[2 * ZBX];
+        }
+        __syncthreads();
+        const int zb = zi - 2;   // the blurred plane whose five input planes are in the ring
+        if (zb < zlo) continue;
+        // z-pass: planes zb - 2 .. zb + 2 are the ring's input planes zi - 4 .. zi
+        // (clamped into the volume when they were loaded)
+        for (int e = tid; e < ZBS; e += ZT) {
+            const unsigned sum = ring[(zi + 6) % 5][e] + 4u * ring[(zi + 7) % 5][e] + 6u * ring[(zi + 8) % 5][e] +
+                                 4u * ring[(zi + 9) % 5][e] + ring[(zi + 10) % 5][e];
+            bz[e] = (sum + 2048u) >> 12;
+        }
+        __syncthreads();
+        const unsigned *pl = bz + oy * ZBX + ox;   // (y - 1, x - 1) of this plane
         int v[3][3];
 #pragma unroll
         for (int j = 0; j < 3; j++)
 #pragma unroll
-            for (int i = 0; i < 3; i++) v[j][i] = (int)pl[j * B3X + i];
-        const int dx = (v[0][2] - v[0][0]) + 2 * (v[1][2] - v[1][0]) + (v[2][2] - v[2][0]);
-        const int dy = (v[2][0] - v[0][0]) + 2 * (v[2][1] - v[0][1]) + (v[2][2] - v[0][2]);
-        const int sm = (v[0][0] + 2 * v[0][1] + v[0][2]) + 2 * (v[1][0] + 2 * v[1][1] + v[1][2]) +
-                       (v[2][0] + 2 * v[2][1] + v[2][2]);
-        if (bz >= 2) {   // output plane z = z0 + bz - 2 (its blurred planes are bz - 2 .. bz)
-            const int z = z0 + bz - 2;
-            if (z >= D) break;
-            const int gxs = dxm + 2 * dx0 + dx, gys = dym + 2 * dy0 + dy, gzs = sm - smm;
-            const unsigned long long s2 = (unsigned long long)((long long)gxs * gxs) +
-                                          (unsigned long long)((long long)gys * gys) +
-                                          (unsigned long long)((long long)gzs * gzs);
-            const unsigned m = isqrt64_exact(s2) >> shift;
-            out[((size_t)z * H + y) * W + x] = (uint16_t)(m > 65535u ? 65535u : m);
+            for (int i = 0; i < 3; i++) v[j][i] = (int)pl[j * ZBX + i];
+        Sob T;
+        T.dx = (v[0][2] - v[0][0]) + 2 * (v[1][2] - v[1][0]) + (v[2][2] - v[2][0]);
+        T.dy = (v[2][0] - v[0][0]) + 2 * (v[2][1] - v[0][1]) + (v[2][2] - v[0][2]);
+        T.sm = (v[0][0] + 2 * v[0][1] + v[0][2]) + 2 * (v[1][0] + 2 * v[1][1] + v[1][2]) +
+               (v[2][0] + 2 * v[2][1] + v[2][2]);
+        if (mine) {
+            // output z = zb - 1 reads planes zb - 2 (clamped at 0), zb - 1, zb
+            if (zb > zlo && zb - 1 >= z0 && zb - 1 < z1) emit(zb - 1, zb >= 2 ? A : B, B, T);
+            // the volume's last plane reads itself in place of plane D
+            if (zb == D - 1 && zb >= z0 && zb < z1) emit(zb, zb > zlo ? B : T, T, T);
         }
-        dxm = dx0; dym = dy0; smm = sm0;
-        dx0 = dx; dy0 = dy; sm0 = sm;
+        A = B;
+        B = T;
     }
 }
 
@@ -224,19 +228,14 @@ ws_status launch_gradient(ws_context *c, const uint8_t *img, int W, int H, int s
 ws_status launch_gradient3d(ws_context *c, const void *vol, int bps, int W, int H, int D, int shift,
                             uint16_t *grad, cudaStream_t s)
 {
-    dim3 grid((W + G3X - 1) / G3X, (H + G3Y - 1) / G3Y, (D + G3Z - 1) / G3Z);
-    cudaError_t e = bps == 1 ? cudaFuncSetAttribute(k_gradient3d<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    G3_SMEM)
-                             : cudaFuncSetAttribute(k_gradient3d<uint16_t>,
-                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, G3_SMEM);
-    if (e != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
+    dim3 grid((W + ZX - 1) / ZX, (H + ZY - 1) / ZY, (D + ZC - 1) / ZC);
     PhaseScope ps(c, PH_GRADIENT, s);
     if (bps == 1)
-        k_gradient3d<uint8_t><<<grid, 256, G3_SMEM, s>>>((const uint8_t *)vol, W, H, D, shift, grad);
+        k_gradient3d<uint8_t><<<grid, ZT, 0, s>>>((const uint8_t *)vol, W, H, D, shift, grad);
     else
-        k_gradient3d<uint16_t><<<grid, 256, G3_SMEM, s>>>((const uint16_t *)vol, W, H, D, shift, grad);
+        k_gradient3d<uint16_t><<<grid, ZT, 0, s>>>((const uint16_t *)vol, W, H, D, shift, grad);
     c->launches += 1;
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WS_OK : set_cuda_error(c, e, "gradient3d launch");
 }
 

@@ -224,14 +224,16 @@ struct Edge {
 
 // Where the segmentation path's adjacency kernels put their pairs of basins
 // (a < b, root pixels) with the lowest pass each one saw:
-//   - a list (hashed == 0): records appended at e[*n], a pair found by several
+//   - a list (HASHED = false): records appended at e[*n], a pair found by several
 //     tiles once per tile.  The waterfall needs no more (its merge rule reads a
 //     pair's minimum over all its records), and appends cost far less than
 //     the table's atomics; 2D images, whose small basins rarely meet across
 //     tiles, take it.  A record past cap is dropped and reported as a full
 //     table.
-//   - the region table (hashed != 0): one record per pair; 3D volumes, whose
-//     large basins meet across many tiles, take it.
+//   - the region table (HASHED = true): one record per pair; 3D volumes,
+//     whose large basins meet across many tiles, take it.
+// The choice is fixed per kernel instantiation (a template parameter of the
+// put functions), so a kernel carries the code of one of them only.
 struct EdgeSink {
     Edge *e;
     int32_t *n;
@@ -241,7 +243,6 @@ struct EdgeSink {
     int32_t *slots;
     int32_t *ecount;
     unsigned long long gmask;
-    int hashed;
 };
 
 static __device__ __forceinline__ unsigned long long mix64(unsigned long long k)
@@ -320,10 +321,11 @@ static __device__ __forceinline__ void list_put(const EdgeSink &S, int i, unsign
 }
 
 // One pair from any thread.
+template <bool HASHED>
 static __device__ __forceinline__ void sink_put1(const EdgeSink &S, unsigned a, unsigned b, unsigned h,
                                                  DevStatus *status)
 {
-    if (S.hashed)
+    if (HASHED)
         edge_insert(((unsigned long long)a << 32) | b, h, S.keys, S.vals, S.slots, S.ecount, S.gmask, status);
     else
         list_put(S, atomicAdd(S.n, 1), a, b, h, status);
@@ -331,10 +333,11 @@ static __device__ __forceinline__ void sink_put1(const EdgeSink &S, unsigned a, 
 
 // The pairs of the lanes with have == true; every lane of the warp calls it
 // (one counter atomic per warp).
+template <bool HASHED>
 static __device__ __forceinline__ void sink_put_warp(const EdgeSink &S, bool have, unsigned a, unsigned b,
                                                      unsigned h, DevStatus *status)
 {
-    if (S.hashed) {
+    if (HASHED) {
         const int sl = have ? edge_insert_slot(((unsigned long long)a << 32) | b, h, S.keys, S.vals, S.gmask, status)
                             : -1;
         append_slots(sl, S.slots, S.ecount);
@@ -589,12 +592,13 @@ static __global__ void __launch_bounds__(NTHR) k_levels(Edge *e0, Edge *e1, int3
             uf[a] = a;
         }
         if (!grid_barrier(status, timeout_ns)) return;
-        // B: newmin(A) = lowest pass of A
+        // B: newmin(A) = lowest pass of A (newmin only falls: an edge whose
+        // pass is not below the value it reads issues no atomic)
         for (int e = blockIdx.x * NTHR + tid; e < E; e += gsz) {
             const Edge ed = ld_edge(cur + e);
             if (ed.a != ed.b) {
-                atomicMin(newmin + ed.a, ed.h);
-                atomicMin(newmin + ed.b, ed.h);
+                if (ed.h < __ldcg(newmin + ed.a)) atomicMin(newmin + ed.a, ed.h);
+                if (ed.h < __ldcg(newmin + ed.b)) atomicMin(newmin + ed.b, ed.h);
             }
         }
         if (!grid_barrier(status, timeout_ns)) return;

@@ -106,6 +106,7 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
     ws_status st = ensure_pixels(c, b.npix, b.ntiles);
     if (st != WS_OK) return st;
     if (CONN == 6 && (st = ensure_ends(c, b.npix, b.ntiles)) != WS_OK) return st;
+    if (kPlateauList<CONN> && (st = ensure_plist(c, b.npix, b.ntiles)) != WS_OK) return st;
     cudaError_t e = cudaMemsetAsync(w.act, 0, 2 * (size_t)b.ntiles, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 16, s);
     if (e == cudaSuccess) e = reset_barrier(c, s);
@@ -136,7 +137,7 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
             if ((e = allow_smem(kern, smem)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
             const int grid = tma ? coop_grid(c, kern, C::NT, smem, b.ntiles) : b.ntiles;
             kern<<<grid, C::NT, smem, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act, w.tlist, w.roots, w.counters,
-                                           c->status, ex);
+                                           c->status, ex, w.plist, w.pspan);
         }
         c->launches += 1;
     }
@@ -151,7 +152,7 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
         const int grid = coop_grid(c, k_plateau2<T, CONN>, C::NT, smem, b.ntiles);
         e = launch_coop(k_plateau2<T, CONN>, grid, C::NT, smem, s, b, w.dist, (const uint8_t *)w.plat, w.act,
                         (const int32_t *)w.tlist, (const int32_t *)w.counters, c->status, tune_plateau_cap(c),
-                        tune_timeout_ns(c));
+                        tune_timeout_ns(c), (const uint16_t *)w.plist, (const int2 *)w.pspan);
         c->launches += 1;
     }
     if (e != cudaSuccess) return set_cuda_error(c, e, "plateau launch");
@@ -172,7 +173,8 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
     {
         PhaseScope ps(c, PH_RESOLVE, s);
         const int grid = b.ntiles < c->num_sms * 8 ? b.ntiles : c->num_sms * 8;
-        k_resolve2<T, CONN><<<grid, C::NT, 0, s>>>(b, w.par, w.dist, w.plat, w.tlist, w.counters, c->status);
+        k_resolve2<T, CONN><<<grid, C::NT, 0, s>>>(b, w.par, w.dist, w.plat, w.tlist, w.counters, c->status,
+                                                   (const uint16_t *)w.plist, (const int2 *)w.pspan);
         k_union2<T, CONN><<<grid, NTHR, 0, s>>>(b, w.par, w.dist, w.plat, w.tlist, w.counters, c->status);
         c->launches += 2;
     }
@@ -183,7 +185,8 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
         const int grid = coop_grid(c, k_jump2<CONN>, NTHR, 0, b.ntiles < c->num_sms * 8 ? b.ntiles : c->num_sms * 8);
         e = launch_coop(k_jump2<CONN>, grid, NTHR, 0, s, b, w.par, (const int32_t *)w.dist, (const int32_t *)w.tlist,
                         w.counters, w.roots, tune_rr(c), c->status, tune_jump_cap(c), tune_timeout_ns(c),
-                        (const uint8_t *)w.plat, w.ends, (const int2 *)w.tends);
+                        (const uint8_t *)w.plat, w.ends, (const int2 *)w.tends, (const uint16_t *)w.plist,
+                        (const int2 *)w.pspan);
         c->launches += 1;
         if (e != cudaSuccess) return set_cuda_error(c, e, "jump launch");
     }
@@ -205,11 +208,16 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
     elist.slots = w.slots;
     elist.ecount = w.ecount;
     elist.gmask = w.edge_cap ? w.edge_cap - 1 : 0;
-    elist.hashed = TC<CONN>::D3 ? 1 : 0;
-    if constexpr (CONN == 6) {  // 3D: roots of the tiles' path ends
+    if constexpr (CONN == 6) {  // 3D: roots of the tiles' path ends (and of their first faces)
+        if (do_rag && (st = ensure_faces(c, b.ntiles)) != WS_OK) return st;
         PhaseScope pc(c, PH_CHASE, s);
         k_chase<<<c->num_sms * 8, NTHR, 0, s>>>(b, w.ends, w.tends, w.code, w.counters, c->status);
         c->launches += 1;
+        if (do_rag) {
+            k_faces<<<b.ntiles < c->num_sms * 16 ? b.ntiles : c->num_sms * 16, NTHR, 0, s>>>(b, w.code, w.ends, w.tends,
+                                                                                           w.faces, c->status);
+            c->launches += 1;
+        }
     }
     {
         PhaseScope ps(c, PH_RAG, s);
@@ -232,7 +240,7 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
             auto kern = tma6 ? k_rag6<T, true> : k_rag6<T, false>;
             if ((e = allow_smem(kern, B6::SMEM)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
             kern<<<b.ntiles, C::NT, B6::SMEM, s>>>(tmc, tmg, b, w.code, w.ends, w.tends, w.aux, do_rag ? 1 : 0, elist,
-                                                   c->status);
+                                                   c->status, do_rag ? (const int32_t *)w.faces : nullptr);
         } else if (tma) {
             if ((e = allow_smem(k_label<T, CONN, true>, B::SMEM)) != cudaSuccess)
                 return set_cuda_error(c, e, "smem attribute");

@@ -48,7 +48,9 @@ constexpr size_t OFF_KCOUNT = OFF_STATUS + a256(sizeof(DevStatus));
 constexpr size_t OFF_CODE = OFF_KCOUNT + 256;                  // 3D path: slot code per pixel
 constexpr size_t OFF_ENDS = OFF_CODE + a256(kMaxPixels * 2);   // 3D path: (end, next), then (root, root)
 constexpr size_t OFF_TENDS = OFF_ENDS + a256(kMaxPixels * 8);  // 3D path: slot span per tile
-constexpr size_t kScratchBytes = OFF_TENDS + a256(kMaxTiles * 8);
+constexpr size_t OFF_PLIST = OFF_TENDS + a256(kMaxTiles * 8); // 2D path: plateau pixels per tile
+constexpr size_t OFF_PSPAN = OFF_PLIST + a256(kMaxPixels * 2); // 2D path: their span per tile
+constexpr size_t kScratchBytes = OFF_PSPAN + a256(kMaxTiles * 8);
 static_assert(kScratchBytes == (size_t)WS_STATIC_SCRATCH_BYTES, "WS_STATIC_SCRATCH_BYTES must match the layout");
 
 }  // namespace
@@ -126,6 +128,10 @@ ws_status setup(int dev, ws_context *out)
         w.ends = reinterpret_cast<int2 *>(base + OFF_ENDS);
         w.ntends = kMaxTiles;
         w.tends = reinterpret_cast<int2 *>(base + OFF_TENDS);
+        w.nplist = kMaxPixels;
+        w.plist = reinterpret_cast<uint16_t *>(base + OFF_PLIST);
+        w.npspan = kMaxTiles;
+        w.pspan = reinterpret_cast<int2 *>(base + OFF_PSPAN);
         sl.ready = true;
     }
     *out = sl.ctx;

@@ -117,7 +117,11 @@ template <int CONN> inline TileGeo tiles_for(const Geo &g)
 }
 
 // counters[] slots in the workspace
-enum { CNT_TILES = 0, CNT_ROOTS = 1, CNT_ENDS = 2 };
+enum { CNT_TILES = 0, CNT_ROOTS = 1, CNT_ENDS = 2, CNT_PLIST = 3 };
+
+// 2D pipelines list every tile's plateau pixels (tile-local indices) for the
+// step II / IV and jumping kernels, which then visit those pixels only.
+template <int CONN> constexpr bool kPlateauList = CONN % 100 == 4 || CONN % 100 == 8;
 
 __device__ __forceinline__ int enc_final(int g) { return -1 - g; }
 __device__ __forceinline__ int dec_final(int e) { return -1 - e; }
@@ -245,8 +249,9 @@ template <typename T, int CONN> struct InitBox {
     static constexpr int ELEMS = RW * C::HY * C::HZ;
     static constexpr int BYTES = ELEMS * (int)sizeof(T);
     static constexpr int STAGE = (BYTES + 127) & ~127;
-    static constexpr int SMEM_TMA = 2 * STAGE + C::NPIX * 4;   // two stages + in-tile arrows
-    static constexpr int SMEM_PLAIN = STAGE + C::NPIX * 4;
+    static constexpr int LISTB = kPlateauList<CONN> ? C::NPIX * 2 : 0;   // staged plateau pixels
+    static constexpr int SMEM_TMA = 2 * STAGE + C::NPIX * 4 + LISTB;   // two stages + in-tile arrows (+ list)
+    static constexpr int SMEM_PLAIN = STAGE + C::NPIX * 4 + LISTB;
 };
 
 template <typename T, int CONN, bool TMA>
@@ -353,13 +358,16 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
     k_init(const __grid_constant__ CUtensorMap tm, const Batch b, int32_t *__restrict__ par,
            int32_t *__restrict__ mi, int32_t *__restrict__ dist, uint8_t *__restrict__ plat,
            uint8_t *__restrict__ act, int32_t *__restrict__ tlist, int32_t *__restrict__ roots, int32_t *counters,
-           DevStatus *status, const StepExport ex)
+           DevStatus *status, const StepExport ex, uint16_t *__restrict__ plist, int2 *__restrict__ pspan)
 {
     using C = TC<CONN>;
     using B = InitBox<T, CONN>;
+    constexpr bool LIST = kPlateauList<CONN>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[2];
+    __shared__ int s_pc, s_pbase;   // the tile's plateau pixels, their first entry in plist
     int *nx = (int *)(smem + (TMA ? 2 : 1) * B::STAGE);
+    uint16_t *sp = (uint16_t *)(nx + C::NPIX);   // the tile's plateau pixels, staged (LIST)
     const int tid = threadIdx.x, lane = tid & 31;
     const int G = gridDim.x;
 
@@ -383,6 +391,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
         const Geo &geo = tc.geo;
         const int x0 = tc.x0, y0 = tc.y0, z0 = tc.z0, base = tc.base;
         const T *g = (const T *)tc.grad;
+        if (LIST && tid == 0) s_pc = 0;   // (ordered before the appends by the barrier below)
         if (TMA) {
             const bool ok = mbar_wait(&bars[s], (unsigned)((j >> 1) & 1), status);
             if (__syncthreads_or(!ok)) return;
@@ -421,9 +430,29 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
             plateau = init_step1<T, CONN, false, EXP>(gs, nx, st, tid, x0, y0, z0, geo, base, ex);
         else
             plateau = init_step1<T, CONN, true, EXP>(gs, nx, st, tid, x0, y0, z0, geo, base, ex);
+        if (LIST && __any_sync(0xffffffffu, plateau)) {   // stage the tile's plateau pixels
+            unsigned pm = 0;
+#pragma unroll
+            for (int k = 0; k < C::PER; k++) pm |= (unsigned)(st[k] == STP) << k;
+            const int np = __popc(pm);
+            int inc = np;   // warp scan of the counts, one shared atomic per warp
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += u;
+            }
+            int off = 0;
+            if (lane == 31) off = atomicAdd(&s_pc, inc);
+            off = __shfl_sync(0xffffffffu, off, 31) + inc - np;
+            for (; pm; pm &= pm - 1) sp[off++] = (uint16_t)(tid + (__ffs(pm) - 1) * C::NT);
+        }
         __syncthreads();  // the gradient box of stage s is no longer read
         if (TMA && tid == 0 && t + 2 * G < b.ntiles)
             init_issue<T, CONN, TMA>(&tm, gs, &bars[s], b, t + 2 * G);
+        if (LIST && tid == 0 && s_pc > 0) {   // the tile's span of plist (read after the next barrier)
+            s_pbase = atomicAdd(counters + CNT_PLIST, s_pc);
+            pspan[t] = make_int2(s_pbase, s_pc);
+        }
 
         // step III inside the tile: pointer doubling through shared memory
         // (in place: every value read is the pointer of a pixel further down
@@ -447,6 +476,8 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
             if (!more) break;
         }
         __syncthreads();
+        if (LIST)
+            for (int q = tid; q < s_pc; q += C::NT) plist[s_pbase + q] = sp[q];
 
 #pragma unroll
         for (int k = 0; k < C::PER; k++) {
@@ -495,8 +526,8 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
         } else if (tid == 0) {
             plat[t] = 0;
         }
-        // (the __syncthreads_or above also orders this tile's nx reads before
-        // the next tile's nx writes)
+        // (the __syncthreads_or above also orders this tile's nx, sp and s_pc
+        // reads before the next tile's writes)
     }
 }
 
@@ -830,9 +861,13 @@ template <typename T, int CONN>
 __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const Batch b, int32_t *dist, const uint8_t *__restrict__ plat,
                                                            uint8_t *act, const int32_t *__restrict__ tlist,
                                                            const int32_t *counters, DevStatus *status, int round_cap,
-                                                           unsigned long long timeout_ns)
+                                                           unsigned long long timeout_ns,
+                                                           const uint16_t *__restrict__ plist,
+                                                           const int2 *__restrict__ pspan)
 {
     using C = TC<CONN>;
+    (void)plist;
+    (void)pspan;
     extern __shared__ __align__(128) unsigned char smem[];
     int *gs = (int *)smem;
     int *ds = gs + C::HS;
@@ -988,16 +1023,29 @@ template <typename T, int CONN>
 __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const Batch b, int32_t *par, const int32_t *__restrict__ dist,
                                                            const uint8_t *__restrict__ plat,
                                                            const int32_t *__restrict__ tlist,
-                                                           const int32_t *counters, DevStatus *status)
+                                                           const int32_t *counters, DevStatus *status,
+                                                           const uint16_t *__restrict__ plist,
+                                                           const int2 *__restrict__ pspan)
 {
     using C = TC<CONN>;
+    constexpr bool LIST = kPlateauList<CONN>;
     __shared__ int lab[C::NPIX];   // tile-local union-find of the minimal-plateau pixels (-1: other pixel)
     const int ntl = counters[CNT_TILES];
     for (int j = blockIdx.x; j < ntl; j += gridDim.x) {
-        const TileCtx tc = tile_ctx<CONN>(b, tlist[j]);
+        const int t = tlist[j];
+        const TileCtx tc = tile_ctx<CONN>(b, t);
         const Geo &geo = tc.geo;
         const T *g = (const T *)tc.grad;
-        for (int i = threadIdx.x; i < C::NPIX; i += C::NT) {
+        // LIST: only the tile's plateau pixels can be minimal-plateau pixels or
+        // point anew (the others have distance 0 or -2)
+        int2 span = make_int2(0, C::NPIX);
+        if (LIST) {
+            for (int i = threadIdx.x; i < C::NPIX; i += C::NT) lab[i] = -1;
+            __syncthreads();
+            span = pspan[t];
+        }
+        for (int ei = threadIdx.x; ei < span.y; ei += C::NT) {
+            const int i = LIST ? (int)plist[span.x + ei] : ei;
             const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
             const int x = tc.x0 + lx, y = tc.y0 + ly, z = tc.z0 + lz;
             int l = -1;
@@ -1108,25 +1156,31 @@ __global__ void __launch_bounds__(NTHR) k_jump2(const Batch b, int32_t *par, con
                                                 const int32_t *__restrict__ tlist, int32_t *counters,
                                                 int32_t *roots, int RR, DevStatus *status, int round_cap,
                                                 unsigned long long timeout_ns, const uint8_t *__restrict__ plat,
-                                                int2 *ends, const int2 *__restrict__ tends)
+                                                int2 *ends, const int2 *__restrict__ tends,
+                                                const uint16_t *__restrict__ plist, const int2 *__restrict__ pspan)
 {
     using C = TC<CONN>;
     constexpr bool SPARSE = CONN == 6;
+    constexpr bool LIST = kPlateauList<CONN>;   // 2D: the tiles' plateau pixels are listed
     const int tid = threadIdx.x, lane = tid & 31;
     const int ntl = counters[CNT_TILES];
     for (int r = 0;; r++) {
         if (blockIdx.x == 0 && tid == 0) status->changed[(r + 1) % 3] = 0;
         int ch = 0;
         for (int j = blockIdx.x; j < ntl; j += gridDim.x) {   // one tile at a time per block
-            const TileCtx tc = tile_ctx<CONN>(b, tlist[j]);
-            for (int i = tid; i < C::NPIX; i += NTHR) {
+            const int t = tlist[j];
+            const TileCtx tc = tile_ctx<CONN>(b, t);
+            const int2 span = LIST ? pspan[t] : make_int2(0, C::NPIX);
+            for (int ei = tid; ei < span.y; ei += NTHR) {
+                const int i = LIST ? (int)plist[span.x + ei] : ei;
                 const int x = tc.x0 + i % C::TX, y = tc.y0 + (i / C::TX) % C::TY, z = tc.z0 + i / (C::TX * C::TY);
                 if (x >= tc.geo.W || y >= tc.geo.H || z >= tc.geo.D) continue;
                 const int p = tc.base + (z * tc.geo.H + y) * tc.geo.W + x;
-                // 2D: only plateau pixels jump, and only across plateau pixels
-                // (the rest of a path is chased tile by tile later; dist is
-                // valid on every tile).  3D: every pixel of a plateau tile jumps.
-                if (!C::D3 && dist[p] <= 0) continue;
+                // 2D: only plateau pixels jump (the listed ones), and only
+                // across plateau pixels (the rest of a path is chased tile by
+                // tile later; dist is valid on every tile).  3D: every pixel
+                // of a plateau tile jumps.
+                if (!C::D3 && !LIST && dist[p] <= 0) continue;
                 const int l0 = __ldcg(par + p);
                 int l = l0;
                 for (int k = 0; k < RR; k++) {
@@ -1162,11 +1216,13 @@ __global__ void __launch_bounds__(NTHR) k_jump2(const Batch b, int32_t *par, con
     // roots of minimal plateaux
     for (int j = blockIdx.x; j < ntl; j += gridDim.x) {
         const TileCtx tc = tile_ctx<CONN>(b, tlist[j]);
-        for (int i0 = 0; i0 < C::NPIX; i0 += NTHR) {   // warp-uniform trip count
-            const int i = i0 + tid;
+        const int2 span = LIST ? pspan[tlist[j]] : make_int2(0, C::NPIX);
+        for (int e0 = 0; e0 < span.y; e0 += NTHR) {   // warp-uniform trip count
+            const int ei = e0 + tid;
             bool isr = false;
             int p = 0;
-            if (i < C::NPIX) {
+            if (ei < span.y) {
+                const int i = LIST ? (int)plist[span.x + ei] : ei;
                 const int x = tc.x0 + i % C::TX, y = tc.y0 + (i / C::TX) % C::TY, z = tc.z0 + i / (C::TX * C::TY);
                 if (x < tc.geo.W && y < tc.geo.H && z < tc.geo.D) {
                     p = tc.base + (z * tc.geo.H + y) * tc.geo.W + x;
@@ -1199,8 +1255,9 @@ __global__ void __launch_bounds__(NTHR) k_jump2(const Batch b, int32_t *par, con
 // read before any atomic: lanes that find their key already present with a
 // pass value <= h issue no atomic at all.  A crowded CTA table sends the pair
 // straight to the sink.
+template <bool HASHED>
 static __device__ __noinline__ void smem_edge_insert(unsigned a, unsigned b, unsigned h, unsigned long long *hk,
-                                                     unsigned *hv, int nslots, const EdgeSink &L, DevStatus *status)
+                                                     unsigned *hv, int nslots, const EdgeSink L, DevStatus *status)
 {
     const unsigned long long key = ((unsigned long long)a << 32) | b;
     unsigned s = (a * 0x9E3779B1u) ^ (b * 0x85EBCA77u);
@@ -1217,7 +1274,7 @@ static __device__ __noinline__ void smem_edge_insert(unsigned a, unsigned b, uns
         }
         s = (s + 1) & (unsigned)(nslots - 1);
     }
-    sink_put1(L, a, b, h, status);
+    sink_put1<HASHED>(L, a, b, h, status);
 }
 
 // Shared-memory layout of k_label: the CTA's edge hash, then the path-end /
@@ -1265,6 +1322,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
 {
     using C = TC<CONN>;
     using B = LabelBox<T, CONN>;
+    constexpr bool HASHED = !kPlateauList<CONN>;   // 2D: the edge list; 26-connectivity: the region table
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     unsigned long long *hk = (unsigned long long *)smem;   // edge hash (after the root phase)
@@ -1410,13 +1468,14 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
                 continue;
             }
             if (rl >= 0)
-                smem_edge_insert((unsigned)(r < rl ? r : rl), (unsigned)(r < rl ? rl : r), hl, hk, hv, C::HASH, L,
-                                 status);
+                smem_edge_insert<HASHED>((unsigned)(r < rl ? r : rl), (unsigned)(r < rl ? rl : r), hl, hk, hv,
+                                         C::HASH, L, status);
             rl = rq;
             hl = h;
         }
         if (rl >= 0)
-            smem_edge_insert((unsigned)(r < rl ? r : rl), (unsigned)(r < rl ? rl : r), hl, hk, hv, C::HASH, L, status);
+            smem_edge_insert<HASHED>((unsigned)(r < rl ? r : rl), (unsigned)(r < rl ? rl : r), hl, hk, hv, C::HASH, L,
+                                     status);
     }
     if (!do_rag) return;
     __syncthreads();
@@ -1424,7 +1483,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
     for (int i0 = 0; i0 < C::HASH; i0 += C::NT) {
         const int i = i0 + tid;
         const unsigned long long k = hk[i];
-        sink_put_warp(L, k != EMPTY_KEY, (unsigned)(k >> 32), (unsigned)k, hv[i], status);
+        sink_put_warp<HASHED>(L, k != EMPTY_KEY, (unsigned)(k >> 32), (unsigned)k, hv[i], status);
     }
 }
 
@@ -1480,6 +1539,57 @@ static __global__ void __launch_bounds__(NTHR) k_chase(const Batch b, int2 *ends
             continue;
         }
         if (e != c0.x || q != c0.y) ends[j] = make_int2(e, e);
+    }
+}
+
+// The roots of every 3D tile's first face in x, y and z (the faces that
+// k_rag6 of the tile before it in that direction compares its last voxels
+// with), tile by tile: faces[t * kFaceN + j] with j = ly * TX + lx for the
+// z0 face, 512 + lz * TX + lx for the y0 face, 1024 + lz * TY + ly for the
+// x0 face; -1 outside the image.  One coalesced load per face voxel then
+// replaces k_rag6's chain of dependent loads (span, slot code, end).
+static constexpr int kFaceN = TT<6>::TX * TT<6>::TY + TT<6>::TX * TT<6>::TZ + TT<6>::TY * TT<6>::TZ;   // 1280
+static_assert(kFaceN * 4 == (int)kFaceBytes, "face roots per tile");
+
+static __global__ void __launch_bounds__(NTHR) k_faces(const Batch b, const uint16_t *__restrict__ code,
+                                                       const int2 *__restrict__ ends, const int2 *__restrict__ tends,
+                                                       int32_t *__restrict__ faces, DevStatus *status)
+{
+    using C = TC<6>;
+    constexpr int PT = (kFaceN + NTHR - 1) / NTHR;   // face voxels per thread and tile (5)
+    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+        const TileCtx tc = tile_ctx<6>(b, t);
+        const int2 te = tends[t];
+        int c[PT];
+#pragma unroll
+        for (int u = 0; u < PT; u++) {   // every slot code first, then every end: two rounds of loads
+            const int j = threadIdx.x + u * NTHR;
+            int lx, ly, lz;
+            if (j < C::TX * C::TY) {
+                lx = j % C::TX, ly = j / C::TX, lz = 0;
+            } else if (j < C::TX * C::TY + C::TX * C::TZ) {
+                const int q = j - C::TX * C::TY;
+                lx = q % C::TX, lz = q / C::TX, ly = 0;
+            } else {
+                const int q = j - C::TX * C::TY - C::TX * C::TZ;
+                ly = q % C::TY, lz = q / C::TY, lx = 0;
+            }
+            const int x = tc.x0 + lx, y = tc.y0 + ly, z = tc.z0 + lz;
+            c[u] = j < kFaceN && x < tc.geo.W && y < tc.geo.H && z < tc.geo.D
+                       ? __ldg(code + tc.base + (z * tc.geo.H + y) * tc.geo.W + x) & (C::NPIX - 1)
+                       : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < PT; u++) {
+            const int j = threadIdx.x + u * NTHR;
+            if (j >= kFaceN) break;
+            int r = -1;
+            if (c[u] >= 0) {
+                if (c[u] < te.y) r = __ldg(&ends[te.x + c[u]].x);
+                else record_error(status, DEV_NONCONVERGED, 15);   // only after an earlier device error
+            }
+            faces[(size_t)t * kFaceN + j] = r;
+        }
     }
 }
 
@@ -1556,7 +1666,8 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
                                                        const uint16_t *__restrict__ code,
                                                        const int2 *__restrict__ ends,
                                                        const int2 *__restrict__ tends, int32_t *mi,
-                                                       int do_rag, const EdgeSink L, DevStatus *status)
+                                                       int do_rag, const EdgeSink L, DevStatus *status,
+                                                       const int32_t *__restrict__ faces)
 {
     using C = TC<6>;
     using B = Rag6Box<T>;
@@ -1660,16 +1771,22 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
         const int fy = tid % C::TY, fz = tid / C::TY;
         const bool vz = col_in && hasz, vy = x < geo.W && hasy && z0 + ly < geo.D;
         const bool vx = tid < B::HX && hasx && y0 + fy < geo.H && z0 + fz < geo.D;
-        const int2 tez = vz ? __ldg(tends + t + ntx * nty) : make_int2(0, 0);
-        const int2 tey = vy ? __ldg(tends + t + ntx) : make_int2(0, 0);
-        const int2 tex = vx ? __ldg(tends + t + 1) : make_int2(0, 0);
-        constexpr int CM = C::NPIX - 1;   // slot bits of a code
-        const int cz = vz ? __ldg(code + base + ((z0 + C::TZ) * geo.H + y) * geo.W + x) & CM : 0;
-        const int cy = vy ? __ldg(code + base + ((z0 + ly) * geo.H + y0 + C::TY) * geo.W + x) & CM : 0;
-        const int cx = vx ? __ldg(code + base + ((z0 + fz) * geo.H + y0 + fy) * geo.W + x0 + C::TX) & CM : 0;
-        fzr = face_root(vz, cz, tez, ends, status);
-        fyr = face_root(vy, cy, tey, ends, status);
-        fxr = face_root(vx, cx, tex, ends, status);
+        if (faces) {   // the neighbouring tiles' first faces, listed by k_faces
+            fzr = vz ? __ldg(faces + (size_t)(t + ntx * nty) * kFaceN + tid) : -1;
+            fyr = vy ? __ldg(faces + (size_t)(t + ntx) * kFaceN + C::TX * C::TY + tid) : -1;
+            fxr = vx ? __ldg(faces + (size_t)(t + 1) * kFaceN + C::TX * C::TY + C::TX * C::TZ + tid) : -1;
+        } else {
+            const int2 tez = vz ? __ldg(tends + t + ntx * nty) : make_int2(0, 0);
+            const int2 tey = vy ? __ldg(tends + t + ntx) : make_int2(0, 0);
+            const int2 tex = vx ? __ldg(tends + t + 1) : make_int2(0, 0);
+            constexpr int CM = C::NPIX - 1;   // slot bits of a code
+            const int cz = vz ? __ldg(code + base + ((z0 + C::TZ) * geo.H + y) * geo.W + x) & CM : 0;
+            const int cy = vy ? __ldg(code + base + ((z0 + ly) * geo.H + y0 + C::TY) * geo.W + x) & CM : 0;
+            const int cx = vx ? __ldg(code + base + ((z0 + fz) * geo.H + y0 + fy) * geo.W + x0 + C::TX) & CM : 0;
+            fzr = face_root(vz, cz, tez, ends, status);
+            fyr = face_root(vy, cy, tey, ends, status);
+            fxr = face_root(vx, cx, tex, ends, status);
+        }
     }
     rh_insert(rown);
     for (int i = tid + C::NT; i < te.y; i += C::NT) rh_insert(__ldg(&ends[te.x + i].x));
@@ -1706,7 +1823,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
             atomicMin(pm + a * B::RM + c2, h);
         } else {
             const int ra = mode < 2 ? rl[ida] : ida, rb = mode < 2 ? rl[idb] : idb;
-            smem_edge_insert((unsigned)(ra < rb ? ra : rb), (unsigned)(ra < rb ? rb : ra), h, hk, hv, B::EH, L,
+            smem_edge_insert<true>((unsigned)(ra < rb ? ra : rb), (unsigned)(ra < rb ? rb : ra), h, hk, hv, B::EH, L,
                              status);
         }
     };
@@ -1780,7 +1897,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
                         if (h < *e) atomicMin(e, h);
                     } else {
                         const int ra = rl[a], rb = rl[c2];
-                        smem_edge_insert((unsigned)(ra < rb ? ra : rb), (unsigned)(ra < rb ? rb : ra), h, hk, hv,
+                        smem_edge_insert<true>((unsigned)(ra < rb ? ra : rb), (unsigned)(ra < rb ? rb : ra), h, hk, hv,
                                          B::EH, L, status);
                     }
                 };
@@ -1903,12 +2020,12 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
                 lo = (unsigned)(ra < rb ? ra : rb);
                 hi = (unsigned)(ra < rb ? rb : ra);
             }
-            sink_put_warp(L, have, lo, hi, h, status);
+            sink_put_warp<true>(L, have, lo, hi, h, status);
         }
     } else {
         for (int i = tid; i < B::EH; i += C::NT) {
             const unsigned long long k = hk[i];
-            sink_put_warp(L, k != EMPTY_KEY, (unsigned)(k >> 32), (unsigned)k, hv[i], status);
+            sink_put_warp<true>(L, k != EMPTY_KEY, (unsigned)(k >> 32), (unsigned)k, hv[i], status);
         }
     }
 }
@@ -2040,6 +2157,7 @@ static __global__ void __launch_bounds__(NTHR) k_write_batch(const Batch b, cons
         }
     }
 }
+
 
 // 3D label write, one CTA per tile: every voxel's canonical id and its id on
 // each waterfall level, from its 16-bit end slot and a per-tile table (slot

@@ -23,7 +23,8 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 3, 4), (8, 8, 32), (9, 17, 33), (20, 30, 70), (5, 64, 100)])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 3, 4), (8, 8, 32), (9, 17, 33), (20, 30, 70), (5, 64, 100),
+                                   (65, 17, 40), (128, 40, 31), (130, 9, 33)])   # several 64-plane chunks
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
 def test_random_volumes(ctx, shape, dtype):
     rng = np.random.default_rng(sum(shape))
