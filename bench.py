@@ -54,7 +54,7 @@ FALLBACK_HBM_GBS = 6800.0
 # Algorithmic bytes per voxel of each phase (minimal input + output of the
 # function the phase computes; b = 2 bytes per uint16 sample).
 PHASE_BYTES = {
-    "step1": 2 + 4 + 2,          # k_init6: read G, write the arrow (par) and the 16-bit end slot
+    "step1": 2 + 2,              # k_init6: read G, write the 16-bit end slot (+ 8 B per path end, ~5% of voxels)
     "rag": 2 + 2,                # k_rag6: read end slots and G (per-basin and per-pair results only)
     "level_write": 2 + 4 * NL,   # k_write6: read end slots, write NL label planes
     "plateau": 2 + 4,            # k_plateau2 (plateau tiles only)
@@ -412,6 +412,32 @@ def run_small_configs(ctx, torch, reps=20):
     return out
 
 
+def run_gradient3d(ctx, torch, vol_d, peak, reps=10):
+    """The 3D gradient (5x5x5 binomial blur, 3x3x3 Sobel, exact isqrt) of the
+    headline volume: 2 B in + 2 B out per voxel; median of `reps` CUDA-event
+    timings after three warm-up runs (input and output larger than L2)."""
+    import statistics
+    out = torch.empty_like(vol_d)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        ctx.gradient3d(vol_d, 0, out=out)
+    ts = []
+    for _ in range(reps):
+        e0.record(stream)
+        ctx.gradient3d(vol_d, 0, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ctx.check()
+    n = vol_d.numel()
+    med = statistics.median(ts)
+    del out
+    return {"workload": f"3D gradient of the {'x'.join(str(d) for d in reversed(vol_d.shape))} uint16 volume: "
+                        "5x5x5 binomial blur, 3x3x3 Sobel, exact isqrt, uint16 out", "ms_median": med,
+            "gvox_s": n / med / 1e6, "alg_hbm_frac": 4 * n / (med / 1e3) / 1e9 / peak}
+
+
 def run_batch(ctx, binding, torch, n=512, NL=6, conn=4, reps=3):
     """Config 3: n 2D uint8 images, sides log-uniform in [64, 2048], as one
     CUDA-graph replay of the batched pipeline vs n per-image ws_segment calls,
@@ -765,6 +791,7 @@ def main():
         del levels_d
         torch.cuda.empty_cache()
         if not args.no_small:
+            line["gradient3d_full"] = run_gradient3d(ctx, torch, grad_d, peak)
             line["small_configs"] = run_small_configs(ctx, torch)
         if not args.no_batch:
             line["batch"] = run_batch(ctx, binding, torch)

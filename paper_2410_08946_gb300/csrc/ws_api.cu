@@ -297,18 +297,6 @@ ws_status ensure_plist(ws_context *c, size_t N, size_t ntiles)
     return WS_OK;
 }
 
-ws_status ensure_faces(ws_context *c, size_t ntiles)
-{
-    Workspace &w = c->w;
-    if (ntiles <= w.nfaces) return WS_OK;
-    const size_t have = w.nfaces;
-    dfree(c, &w.faces, w.nfaces * kFaceBytes);
-    w.nfaces = grown(c, ntiles, have, false, kFaceBytes);
-    ws_status st = dalloc(c, &w.faces, w.nfaces * kFaceBytes);
-    if (st) w.nfaces = 0;
-    return st;
-}
-
 // Region-graph export arrays: K regions (node sizes and CSR row starts), `sums`
 // value sums, `entries` directed edge entries (two key/value buffers for the
 // radix sort, digit counts of 4096-entry tiles).
@@ -391,7 +379,6 @@ size_t workspace_bound(size_t npix, size_t ntiles, size_t nimg, int conn, int NL
 {
     size_t b = npix * 17 + ntiles * 7 + 4096;                      // per-pixel and per-tile arrays
     if (conn == 6) b += npix * 10 + ntiles * 8;                    // 3D slot codes, path ends, slot spans
-    if (conn == 6 && NL > 1) b += ntiles * kFaceBytes;             // 3D face roots
     if (conn == 4 || conn == 8) b += npix * 2 + ntiles * 8;        // 2D plateau pixel lists
     if (nimg > 1) b += nimg * (kDescBytes + 4);                    // batch descriptors
     if (NL > 1) {
@@ -422,8 +409,6 @@ void release_workspace(ws_context *c)
     w.ntends = 0;
     dfree(c, &w.plist, w.nplist * 2);
     w.nplist = 0;
-    dfree(c, &w.faces, w.nfaces * kFaceBytes);
-    w.nfaces = 0;
     dfree(c, &w.pspan, w.npspan * 8);
     w.npspan = 0;
     dfree(c, &w.keys, w.edge_cap * 8);
@@ -577,7 +562,7 @@ void ws_context_destroy(ws_context *c)
                     w.counters, w.bitmap, w.gcnt, w.csum,   w.keys,   w.vals,   w.slots,  w.ecount,
                     w.gmap,  w.newmin, w.uf,     w.rank,   w.bsum,   w.kcount, w.grad_stage, w.levels_stage,
                     w.counts_stage, w.descs, w.rbase, w.lcount, w.ea, w.eb, w.ecnt, w.code, w.ends, w.tends,
-                    w.plist, w.pspan, w.faces};
+                    w.plist, w.pspan};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     const Workspace::RGraph &r = w.rg;

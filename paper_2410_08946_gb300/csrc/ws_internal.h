@@ -45,8 +45,6 @@ struct Workspace {
     uint16_t *code = nullptr;     // [ncode]
     int2 *ends = nullptr;         // [ncode]
     int2 *tends = nullptr;        // (first slot, slot count) per tile  [ntends]
-    size_t nfaces = 0;
-    int32_t *faces = nullptr;     // roots of every tile's first x, y, z faces [nfaces * 1280]
     // 2D path: the plateau pixels of every tile (tile-local indices), per tile
     // the span of its entries in plist
     size_t nplist = 0, npspan = 0;
@@ -170,9 +168,6 @@ constexpr int kMaxLevels = 64;
 // Bytes reserved per image descriptor of a batch (>= sizeof(ImgDesc)).
 constexpr size_t kDescBytes = 128;
 
-// Bytes of face roots per 3D tile (k_faces): 32 x 16 + 32 x 16 + 16 x 16 int32.
-constexpr size_t kFaceBytes = 1280 * 4;
-
 // Effective tuning values.
 int tune_plateau_cap(const ws_context *c);
 int tune_jump_cap(const ws_context *c);
@@ -189,7 +184,7 @@ ws_status ensure_regions(ws_context *c, size_t kmax, int levels);
 ws_status ensure_batch(ws_context *c, size_t n);
 ws_status ensure_ends(ws_context *c, size_t N, size_t ntiles);
 ws_status ensure_plist(ws_context *c, size_t N, size_t ntiles);
-ws_status ensure_faces(ws_context *c, size_t ntiles);
+
 ws_status ensure_rgraph(ws_context *c, size_t K, size_t sums, size_t entries);
 ws_status ensure_rec(ws_context *c, size_t bytes);
 // Region-table slots of a call over npix pixels (c: the context's tuning, or nullptr).

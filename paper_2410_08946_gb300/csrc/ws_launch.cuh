@@ -208,16 +208,10 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
     elist.slots = w.slots;
     elist.ecount = w.ecount;
     elist.gmask = w.edge_cap ? w.edge_cap - 1 : 0;
-    if constexpr (CONN == 6) {  // 3D: roots of the tiles' path ends (and of their first faces)
-        if (do_rag && (st = ensure_faces(c, b.ntiles)) != WS_OK) return st;
+    if constexpr (CONN == 6) {  // 3D: roots of the tiles' path ends
         PhaseScope pc(c, PH_CHASE, s);
         k_chase<<<c->num_sms * 8, NTHR, 0, s>>>(b, w.ends, w.tends, w.code, w.counters, c->status);
         c->launches += 1;
-        if (do_rag) {
-            k_faces<<<b.ntiles < c->num_sms * 16 ? b.ntiles : c->num_sms * 16, NTHR, 0, s>>>(b, w.code, w.ends, w.tends,
-                                                                                           w.faces, c->status);
-            c->launches += 1;
-        }
     }
     {
         PhaseScope ps(c, PH_RAG, s);
@@ -240,7 +234,7 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
             auto kern = tma6 ? k_rag6<T, true> : k_rag6<T, false>;
             if ((e = allow_smem(kern, B6::SMEM)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
             kern<<<b.ntiles, C::NT, B6::SMEM, s>>>(tmc, tmg, b, w.code, w.ends, w.tends, w.aux, do_rag ? 1 : 0, elist,
-                                                   c->status, do_rag ? (const int32_t *)w.faces : nullptr);
+                                                   c->status);
         } else if (tma) {
             if ((e = allow_smem(k_label<T, CONN, true>, B::SMEM)) != cudaSuccess)
                 return set_cuda_error(c, e, "smem attribute");

@@ -900,8 +900,11 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const Batch b, int32_
                     const int q = (z * geo.H + y) * geo.W + x;
                     gs[i] = (int)g[q];
                     // a pixel of a tile without plateau pixels that is equal to a
-                    // plateau neighbour has a lower neighbour: distance 0
-                    ds[i] = plat[tc.tile0 + tile_of_c<CONN>(tc.tg, x, y, z)] ? __ldcg(dist + tc.base + q) : 0;
+                    // plateau neighbour has a lower neighbour: distance 0 (the
+                    // tile's own pixels need no look-up: it is a plateau tile)
+                    const bool own = hx >= 1 && hx <= C::TX && hy >= 1 && hy <= C::TY &&
+                                     (!C::D3 || (hz >= 1 && hz <= C::TZ));
+                    ds[i] = own || plat[tc.tile0 + tile_of_c<CONN>(tc.tg, x, y, z)] ? __ldcg(dist + tc.base + q) : 0;
                 } else {
                     gs[i] = -1;
                     ds[i] = INF_D;
@@ -1480,10 +1483,38 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_label(const __grid_constant__ 
     if (!do_rag) return;
     __syncthreads();
     static_assert(C::HASH % C::NT == 0, "warp-uniform flush");
-    for (int i0 = 0; i0 < C::HASH; i0 += C::NT) {
-        const int i = i0 + tid;
+    if (HASHED) {
+        for (int i0 = 0; i0 < C::HASH; i0 += C::NT) {
+            const int i = i0 + tid;
+            const unsigned long long k = hk[i];
+            sink_put_warp<true>(L, k != EMPTY_KEY, (unsigned)(k >> 32), (unsigned)k, hv[i], status);
+        }
+        return;
+    }
+    // the list: the tile's pairs take one span of it (one global atomic per
+    // tile; each warp's entries are placed by a shared atomic per pass)
+    constexpr int NP = C::HASH / C::NT;
+    __shared__ int s_n, s_base;
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+    int off[NP];
+    unsigned msk[NP];
+#pragma unroll
+    for (int u = 0; u < NP; u++) {
+        msk[u] = __ballot_sync(0xffffffffu, hk[u * C::NT + tid] != EMPTY_KEY);
+        int o = 0;
+        if (lane == 0 && msk[u]) o = atomicAdd(&s_n, __popc(msk[u]));
+        off[u] = __shfl_sync(0xffffffffu, o, 0) + __popc(msk[u] & ((1u << lane) - 1u));
+    }
+    __syncthreads();
+    if (tid == 0) s_base = s_n ? atomicAdd(L.n, s_n) : 0;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NP; u++) {
+        if (!((msk[u] >> lane) & 1u)) continue;
+        const int i = u * C::NT + tid;
         const unsigned long long k = hk[i];
-        sink_put_warp<HASHED>(L, k != EMPTY_KEY, (unsigned)(k >> 32), (unsigned)k, hv[i], status);
+        list_put(L, s_base + off[u], (unsigned)(k >> 32), (unsigned)k, hv[i], status);
     }
 }
 
@@ -1539,57 +1570,6 @@ static __global__ void __launch_bounds__(NTHR) k_chase(const Batch b, int2 *ends
             continue;
         }
         if (e != c0.x || q != c0.y) ends[j] = make_int2(e, e);
-    }
-}
-
-// The roots of every 3D tile's first face in x, y and z (the faces that
-// k_rag6 of the tile before it in that direction compares its last voxels
-// with), tile by tile: faces[t * kFaceN + j] with j = ly * TX + lx for the
-// z0 face, 512 + lz * TX + lx for the y0 face, 1024 + lz * TY + ly for the
-// x0 face; -1 outside the image.  One coalesced load per face voxel then
-// replaces k_rag6's chain of dependent loads (span, slot code, end).
-static constexpr int kFaceN = TT<6>::TX * TT<6>::TY + TT<6>::TX * TT<6>::TZ + TT<6>::TY * TT<6>::TZ;   // 1280
-static_assert(kFaceN * 4 == (int)kFaceBytes, "face roots per tile");
-
-static __global__ void __launch_bounds__(NTHR) k_faces(const Batch b, const uint16_t *__restrict__ code,
-                                                       const int2 *__restrict__ ends, const int2 *__restrict__ tends,
-                                                       int32_t *__restrict__ faces, DevStatus *status)
-{
-    using C = TC<6>;
-    constexpr int PT = (kFaceN + NTHR - 1) / NTHR;   // face voxels per thread and tile (5)
-    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
-        const TileCtx tc = tile_ctx<6>(b, t);
-        const int2 te = tends[t];
-        int c[PT];
-#pragma unroll
-        for (int u = 0; u < PT; u++) {   // every slot code first, then every end: two rounds of loads
-            const int j = threadIdx.x + u * NTHR;
-            int lx, ly, lz;
-            if (j < C::TX * C::TY) {
-                lx = j % C::TX, ly = j / C::TX, lz = 0;
-            } else if (j < C::TX * C::TY + C::TX * C::TZ) {
-                const int q = j - C::TX * C::TY;
-                lx = q % C::TX, lz = q / C::TX, ly = 0;
-            } else {
-                const int q = j - C::TX * C::TY - C::TX * C::TZ;
-                ly = q % C::TY, lz = q / C::TY, lx = 0;
-            }
-            const int x = tc.x0 + lx, y = tc.y0 + ly, z = tc.z0 + lz;
-            c[u] = j < kFaceN && x < tc.geo.W && y < tc.geo.H && z < tc.geo.D
-                       ? __ldg(code + tc.base + (z * tc.geo.H + y) * tc.geo.W + x) & (C::NPIX - 1)
-                       : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < PT; u++) {
-            const int j = threadIdx.x + u * NTHR;
-            if (j >= kFaceN) break;
-            int r = -1;
-            if (c[u] >= 0) {
-                if (c[u] < te.y) r = __ldg(&ends[te.x + c[u]].x);
-                else record_error(status, DEV_NONCONVERGED, 15);   // only after an earlier device error
-            }
-            faces[(size_t)t * kFaceN + j] = r;
-        }
     }
 }
 
@@ -1666,8 +1646,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
                                                        const uint16_t *__restrict__ code,
                                                        const int2 *__restrict__ ends,
                                                        const int2 *__restrict__ tends, int32_t *mi,
-                                                       int do_rag, const EdgeSink L, DevStatus *status,
-                                                       const int32_t *__restrict__ faces)
+                                                       int do_rag, const EdgeSink L, DevStatus *status)
 {
     using C = TC<6>;
     using B = Rag6Box<T>;
@@ -1771,22 +1750,16 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
         const int fy = tid % C::TY, fz = tid / C::TY;
         const bool vz = col_in && hasz, vy = x < geo.W && hasy && z0 + ly < geo.D;
         const bool vx = tid < B::HX && hasx && y0 + fy < geo.H && z0 + fz < geo.D;
-        if (faces) {   // the neighbouring tiles' first faces, listed by k_faces
-            fzr = vz ? __ldg(faces + (size_t)(t + ntx * nty) * kFaceN + tid) : -1;
-            fyr = vy ? __ldg(faces + (size_t)(t + ntx) * kFaceN + C::TX * C::TY + tid) : -1;
-            fxr = vx ? __ldg(faces + (size_t)(t + 1) * kFaceN + C::TX * C::TY + C::TX * C::TZ + tid) : -1;
-        } else {
-            const int2 tez = vz ? __ldg(tends + t + ntx * nty) : make_int2(0, 0);
-            const int2 tey = vy ? __ldg(tends + t + ntx) : make_int2(0, 0);
-            const int2 tex = vx ? __ldg(tends + t + 1) : make_int2(0, 0);
-            constexpr int CM = C::NPIX - 1;   // slot bits of a code
-            const int cz = vz ? __ldg(code + base + ((z0 + C::TZ) * geo.H + y) * geo.W + x) & CM : 0;
-            const int cy = vy ? __ldg(code + base + ((z0 + ly) * geo.H + y0 + C::TY) * geo.W + x) & CM : 0;
-            const int cx = vx ? __ldg(code + base + ((z0 + fz) * geo.H + y0 + fy) * geo.W + x0 + C::TX) & CM : 0;
-            fzr = face_root(vz, cz, tez, ends, status);
-            fyr = face_root(vy, cy, tey, ends, status);
-            fxr = face_root(vx, cx, tex, ends, status);
-        }
+        const int2 tez = vz ? __ldg(tends + t + ntx * nty) : make_int2(0, 0);
+        const int2 tey = vy ? __ldg(tends + t + ntx) : make_int2(0, 0);
+        const int2 tex = vx ? __ldg(tends + t + 1) : make_int2(0, 0);
+        constexpr int CM = C::NPIX - 1;   // slot bits of a code
+        const int cz = vz ? __ldg(code + base + ((z0 + C::TZ) * geo.H + y) * geo.W + x) & CM : 0;
+        const int cy = vy ? __ldg(code + base + ((z0 + ly) * geo.H + y0 + C::TY) * geo.W + x) & CM : 0;
+        const int cx = vx ? __ldg(code + base + ((z0 + fz) * geo.H + y0 + fy) * geo.W + x0 + C::TX) & CM : 0;
+        fzr = face_root(vz, cz, tez, ends, status);
+        fyr = face_root(vy, cy, tey, ends, status);
+        fxr = face_root(vx, cx, tex, ends, status);
     }
     rh_insert(rown);
     for (int i = tid + C::NT; i < te.y; i += C::NT) rh_insert(__ldg(&ends[te.x + i].x));
