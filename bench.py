@@ -487,6 +487,7 @@ def run_batch(ctx, binding, torch, n=512, NL=6, conn=4, reps=3):
     ctx.segment_batch(grads, conn, NL, [o[0] for o in outs], [o[1] for o in outs])
     ctx.check()
     phases = {k: round(v[0], 4) for k, v in ctx.phase_times().items() if v[1]}
+    counts = ctx.counters()
     ctx.set_profiling(False)
     ctx.set_tuning()
     return {"workload": f"{n} 2D uint8 crops of a 4096^2 blob gradient, sides log-uniform [64, 2048], "
@@ -494,6 +495,7 @@ def run_batch(ctx, binding, torch, n=512, NL=6, conn=4, reps=3):
             "batched_graph_ms": ms_graph, "batched_gvox_s": npx / ms_graph / 1e6,
             "per_image_ms": ms_single, "per_image_gvox_s": npx / ms_single / 1e6,
             "speedup": ms_single / ms_graph, "identical": bool(same), "phases_ms_eager": phases,
+            "device_counts": counts,
             "autotune": {"params": tuned["params"], "tile_shape": autotune.SHAPES[tuned["params"]["tile_shape"]],
                          "eager_ms": tuned["ms"], "eager_ms_defaults": default_ms,
                          "candidates": len(tuned["table"])}}
@@ -763,6 +765,7 @@ def main():
                               "unit": "GB/s", "frac": path_achieved / peak},
             "path_dram": path_dram(N, ms, peak),
             "phases_ms": {k: round(v, 4) for k, v in per_step.items()},
+            "device_counts": ctx.counters(),
             "gpu_launches": launches, "clocks": clocks}
 
     if not args.no_e2e:

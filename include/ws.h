@@ -146,6 +146,21 @@ ws_status ws_context_phase_times(ws_context *ctx, double *total_ms, long long *c
 /* Number of CUDA kernels this context has enqueued since it was created. */
 unsigned long long ws_context_launches(const ws_context *ctx);
 
+/* Counts the device kept for the last watershed call of this context (for a
+ * batch: over all its images), after waiting for `stream`.  out[0..n) gets,
+ * in this order (as many as n asks for, at most WS_NUM_COUNTERS):
+ *   0  global rounds of the step II distance relaxation (Alg. 3's fixpoint)
+ *   1  global rounds of step III pointer jumping on plateau tiles
+ *   2  level-0 edge records of the waterfall (pairs of adjacent basins; a 2D
+ *      call lists a pair once per tile that sees it)
+ *   3  K0, the basins of level 0
+ *   4  3D 6-connectivity: in-tile path ends chased across tiles
+ *   5  tiles that hold plateau pixels
+ *   6  2D: plateau pixels (states 2 and 3 of Eq. 1)
+ * Returns WS_ERR_INVALID for a NULL context or out. */
+#define WS_NUM_COUNTERS 7
+ws_status ws_context_counters(ws_context *ctx, ws_stream_t stream, int64_t *out, int n);
+
 /* ------------------------------------------------------------------------ */
 /* hot path                                                                  */
 /* ------------------------------------------------------------------------ */

@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
             "ws_phase_name": ([I], ctypes.c_char_p),
             "ws_context_phase_times": ([P, P, P, I], I),
             "ws_context_launches": ([P], ctypes.c_ulonglong),
+            "ws_context_counters": ([P, P, P, I], I),
             "ws_segment_batch": ([P, I, ctypes.POINTER(ws_item), I, I, I, P], I),
             "ws_graph_create": ([P, I, ctypes.POINTER(ws_item), I, I, I, P, ctypes.POINTER(P)], I),
             "ws_graph_launch": ([P, P], I),
@@ -214,6 +215,15 @@ class Context:
     def launches(self) -> int:
         """Kernels this context has enqueued so far."""
         return int(self.lib.ws_context_launches(self.handle))
+
+    COUNTERS = ("plateau_rounds", "jump_rounds", "edge_records", "basins", "path_ends", "plateau_tiles",
+                "plateau_pixels")
+
+    def counters(self, stream=None) -> dict:
+        """The device's counts for the last watershed call (waits for the stream)."""
+        out = (ctypes.c_int64 * len(self.COUNTERS))()
+        self._ok(self.lib.ws_context_counters(self.handle, _stream(stream), out, len(self.COUNTERS)))
+        return dict(zip(self.COUNTERS, (int(v) for v in out)))
 
     # -- entry points -------------------------------------------------------
     def gradient(self, img, quant_shift: int = 0, out=None, stream=None):

@@ -651,6 +651,20 @@ ws_status ws_context_phase_times(ws_context *c, double *total_ms, long long *cal
 
 unsigned long long ws_context_launches(const ws_context *c) { return c ? c->launches : 0; }
 
+ws_status ws_context_counters(ws_context *c, ws_stream_t stream, int64_t *out, int n)
+{
+    if (!c || !out) return WS_ERR_INVALID;
+    DevStatus st{};
+    int32_t cnt[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&st, c->status, sizeof st, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && c->w.counters) e = cudaMemcpy(cnt, c->w.counters, sizeof cnt, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_cuda_error(c, e, "counters");
+    const int64_t v[WS_NUM_COUNTERS] = {st.rounds_plateau, st.rounds_jump, st.edges, cnt[1], cnt[2], cnt[0], cnt[3]};
+    for (int i = 0; i < n && i < WS_NUM_COUNTERS; i++) out[i] = v[i];
+    return WS_OK;
+}
+
 ws_status ws_context_set_tuning(ws_context *c, const ws_tuning *t)
 {
     if (!c || !t) return WS_ERR_INVALID;

@@ -660,27 +660,45 @@ static __global__ void __launch_bounds__(NTHR) k_levels(Edge *e0, Edge *e1, int3
             gout[c] = __ldcg(lab + A);
         }
         if (k + 2 < NL) {
-            for (int e0i = blockIdx.x * NTHR; e0i < E; e0i += gsz) {
-                const int e = e0i + tid;
-                bool keep = false;
+            // the edges between different level-(k+1) regions, relabelled; each
+            // block compacts one contiguous range of the list (counted first, so
+            // that it takes its span of the next list with one atomic), in order
+            auto next_edge = [&](int e, Edge &ne) -> bool {
+                const Edge ed = ld_edge(cur + e);
+                if (ed.a == ed.b) return false;
+                const int A = __ldcg(lab + ed.a), B = __ldcg(lab + ed.b);
+                if (A == B) return false;
+                ne.a = A < B ? A : B;
+                ne.b = A < B ? B : A;
+                ne.h = ed.h;
+                return true;
+            };
+            const int per = (E + (int)gridDim.x - 1) / (int)gridDim.x;
+            const int r0 = min(E, (int)blockIdx.x * per), r1 = min(E, r0 + per);
+            int cnt = 0;
+            for (int e = r0 + tid; e < r1; e += NTHR) {
+                Edge ne;
+                cnt += next_edge(e, ne) ? 1 : 0;
+            }
+            const int tot = block_sum(cnt, red);
+            if (tid == 0) carry = tot ? atomicAdd(ecnt + k + 1, tot) : 0;
+            __syncthreads();
+            int pos = carry;
+            for (int e0 = r0; e0 < r1; e0 += NTHR) {   // trip count uniform in the block
+                const int e = e0 + tid;
                 Edge ne{0, 0, 0};
-                if (e < E) {
-                    const Edge ed = ld_edge(cur + e);
-                    if (ed.a != ed.b) {
-                        const int A = __ldcg(lab + ed.a), B = __ldcg(lab + ed.b);
-                        if (A != B) {
-                            keep = true;
-                            ne.a = A < B ? A : B;
-                            ne.b = A < B ? B : A;
-                            ne.h = ed.h;
-                        }
-                    }
-                }
+                const bool keep = e < r1 && next_edge(e, ne);
                 const unsigned bl = __ballot_sync(0xffffffffu, keep);
-                int base = 0;
-                if (lane == 0 && bl) base = atomicAdd(ecnt + k + 1, __popc(bl));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (keep) nxt[base + __popc(bl & ((1u << lane) - 1u))] = ne;
+                if (lane == 0) red[wid] = __popc(bl);
+                __syncthreads();
+                int o = pos, all_w = 0;
+                for (int w = 0; w < NTHR / 32; w++) {
+                    if (w < wid) o += red[w];
+                    all_w += red[w];
+                }
+                if (keep) nxt[o + __popc(bl & ((1u << lane) - 1u))] = ne;
+                pos += all_w;
+                __syncthreads();
             }
         }
         Kk = all;

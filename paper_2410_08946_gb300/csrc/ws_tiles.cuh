@@ -366,6 +366,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[2];
     __shared__ int s_pc, s_pbase;   // the tile's plateau pixels, their first entry in plist
+    __shared__ int s_rc, s_rbase;   // the tile's strict minima, their first entry in roots
     int *nx = (int *)(smem + (TMA ? 2 : 1) * B::STAGE);
     uint16_t *sp = (uint16_t *)(nx + C::NPIX);   // the tile's plateau pixels, staged (LIST)
     const int tid = threadIdx.x, lane = tid & 31;
@@ -391,7 +392,10 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
         const Geo &geo = tc.geo;
         const int x0 = tc.x0, y0 = tc.y0, z0 = tc.z0, base = tc.base;
         const T *g = (const T *)tc.grad;
-        if (LIST && tid == 0) s_pc = 0;   // (ordered before the appends by the barrier below)
+        if (tid == 0) {   // (ordered before the appends by the barrier below)
+            s_pc = 0;
+            s_rc = 0;
+        }
         if (TMA) {
             const bool ok = mbar_wait(&bars[s], (unsigned)((j >> 1) & 1), status);
             if (__syncthreads_or(!ok)) return;
@@ -446,12 +450,33 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
             off = __shfl_sync(0xffffffffu, off, 31) + inc - np;
             for (; pm; pm &= pm - 1) sp[off++] = (uint16_t)(tid + (__ffs(pm) - 1) * C::NT);
         }
+        // the strict minima are roots: the thread's place in the tile's span of
+        // the root list (one global atomic per tile, taken below)
+        unsigned rm = 0;
+#pragma unroll
+        for (int k = 0; k < C::PER; k++) rm |= (unsigned)(st[k] == ST1) << k;
+        int roff = 0;
+        if (__any_sync(0xffffffffu, rm)) {
+            const int nr = __popc(rm);
+            int inc = nr;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += u;
+            }
+            int wo = 0;
+            if (lane == 31) wo = atomicAdd(&s_rc, inc);
+            roff = __shfl_sync(0xffffffffu, wo, 31) + inc - nr;
+        }
         __syncthreads();  // the gradient box of stage s is no longer read
         if (TMA && tid == 0 && t + 2 * G < b.ntiles)
             init_issue<T, CONN, TMA>(&tm, gs, &bars[s], b, t + 2 * G);
-        if (LIST && tid == 0 && s_pc > 0) {   // the tile's span of plist (read after the next barrier)
-            s_pbase = atomicAdd(counters + CNT_PLIST, s_pc);
-            pspan[t] = make_int2(s_pbase, s_pc);
+        if (tid == 0) {   // the tile's spans (read after the next barrier)
+            if (LIST && s_pc > 0) {
+                s_pbase = atomicAdd(counters + CNT_PLIST, s_pc);
+                pspan[t] = make_int2(s_pbase, s_pc);
+            }
+            if (s_rc > 0) s_rbase = atomicAdd(counters + CNT_ROOTS, s_rc);
         }
 
         // step III inside the tile: pointer doubling through shared memory
@@ -489,20 +514,11 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
             par[p] = e < 0 ? dec_final(e) : p;  // e >= 0 does not survive the doubling
             if (st[k] != ST0) mi[p] = 0x7fffffff;
         }
-        // list the strict minima (roots known now)
-#pragma unroll
-        for (int k = 0; k < C::PER; k++) {
-            const bool isr = st[k] == ST1;
-            const unsigned bb = __ballot_sync(0xffffffffu, isr);
-            if (!bb) continue;
-            int rb = 0;
-            if (lane == 0) rb = atomicAdd(counters + CNT_ROOTS, __popc(bb));
-            rb = __shfl_sync(0xffffffffu, rb, 0);
-            if (isr) {
-                const int i = tid + k * C::NT;
-                const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
-                roots[rb + __popc(bb & ((1u << lane) - 1u))] = base + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
-            }
+        // list the strict minima in the tile's span
+        for (int rp = s_rbase + roff; rm; rm &= rm - 1) {
+            const int i = tid + (__ffs(rm) - 1) * C::NT;
+            const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+            roots[rp++] = base + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx;
         }
         // dist: on plateau tiles the start of step II; in 2D on every tile
         // (k_jump2 tells plateau pixels from the others by it)
@@ -526,8 +542,8 @@ __global__ void __launch_bounds__(TT<CONN>::NT, CONN == 26 ? 2 : 1)
         } else if (tid == 0) {
             plat[t] = 0;
         }
-        // (the __syncthreads_or above also orders this tile's nx, sp and s_pc
-        // reads before the next tile's writes)
+        // (the __syncthreads_or above also orders this tile's nx, sp, s_pc and
+        // s_rbase reads before the next tile's writes)
     }
 }
 
