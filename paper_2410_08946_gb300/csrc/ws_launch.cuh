@@ -233,6 +233,10 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
             }
             auto kern = tma6 ? k_rag6<T, true> : k_rag6<T, false>;
             if ((e = allow_smem(kern, B6::SMEM)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
+            // three CTAs per SM need all of the SM's unified memory as shared memory
+            if ((e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+                return set_cuda_error(c, e, "smem carveout");
             kern<<<b.ntiles, C::NT, B6::SMEM, s>>>(tmc, tmg, b, w.code, w.ends, w.tends, w.aux, do_rag ? 1 : 0, elist,
                                                    c->status);
         } else if (tma) {

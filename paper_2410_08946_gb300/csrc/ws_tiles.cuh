@@ -27,10 +27,12 @@
 // 3D volumes with 6-connectivity take a variant of this pipeline with one z
 // column of the tile per thread:
 //   k_init6     as k_init, and numbers the tile's in-tile path ends (slots):
-//               per pixel the 16-bit slot of its end, per tile the list of
-//               its end pixels; par holds the arrow of Eq. 1
-//   k_chase     the root of every listed end, following par out of the
-//               tile and the slot codes through the next tiles
+//               per pixel a 16-bit code (the slot of its end), per tile the
+//               list of its end pixels, each with the next pixel of its path
+//               (the arrow of Eq. 1 out of the tile); par holds the arrows
+//               on plateau tiles only
+//   k_chase     the root of every listed end, following the next pixels
+//               and the slot codes through the next tiles
 //   k_rag6      per tile: roots by slot lookup, smallest index per basin,
 //               and Alg. 5 step V from per-warp lists of boundary pixels
 //   k_rank_*    canonical ids: rank of every basin's smallest pixel index
@@ -1590,11 +1592,13 @@ static __global__ void __launch_bounds__(NTHR) k_chase(const Batch b, int2 *ends
 }
 
 // Shared-memory layout of k_rag6: the roots (then basin ids) of the +x, +y,
-// +z face pixels of the neighbouring tiles, the basin id of every slot of the
-// tile, the tile's basin list and its hash, the smallest index per basin,
-// the basin-pair pass matrix, the edge hash for crowded tiles, then the
-// slot-code box and the gradient box of the tile and its forward faces (x
-// from x0, rows padded to 16-byte multiples).
+// +z face pixels of the neighbouring tiles, the tile's basin list and its
+// hash, the smallest index per basin; one region that holds first the basin
+// id of every slot of the tile, then the basin-pair pass matrix (or the edge
+// hash of a crowded tile); the packed ids of every column; then the
+// slot-code box (later the warps' lists of boundary pixels) and the gradient
+// box of the tile and its forward faces (x from x0, rows padded to 16-byte
+// multiples).  74,752 bytes for uint16 (three CTAs per SM).
 template <typename T> struct Rag6Box {
     using C = TC<6>;
     static constexpr int BY = C::TY + 1, BZ = C::TZ + 1;
@@ -1606,26 +1610,31 @@ template <typename T> struct Rag6Box {
     static constexpr int RB = 253;        // basins a tile can number (ids 0..RB-1)
     static constexpr int RH = 512;        // basin hash slots
     static constexpr int RM = 64;         // basins of the pass matrix
+    static constexpr int PMN = 2048;      // pass matrix entries: pairs a < c of RM ids (2016), padded
     static constexpr int EH = 512;        // edge hash slots (tiles with more than RM basins)
+    static constexpr int WL = C::TX * C::TZ;                  // boundary items per warp (every pixel)
+    static constexpr int WLBYTES = (C::NT / 32) * WL * 2;
     static constexpr int OFF_HR = 0;                          // int32 [NH]
-    static constexpr int OFF_SS = OFF_HR + NH * 4;            // uint8 [NPIX]
-    static constexpr int OFF_RL = OFF_SS + C::NPIX;           // int32 [256]
+    static constexpr int OFF_RL = OFF_HR + NH * 4;            // int32 [256]
     static constexpr int OFF_RHK = OFF_RL + 256 * 4;          // int32 [RH]
     static constexpr int OFF_RHV = OFF_RHK + RH * 4;          // int32 [RH]
     static constexpr int OFF_RMIN = OFF_RHV + RH * 4;         // int32 [256]
-    static constexpr int OFF_PM = OFF_RMIN + 256 * 4;         // uint32 [RM * RM]
-    static constexpr int OFF_COL = OFF_PM + RM * RM * 4;      // uint4 [NT]: packed basin ids of each column
+    // uint8 [NPIX] slot ids, then uint32 [PMN] pass matrix or (uint64 [EH], uint32 [EH]) edge hash
+    static constexpr int OFF_U = OFF_RMIN + 256 * 4;
+    static constexpr int UBYTES = C::NPIX > PMN * 4 ? (C::NPIX > EH * 12 ? C::NPIX : EH * 12)
+                                                    : (PMN * 4 > EH * 12 ? PMN * 4 : EH * 12);
+    static constexpr int OFF_COL = OFF_U + UBYTES;            // uint4 [NT]: packed basin ids of each column
     static constexpr int OFF_XF = OFF_COL + C::NT * 16;       // uint8 [TY][TZ]: ids of the +x face
     static constexpr int OFF_YF = OFF_XF + C::TY * C::TZ;     // uint8 [TX][TZ]: ids of the +y face
-    static constexpr int WL = C::TX * C::TZ;                  // boundary items per warp (every pixel)
-    static constexpr int OFF_WL = OFF_YF + C::TX * C::TZ;     // uint16 [NT / 32][WL]
-    static constexpr int OFF_HK = (OFF_WL + (C::NT / 32) * WL * 2 + 7) & ~7;   // uint64 [EH]
-    static constexpr int OFF_HV = OFF_HK + EH * 8;            // uint32 [EH]
-    static constexpr int OFF_C = (OFF_HV + EH * 4 + 127) & ~127;
-    static constexpr int OFF_G = OFF_C + ((CBYTES + 127) & ~127);
+    static constexpr int OFF_C = (OFF_YF + C::TX * C::TZ + 127) & ~127;   // code box, then uint16 [NT / 32][WL]
+    static constexpr int OFF_G = OFF_C + (((CBYTES > WLBYTES ? CBYTES : WLBYTES) + 127) & ~127);
     static constexpr int SMEM = OFF_G + ((GBYTES + 127) & ~127);
-    static_assert(OFF_HK % 8 == 0, "edge keys are 8-byte words");
+    static_assert(OFF_U % 8 == 0, "edge keys are 8-byte words");
+    static_assert(RM * (RM - 1) / 2 <= PMN && PMN % C::NT == 0 && EH % C::NT == 0, "warp-uniform flush");
 };
+
+// Entry of the pass matrix for basin ids a < c.
+__device__ __forceinline__ int pm_index(int a, int c) { return (c * (c - 1) >> 1) + a; }
 
 // root of slot c of a neighbouring tile whose span of the end list is e,
 // -1 if invalid
@@ -1657,7 +1666,7 @@ __device__ __forceinline__ int face_root(bool valid, int c, int2 e, const int2 *
 //     -z inside the tile can hold the tile's smallest index of that basin;
 //     those candidates take a shared atomic min per basin id.
 template <typename T, bool TMA>
-__global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ CUtensorMap tmc,
+__global__ void __launch_bounds__(TT<6>::NT, 3) k_rag6(const __grid_constant__ CUtensorMap tmc,
                                                        const __grid_constant__ CUtensorMap tmg, const Batch b,
                                                        const uint16_t *__restrict__ code,
                                                        const int2 *__restrict__ ends,
@@ -1672,16 +1681,16 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
     __shared__ int s_nr, s_full;
     int *hr = (int *)(smem + B::OFF_HR);
     int *hxr = hr, *hyr = hr + B::HX, *hzr = hyr + B::HY;
-    uint8_t *ss = smem + B::OFF_SS;
+    uint8_t *ss = smem + B::OFF_U;
     int *rl = (int *)(smem + B::OFF_RL);
     int *rhk = (int *)(smem + B::OFF_RHK);
     int *rhv = (int *)(smem + B::OFF_RHV);
     int *rmin = (int *)(smem + B::OFF_RMIN);
-    unsigned *pm = (unsigned *)(smem + B::OFF_PM);
+    unsigned *pm = (unsigned *)(smem + B::OFF_U);
     uint4 *colw = (uint4 *)(smem + B::OFF_COL);
     uint8_t *xfb = smem + B::OFF_XF, *yfb = smem + B::OFF_YF;
-    unsigned long long *hk = (unsigned long long *)(smem + B::OFF_HK);
-    unsigned *hv = (unsigned *)(smem + B::OFF_HV);
+    unsigned long long *hk = (unsigned long long *)(smem + B::OFF_U);
+    unsigned *hv = (unsigned *)(smem + B::OFF_U + B::EH * 8);
     uint16_t *cb = (uint16_t *)(smem + B::OFF_C);
     T *gb = (T *)(smem + B::OFF_G);
     const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
@@ -1797,19 +1806,25 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
     __syncthreads();
     const int nr = s_nr;
     const int mode = (s_full || nr > B::RB) ? 2 : (nr > B::RM ? 1 : 0);   // uniform in the CTA
-    if (do_rag && mode == 0)
-        for (int i = tid; i < B::RM * B::RM; i += C::NT) pm[i] = 0xffffffffu;
-    if (do_rag && mode > 0)
-        for (int i = tid; i < B::EH; i += C::NT) {
-            hk[i] = EMPTY_KEY;
-            hv[i] = 0xffffffffu;
-        }
+    // the pass matrix or the edge hash shares its words with the slot ids:
+    // cleared once those are read (modes 0, 1) or right away (mode 2, which
+    // numbers no slots)
+    auto clear_pairs = [&]() {
+        if (mode == 0)
+            for (int i = tid; i < B::PMN; i += C::NT) pm[i] = 0xffffffffu;
+        else
+            for (int i = tid; i < B::EH; i += C::NT) {
+                hk[i] = EMPTY_KEY;
+                hv[i] = 0xffffffffu;
+            }
+    };
+    if (do_rag && mode == 2) clear_pairs();
     const int first = te.x;
 
     auto edge = [&](int ida, int idb, unsigned h) {   // ids (mode 0, 1) or roots (mode 2)
         if (mode == 0) {
             const int a = ida < idb ? ida : idb, c2 = ida < idb ? idb : ida;
-            atomicMin(pm + a * B::RM + c2, h);
+            atomicMin(pm + pm_index(a, c2), h);
         } else {
             const int ra = mode < 2 ? rl[ida] : ida, rb = mode < 2 ? rl[idb] : idb;
             smem_edge_insert<true>((unsigned)(ra < rb ? ra : rb), (unsigned)(ra < rb ? rb : ra), h, hk, hv, B::EH, L,
@@ -1851,7 +1866,8 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
         }
         colw[tid] = make_uint4(P[0], P[1], P[2], P[3]);
         const unsigned P4 = do_rag ? ((unsigned)hzr[tid] & 0xffu) : 0xffu;   // +z face pixel
-        __syncthreads();
+        __syncthreads();   // slot ids read; the code box is read no more
+        if (do_rag) clear_pairs();
         // smallest index: candidates differ from their -z, -y, -x neighbours
         {
             const uint4 ym = ly > 0 ? colw[tid - 32] : make_uint4(~0u, ~0u, ~0u, ~0u);
@@ -1872,17 +1888,18 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
             }
         }
         if (do_rag) {
+            __syncthreads();   // pass matrix / edge hash cleared
             // pass values of the +x, +y, +z pairs of different basins
             const unsigned *ynw = ly + 1 < C::TY ? (const unsigned *)(colw + tid + 32) : (const unsigned *)yfb + 4 * lane;
             const unsigned *xfw = (const unsigned *)xfb + 4 * ly;
             const uint8_t *colb = (const uint8_t *)colw;   // byte k of column c: colb[c * 16 + k]
-            uint16_t *wlst = (uint16_t *)(smem + B::OFF_WL) + ly * B::WL;
+            uint16_t *wlst = (uint16_t *)(smem + B::OFF_C) + ly * B::WL;   // the code box is read no more
             auto pass = [&](auto matrix) {
                 constexpr bool MATRIX = decltype(matrix)::value;
                 auto note = [&](int ida, int idb, unsigned h) {
                     const int a = ida < idb ? ida : idb, c2 = ida < idb ? idb : ida;
                     if (MATRIX) {
-                        unsigned *e = pm + a * B::RM + c2;
+                        unsigned *e = pm + pm_index(a, c2);
                         if (h < *e) atomicMin(e, h);
                     } else {
                         const int ra = rl[a], rb = rl[c2];
@@ -1998,14 +2015,17 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_rag6(const __grid_constant__ C
     __syncthreads();
     if (mode < 2 && tid < nr && tid < B::RB && rmin[tid] != 0x7fffffff) atomicMin(mi + rl[tid], rmin[tid]);
     if (!do_rag) return;
-    static_assert((B::RM * B::RM) % C::NT == 0 && B::EH % C::NT == 0, "warp-uniform flush");
     if (mode == 0) {
-        for (int e = tid; e < B::RM * B::RM; e += C::NT) {
+        for (int e = tid; e < B::PMN; e += C::NT) {
             const unsigned h = pm[e];
             const bool have = h != 0xffffffffu;
             unsigned lo = 0, hi = 0;
             if (have) {   // the basin list is read for the few pairs present only
-                const int ra = rl[e / B::RM], rb = rl[e % B::RM];
+                // the ids (a, c) of entry e = c (c - 1) / 2 + a, a < c
+                int c = (int)((1.0f + __fsqrt_rn(1.0f + 8.0f * (float)e)) * 0.5f);
+                while (pm_index(0, c) > e) c--;
+                while (pm_index(0, c + 1) <= e) c++;
+                const int ra = rl[e - pm_index(0, c)], rb = rl[c];
                 lo = (unsigned)(ra < rb ? ra : rb);
                 hi = (unsigned)(ra < rb ? rb : ra);
             }
