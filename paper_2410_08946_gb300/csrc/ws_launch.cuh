@@ -125,7 +125,11 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
                             : (full ? k_init6<T, false, true> : k_init6<T, false, false>);
             const size_t smem = tma ? B6::SMEM_TMA : B6::SMEM_PLAIN;
             if ((e = allow_smem(kern, smem)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
-            // TMA: persistent CTAs, two tiles in flight each; plain loads: one CTA per tile
+            // three CTAs per SM need all of the SM's unified memory as shared memory
+            if ((e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+                return set_cuda_error(c, e, "smem carveout");
+            // TMA: persistent CTAs (the next tile's box loads during this one); plain loads: one CTA per tile
             const int grid = tma ? coop_grid(c, kern, C::NT, smem, b.ntiles) : b.ntiles;
             kern<<<grid, C::NT, smem, s>>>(tm, b, w.par, w.aux, w.dist, w.plat, w.act, w.tlist, w.roots, w.code,
                                            w.ends, w.tends, w.counters, c->status, ex);

@@ -578,8 +578,10 @@ __device__ __forceinline__ unsigned umin2(unsigned a, unsigned b) { return a < b
 template <typename T> struct Init6Box {
     using B = InitBox<T, 6>;
     static constexpr int NPIX = TC<6>::NPIX;
-    static constexpr int SMEM_TMA = 2 * B::STAGE + NPIX * 4 + NPIX * 2;   // two stages, pointers, slots
-    static constexpr int SMEM_PLAIN = B::STAGE + NPIX * 4 + NPIX * 2;
+    // one gradient box, 16-bit in-tile pointers, slots: 63,872 bytes for
+    // uint16, so three CTAs share an SM
+    static constexpr int SMEM_TMA = B::STAGE + NPIX * 2 + NPIX * 2;
+    static constexpr int SMEM_PLAIN = SMEM_TMA;
 };
 
 // Global offset of neighbour n (ascending index order: -z, -y, -x, +x, +y, +z).
@@ -596,7 +598,7 @@ __device__ __forceinline__ int go6(int n, const Geo &geo)
 // whose halo lies inside the image.  FULL also writes every pixel's arrow into
 // par; when ex.s is set, the states and arrows of Eq. 1 go into ex.
 template <typename T, bool CHECK, bool FULL>
-__device__ __forceinline__ void init6_step1(const T *gs, int *nx, uint16_t *slotof, int32_t *par,
+__device__ __forceinline__ void init6_step1(const T *gs, uint16_t *nx, uint16_t *slotof, int32_t *par,
                                             const int *lo_tab, int tid, int lx, int ly, int h0, int p0, int x, int y,
                                             int z0, const Geo &geo, unsigned &stb, unsigned &endb, unsigned &minb,
                                             int &plateau, const StepExport &ex)
@@ -638,7 +640,7 @@ __device__ __forceinline__ void init6_step1(const T *gs, int *nx, uint16_t *slot
         const int i = tid + k * C::NT;
         const bool follow = in && st0 && (tin & 1u);   // the arrow stays in the tile
         const int nn = has ? n : 0;
-        nx[i] = follow ? i + lo_tab[nn] : i;
+        nx[i] = (uint16_t)(follow ? i + lo_tab[nn] : i);
         if (FULL && in) par[p] = st0 ? p + go6(nn, geo) : p;
         // Only ws_step1 sets ex.s.  The uniform branch costs one instruction
         // per pixel and also keeps the compiler from interleaving all sixteen
@@ -663,7 +665,7 @@ __device__ __forceinline__ void init6_step1(const T *gs, int *nx, uint16_t *slot
 // (the step II / IV kernels and k_jump2 work there); elsewhere the arrow of a
 // path end travels with it in `ends`.
 template <typename T, bool TMA, bool FULL>
-__global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ CUtensorMap tm, const Batch b,
+__global__ void __launch_bounds__(TT<6>::NT, 3) k_init6(const __grid_constant__ CUtensorMap tm, const Batch b,
                                                         int32_t *__restrict__ par, int32_t *__restrict__ mi,
                                                         int32_t *__restrict__ dist, uint8_t *__restrict__ plat,
                                                         uint8_t *__restrict__ act, int32_t *__restrict__ tlist,
@@ -676,12 +678,12 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
     static_assert(C::NT == C::TX * C::TY && C::TX == 32 && C::PER == C::TZ && C::NT / 32 <= 32, "column layout");
     constexpr int NW = C::NT / 32;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bars[2];
+    __shared__ uint64_t bar;
     __shared__ int wbase[NW];
     __shared__ int s_first;
     __shared__ int lo_tab[6];
-    int *nx = (int *)(smem + (TMA ? 2 : 1) * B::STAGE);
-    uint16_t *slotof = (uint16_t *)(nx + C::NPIX);
+    uint16_t *nx = (uint16_t *)(smem + B::STAGE);
+    uint16_t *slotof = nx + C::NPIX;
     const int tid = threadIdx.x, lane = tid & 31, lx = lane, ly = tid >> 5;
     const int G = gridDim.x;
     constexpr int SZ = C::HY * B::RW;              // box step of one z
@@ -691,27 +693,24 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
         lo_tab[tid] = l[tid];
     }
 
-    if (TMA) {  // a single image (b.one); two tiles in flight per CTA
+    if (TMA) {  // a single image (b.one); the next tile's box loads while this tile's paths are doubled
         if (tid == 0) {
-            mbar_init(&bars[0], 1);
-            mbar_init(&bars[1], 1);
+            mbar_init(&bar, 1);
             mbar_fence_init();
             const int t0 = blockIdx.x;
-            if (t0 < b.ntiles) init_issue<T, 6, TMA>(&tm, (T *)smem, &bars[0], b, t0);
-            if (t0 + G < b.ntiles) init_issue<T, 6, TMA>(&tm, (T *)(smem + B::STAGE), &bars[1], b, t0 + G);
+            if (t0 < b.ntiles) init_issue<T, 6, TMA>(&tm, (T *)smem, &bar, b, t0);
         }
     }
     __syncthreads();
 
     int j = 0;
     for (int t = blockIdx.x; t < b.ntiles; t += G, j++) {
-        const int s = TMA ? (j & 1) : 0;
-        T *gs = (T *)(smem + s * B::STAGE);
+        T *gs = (T *)smem;
         const TileCtx tc = tile_ctx<6>(b, t);
         const Geo &geo = tc.geo;
         const int x0 = tc.x0, y0 = tc.y0, z0 = tc.z0, base = tc.base;
         if (TMA) {
-            const bool ok = mbar_wait(&bars[s], (unsigned)((j >> 1) & 1), status);
+            const bool ok = mbar_wait(&bar, (unsigned)(j & 1), status);
             if (__syncthreads_or(!ok)) return;
         } else {
             const T *g = (const T *)tc.grad;
@@ -775,8 +774,8 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
             lpre = inc - ne;
             if (lane == 31) wbase[ly] = inc;
         }
-        __syncthreads();  // the gradient box of stage s is no longer read
-        if (TMA && tid == 0 && t + 2 * G < b.ntiles) init_issue<T, 6, TMA>(&tm, gs, &bars[s], b, t + 2 * G);
+        __syncthreads();  // the gradient box is no longer read: load the next tile's
+        if (TMA && tid == 0 && t + G < b.ntiles) init_issue<T, 6, TMA>(&tm, gs, &bar, b, t + G);
         int first = 0, nend = 0;
         if (ly == 0) {
             const int c = lane < NW ? wbase[lane] : 0;
@@ -823,7 +822,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 2) k_init6(const __grid_constant__ 
         int cur[C::TZ];
 #pragma unroll
         for (int k = 0; k < C::TZ; k++) cur[k] = nx[tid + k * C::NT];
-        volatile int *vnx = nx;
+        volatile uint16_t *vnx = nx;
         for (int round = 0; round < C::NPIX; round++) {
             int more = 0;
 #pragma unroll
