@@ -762,7 +762,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 3) k_init6(const __grid_constant__ 
         }
         // number the ends: the thread's ends get consecutive slots after those
         // of the lanes before it (warp scan) and of the warps before it
-        int lpre;
+        int lpre, wtot;
         {
             const int ne = __popc(endb);
             int inc = ne;
@@ -772,6 +772,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 3) k_init6(const __grid_constant__ 
                 if (lane >= o) inc += u;
             }
             lpre = inc - ne;
+            wtot = __shfl_sync(0xffffffffu, inc, 31);
             if (lane == 31) wbase[ly] = inc;
         }
         __syncthreads();  // the gradient box is no longer read: load the next tile's
@@ -794,23 +795,45 @@ __global__ void __launch_bounds__(TT<6>::NT, 3) k_init6(const __grid_constant__ 
             }
         }
         __syncthreads();
-        const int slot0 = wbase[ly] + lpre;   // the slot of this thread's first end
         {
-            // each end: its slot goes below its lowest neighbour in its slotof
-            // entry, and its entry of ends is (the end, the next pixel of its
-            // path: the neighbour its arrow leads to out of the tile, or itself
-            // for a minimum or a plateau pixel)
-            const int fst = s_first;
-            for (unsigned m = endb; m; m &= m - 1) {
-                const int k = __ffs(m) - 1;
-                uint16_t *se = slotof + tid + k * C::NT;
-                const unsigned v = *se;
-                const int sl = slot0 + __popc(endb & ((1u << k) - 1u));
-                *se = (uint16_t)(v | (unsigned)sl);
-                const int e = p0 + k * HW;
-                const int nxt = ((stb >> (2 * k)) & 3u) == (unsigned)ST0 ? e + go6((int)(v >> 13), geo) : e;
-                ends[fst + sl] = make_int2(e, nxt);
+            // the warp's ends take the slots wbase[ly] + 0 .. wtot - 1 in lane
+            // order (a lane's own ends in z order); lane j writes the warp's
+            // ends j, j + 32, ...: the owner lane o of end j is the last lane
+            // with lpre <= j, and the end is the (j - lpre(o))-th voxel of o's
+            // column with an endb bit.  Each end's slot goes below its lowest
+            // neighbour in its slotof entry; its entry of ends is (the end,
+            // the next voxel of its path: the neighbour its arrow leads to out
+            // of the tile, or itself for a minimum or a plateau voxel).
+            const int ws0 = wbase[ly], fst = s_first + ws0;
+            const int rounds = (wtot + 31) >> 5;
+            for (int r = 0; r < rounds; r++) {
+                const int jj = r * 32 + lane;
+                int o = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int lp = __shfl_sync(0xffffffffu, lpre, o + step);
+                    if (lp <= jj) o += step;
+                }
+                const unsigned eo = __shfl_sync(0xffffffffu, endb, o);
+                const unsigned so = __shfl_sync(0xffffffffu, stb, o);
+                const int lo = __shfl_sync(0xffffffffu, lpre, o);
+                if (jj < wtot) {
+                    // k: the voxel of the (jj - lo)-th set bit of eo
+                    const int rk = jj - lo;
+                    int k = 0;
+#pragma unroll
+                    for (int step = 8; step > 0; step >>= 1)
+                        if (__popc(eo & ((1u << (k + step)) - 1u)) <= rk) k += step;
+                    uint16_t *se = slotof + ly * 32 + o + k * C::NT;
+                    const unsigned v = *se;
+                    const int sl = ws0 + jj;
+                    *se = (uint16_t)(v | (unsigned)sl);
+                    const int e = p0 + (o - lane) + k * HW;
+                    const int nxt = ((so >> (2 * k)) & 3u) == (unsigned)ST0 ? e + go6((int)(v >> 13), geo) : e;
+                    ends[fst + jj] = make_int2(e, nxt);
+                }
             }
+            __syncwarp();   // the slotof entries of the warp's ends are written
         }
 
         // step III inside the tile: pointer doubling.  A value read while its
