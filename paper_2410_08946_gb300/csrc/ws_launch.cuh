@@ -151,7 +151,8 @@ template <typename T, int CONN> static ws_status run_front(ws_context *c, const 
     }
     {
         PhaseScope ps(c, PH_PLATEAU, s);
-        const size_t smem = (size_t)C::HS * 8;
+        // box of G and distances (2D: and the staged plateau pixels with their starting distances)
+        const size_t smem = (size_t)C::HS * 8 + (kPlateauList<CONN> ? (size_t)C::NPIX * 6 : 0);
         if ((e = allow_smem(k_plateau2<T, CONN>, smem)) != cudaSuccess) return set_cuda_error(c, e, "smem attribute");
         const int grid = coop_grid(c, k_plateau2<T, CONN>, C::NT, smem, b.ntiles);
         e = launch_coop(k_plateau2<T, CONN>, grid, C::NT, smem, s, b, w.dist, (const uint8_t *)w.plat, w.act,

@@ -893,6 +893,37 @@ __global__ void __launch_bounds__(TT<6>::NT, 3) k_init6(const __grid_constant__ 
     }
 }
 
+// find / union in a tile-local union-find (the smaller index is the
+// root; atomicCAS links a root to a smaller root)
+__device__ __forceinline__ int lu_find(int *lab, int a)
+{
+    volatile int *v = lab;
+    for (int it = 0; it < (1 << 16); it++) {
+        const int b = v[a];
+        if (b == a) return a;
+        const int c = v[b];
+        if (c == b) return b;
+        v[a] = c;   // path halving
+        a = c;
+    }
+    return a;
+}
+
+__device__ __forceinline__ void lu_union(int *lab, int a, int b)
+{
+    for (int it = 0; it < (1 << 16); it++) {
+        a = lu_find(lab, a);
+        b = lu_find(lab, b);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(lab + a, a, b) == a) return;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // k_plateau2: step II distances on plateau tiles (cooperative)
 // ---------------------------------------------------------------------------
@@ -906,11 +937,14 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const Batch b, int32_
                                                            const int2 *__restrict__ pspan)
 {
     using C = TC<CONN>;
-    (void)plist;
-    (void)pspan;
+    // 2D: the relaxation visits the tile's plateau pixels only (its span of
+    // plist, staged as box indices in pl with their starting distances in po)
+    constexpr bool LIST = kPlateauList<CONN>;
     extern __shared__ __align__(128) unsigned char smem[];
     int *gs = (int *)smem;
     int *ds = gs + C::HS;
+    int *po = ds + C::HS;                              // (LIST) [NPIX]
+    uint16_t *pl = (uint16_t *)(po + C::NPIX);         // (LIST) [NPIX]
     __shared__ int flag_s;
     const int tid = threadIdx.x;
     const int ntl = counters[CNT_TILES];
@@ -950,48 +984,85 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const Batch b, int32_
                     ds[i] = INF_D;
                 }
             }
-            __syncthreads();
-            int orig[C::PER];
+            int border = 0;
+            if constexpr (LIST) {
+                const int2 span = pspan[t];
+                for (int e = tid; e < span.y; e += C::NT) {
+                    const int i = plist[span.x + e];
+                    pl[e] = (uint16_t)(((i / C::TX) + 1) * C::HX + i % C::TX + 1);
+                }
+                __syncthreads();   // the box and the list are written
+                for (int e = tid; e < span.y; e += C::NT) po[e] = ds[pl[e]];
+                for (int it = 0; it < 4 * C::NPIX + 8; it++) {
+                    int ch = 0;
+                    for (int e = tid; e < span.y; e += C::NT) {
+                        const int h = pl[e];
+                        const int gv = gs[h];
+                        const int d = ds[h];
+                        if (d <= 0) continue;
+                        int best = d;
 #pragma unroll
-            for (int k = 0; k < C::PER; k++) {
-                const int i = tid + k * C::NT;
-                const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
-                orig[k] = ds[((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * C::HX + lx + 1];
-            }
-            for (int it = 0; it < 4 * C::NPIX + 8; it++) {
-                int ch = 0;
+                        for (int n = 0; n < Nb<CONN>::n; n++) {
+                            const int hn = h + Nb<CONN>::dy(n) * C::HX + Nb<CONN>::dx(n);
+                            if (gs[hn] == gv) best = imin(best, ds[hn] + 1);
+                        }
+                        if (best < d) {
+                            ds[h] = best;
+                            ch = 1;
+                        }
+                    }
+                    if (!__syncthreads_or(ch)) break;
+                }
+                for (int e = tid; e < span.y; e += C::NT) {
+                    const int h = pl[e];
+                    if (ds[h] == po[e]) continue;
+                    const int lx = h % C::HX - 1, ly = h / C::HX - 1;
+                    __stcg(dist + tc.base + (y0 + ly) * geo.W + x0 + lx, ds[h]);
+                    if (lx == 0 || lx == C::TX - 1 || ly == 0 || ly == C::TY - 1) border = 1;
+                }
+            } else {
+                __syncthreads();
+                int orig[C::PER];
+#pragma unroll
+                for (int k = 0; k < C::PER; k++) {
+                    const int i = tid + k * C::NT;
+                    const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+                    orig[k] = ds[((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * C::HX + lx + 1];
+                }
+                for (int it = 0; it < 4 * C::NPIX + 8; it++) {
+                    int ch = 0;
+#pragma unroll
+                    for (int k = 0; k < C::PER; k++) {
+                        const int i = tid + k * C::NT;
+                        const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
+                        const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * C::HX + lx + 1;
+                        const int gv = gs[h];
+                        const int d = ds[h];
+                        if (gv < 0 || d <= 0) continue;
+                        int best = d;
+#pragma unroll
+                        for (int n = 0; n < Nb<CONN>::n; n++) {
+                            const int hn = h + (Nb<CONN>::dz(n) * C::HY + Nb<CONN>::dy(n)) * C::HX + Nb<CONN>::dx(n);
+                            if (gs[hn] == gv) best = imin(best, ds[hn] + 1);
+                        }
+                        if (best < d) {
+                            ds[h] = best;
+                            ch = 1;
+                        }
+                    }
+                    if (!__syncthreads_or(ch)) break;
+                }
 #pragma unroll
                 for (int k = 0; k < C::PER; k++) {
                     const int i = tid + k * C::NT;
                     const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
                     const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * C::HX + lx + 1;
-                    const int gv = gs[h];
-                    const int d = ds[h];
-                    if (gv < 0 || d <= 0) continue;
-                    int best = d;
-#pragma unroll
-                    for (int n = 0; n < Nb<CONN>::n; n++) {
-                        const int hn = h + (Nb<CONN>::dz(n) * C::HY + Nb<CONN>::dy(n)) * C::HX + Nb<CONN>::dx(n);
-                        if (gs[hn] == gv) best = imin(best, ds[hn] + 1);
+                    if (ds[h] != orig[k]) {
+                        __stcg(dist + tc.base + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx, ds[h]);
+                        if (lx == 0 || lx == C::TX - 1 || ly == 0 || ly == C::TY - 1 ||
+                            (C::D3 && (lz == 0 || lz == C::TZ - 1)))
+                            border = 1;
                     }
-                    if (best < d) {
-                        ds[h] = best;
-                        ch = 1;
-                    }
-                }
-                if (!__syncthreads_or(ch)) break;
-            }
-            int border = 0;
-#pragma unroll
-            for (int k = 0; k < C::PER; k++) {
-                const int i = tid + k * C::NT;
-                const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
-                const int h = ((C::D3 ? lz + 1 : 0) * C::HY + ly + 1) * C::HX + lx + 1;
-                if (ds[h] != orig[k]) {
-                    __stcg(dist + tc.base + ((z0 + lz) * geo.H + y0 + ly) * geo.W + x0 + lx, ds[h]);
-                    if (lx == 0 || lx == C::TX - 1 || ly == 0 || ly == C::TY - 1 ||
-                        (C::D3 && (lz == 0 || lz == C::TZ - 1)))
-                        border = 1;
                 }
             }
             if (__syncthreads_or(border) && tid == 0) {
@@ -1027,37 +1098,6 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_plateau2(const Batch b, int32_
 // k_resolve2: step II pointer choice and step IV Union on plateau tiles
 // ---------------------------------------------------------------------------
 
-// find / union in a tile-local union-find (the smaller local index is the
-// root; atomicCAS links a root to a smaller root)
-__device__ __forceinline__ int lu_find(int *lab, int a)
-{
-    volatile int *v = lab;
-    for (int it = 0; it < (1 << 16); it++) {
-        const int b = v[a];
-        if (b == a) return a;
-        const int c = v[b];
-        if (c == b) return b;
-        v[a] = c;   // path halving
-        a = c;
-    }
-    return a;
-}
-
-__device__ __forceinline__ void lu_union(int *lab, int a, int b)
-{
-    for (int it = 0; it < (1 << 16); it++) {
-        a = lu_find(lab, a);
-        b = lu_find(lab, b);
-        if (a == b) return;
-        if (a < b) {
-            const int t = a;
-            a = b;
-            b = t;
-        }
-        if (atomicCAS(lab + a, a, b) == a) return;
-    }
-}
-
 // Step II pointer choice on the plateau tiles, and step IV inside each tile:
 // the minimal-plateau pixels of a tile are joined in a shared-memory union-find
 // and each points at its component's smallest pixel (k_union2 joins the
@@ -1073,6 +1113,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const Batch b, int32_
     using C = TC<CONN>;
     constexpr bool LIST = kPlateauList<CONN>;
     __shared__ int lab[C::NPIX];   // tile-local union-find of the minimal-plateau pixels (-1: other pixel)
+    __shared__ uint16_t sl[LIST ? C::NPIX : 1];   // (LIST) the tile's plateau pixels
     const int ntl = counters[CNT_TILES];
     for (int j = blockIdx.x; j < ntl; j += gridDim.x) {
         const int t = tlist[j];
@@ -1089,6 +1130,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const Batch b, int32_
         }
         for (int ei = threadIdx.x; ei < span.y; ei += C::NT) {
             const int i = LIST ? (int)plist[span.x + ei] : ei;
+            if (LIST) sl[ei] = (uint16_t)i;
             const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
             const int x = tc.x0 + lx, y = tc.y0 + ly, z = tc.z0 + lz;
             int l = -1;
@@ -1119,8 +1161,10 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const Batch b, int32_
             lab[i] = l;
         }
         __syncthreads();
-        // unions with the forward neighbours inside the tile
-        for (int i = threadIdx.x; i < C::NPIX; i += C::NT) {
+        // unions with the forward neighbours inside the tile (LIST: the
+        // minimal-plateau pixels are among the listed ones)
+        for (int ei = threadIdx.x; ei < span.y; ei += C::NT) {
+            const int i = LIST ? (int)sl[ei] : ei;
             if (lab[i] < 0) continue;
             const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
             const unsigned gp = g[((tc.z0 + lz) * geo.H + tc.y0 + ly) * geo.W + tc.x0 + lx];
@@ -1135,7 +1179,8 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const Batch b, int32_
         }
         __syncthreads();
         // every minimal-plateau pixel points at its in-tile component's smallest pixel
-        for (int i = threadIdx.x; i < C::NPIX; i += C::NT) {
+        for (int ei = threadIdx.x; ei < span.y; ei += C::NT) {
+            const int i = LIST ? (int)sl[ei] : ei;
             if (lab[i] < 0) continue;
             const int r = lu_find(lab, i);
             const int rx = r % C::TX, ry = (r / C::TX) % C::TY, rz = r / (C::TX * C::TY);
@@ -1156,12 +1201,23 @@ __global__ void __launch_bounds__(NTHR) k_union2(const Batch b, int32_t *par, co
                                                const int32_t *counters, DevStatus *status)
 {
     using C = TC<CONN>;
+    // 2D: the pixels with a forward neighbour outside the tile are its last
+    // column, its last row and (8-connectivity) its first column; they are
+    // enumerated directly (e -> (lx, ly)), 3D tests every pixel of the tile
+    constexpr bool D2 = !C::D3;
+    constexpr bool X0 = CONN % 100 == 8;
+    constexpr int NB = D2 ? C::TY + C::TX - 1 + (X0 ? C::TY - 1 : 0) : C::NPIX;
     const int ntl = counters[CNT_TILES];
     for (int j = blockIdx.x; j < ntl; j += gridDim.x) {
         const TileCtx tc = tile_ctx<CONN>(b, tlist[j]);
         const Geo &geo = tc.geo;
         const T *g = (const T *)tc.grad;
-        for (int i = threadIdx.x; i < C::NPIX; i += NTHR) {
+        for (int ei = threadIdx.x; ei < NB; ei += NTHR) {
+            int i = ei;
+            if (D2)
+                i = ei < C::TY ? ei * C::TX + C::TX - 1
+                               : (ei < C::TY + C::TX - 1 ? (C::TY - 1) * C::TX + ei - C::TY
+                                                         : (ei - (C::TY + C::TX - 1)) * C::TX);
             const int lx = i % C::TX, ly = (i / C::TX) % C::TY, lz = i / (C::TX * C::TY);
             // only pixels with a forward neighbour outside the tile
             const bool border = lx == C::TX - 1 || ly == C::TY - 1 || (C::D3 && lz == C::TZ - 1) ||
