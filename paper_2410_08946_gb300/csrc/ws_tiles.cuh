@@ -2227,7 +2227,11 @@ static __global__ void __launch_bounds__(NTHR) k_write_batch(const Batch b, cons
     int cur = -1, lo = 0, hi = -1;   // cached image of the previous pixel
     ImgDesc d{};
     int rb = 0;
-    for (int g = blockIdx.x * NTHR + threadIdx.x; g < b.npix; g += gridDim.x * NTHR) {
+    // each CTA writes one contiguous range of the batch's pixels, so that a
+    // thread's next pixel is almost always in the image of its last one
+    const int chunk = (int)(((long long)b.npix + gridDim.x - 1) / gridDim.x);
+    const int g0 = blockIdx.x * chunk, g1 = (int)min((long long)b.npix, (long long)g0 + chunk);
+    for (int g = g0 + threadIdx.x; g < g1; g += NTHR) {
         if (g < lo || g > hi) {
             cur = img_of_pixel(b, g);
             d = img_desc(b, cur);
