@@ -1114,6 +1114,9 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const Batch b, int32_
     constexpr bool LIST = kPlateauList<CONN>;
     __shared__ int lab[C::NPIX];   // tile-local union-find of the minimal-plateau pixels (-1: other pixel)
     __shared__ uint16_t sl[LIST ? C::NPIX : 1];   // (LIST) the tile's plateau pixels
+    // (LIST) a plateau pixel's descent on this tile's plateau: the local index
+    // of the next plateau pixel, or ~(global pixel) where it leaves them
+    __shared__ int nt[LIST ? C::NPIX : 1];
     const int ntl = counters[CNT_TILES];
     for (int j = blockIdx.x; j < ntl; j += gridDim.x) {
         const int t = tlist[j];
@@ -1141,7 +1144,7 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const Batch b, int32_
                     l = i;
                 } else if (d > 0) {
                     const unsigned gp = g[p];
-                    int best = -1;
+                    int best = -1, bestl = -1;
 #pragma unroll
                     for (int n = 0; n < Nb<CONN>::n; n++) {
                         const int xx = x + Nb<CONN>::dx(n), yy = y + Nb<CONN>::dy(n), zz = z + Nb<CONN>::dz(n);
@@ -1149,18 +1152,49 @@ __global__ void __launch_bounds__(TT<CONN>::NT) k_resolve2(const Batch b, int32_
                         const int q = (zz * geo.H + yy) * geo.W + xx;
                         if (g[q] != gp) continue;
                         const int dq = plat[tc.tile0 + tile_of_c<CONN>(tc.tg, xx, yy, zz)] ? dist[tc.base + q] : 0;
-                        if (dq == d - 1 && q > best) best = q;
+                        if (dq == d - 1 && q > best) {
+                            best = q;
+                            const int ax = lx + Nb<CONN>::dx(n), ay = ly + Nb<CONN>::dy(n);
+                            bestl = ax >= 0 && ax < C::TX && ay >= 0 && ay < C::TY ? ay * C::TX + ax : -1;
+                        }
                     }
                     if (best < 0) {
                         record_error(status, DEV_NONCONVERGED, 7);
                         best = p;
+                        bestl = -1;
                     }
-                    par[tc.base + p] = tc.base + best;
+                    if (LIST)
+                        nt[i] = d > 1 && bestl >= 0 ? bestl : ~(tc.base + best);
+                    else
+                        par[tc.base + p] = tc.base + best;
                 }
             }
             lab[i] = l;
         }
         __syncthreads();
+        if (LIST) {
+            // step III along the tile's plateau pixels (pointer doubling in
+            // shared memory): each plateau pixel then points where its descent
+            // leaves them -- a pixel at distance 0 or one of another tile
+            for (int round = 0; round < C::NPIX; round++) {
+                int more = 0;
+                for (int ei = threadIdx.x; ei < span.y; ei += C::NT) {
+                    const int i = sl[ei];
+                    const int c = nt[i];
+                    if (lab[i] >= 0 || c < 0) continue;
+                    const int c2 = nt[c];
+                    nt[i] = c2;
+                    more |= c2 >= 0;
+                }
+                if (!__syncthreads_or(more)) break;
+            }
+            for (int ei = threadIdx.x; ei < span.y; ei += C::NT) {
+                const int i = sl[ei];
+                if (lab[i] >= 0) continue;
+                const int lx = i % C::TX, ly = i / C::TX;
+                par[tc.base + (tc.y0 + ly) * geo.W + tc.x0 + lx] = ~nt[i];
+            }
+        }
         // unions with the forward neighbours inside the tile (LIST: the
         // minimal-plateau pixels are among the listed ones)
         for (int ei = threadIdx.x; ei < span.y; ei += C::NT) {
@@ -1711,6 +1745,14 @@ template <typename T> struct Rag6Box {
     static_assert(RM * (RM - 1) / 2 <= PMN && PMN % C::NT == 0 && EH % C::NT == 0, "warp-uniform flush");
 };
 
+// Bit 7 of byte k set where byte k of a and b differ (no carry crosses a
+// byte: the low seven bits of each byte plus 0x7f stay inside it).
+__device__ __forceinline__ unsigned ne4(unsigned a, unsigned b)
+{
+    const unsigned x = a ^ b;
+    return (((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x) & 0x80808080u;
+}
+
 // Entry of the pass matrix for basin ids a < c.
 __device__ __forceinline__ int pm_index(int a, int c) { return (c * (c - 1) >> 1) + a; }
 
@@ -1955,8 +1997,7 @@ __global__ void __launch_bounds__(TT<6>::NT, 3) k_rag6(const __grid_constant__ C
                 const unsigned zm = __funnelshift_l(w > 0 ? P[w - 1] : ~0u, P[w], 8);   // bytes k - 1
                 unsigned xm = __shfl_up_sync(0xffffffffu, P[w], 1);
                 if (lane == 0) xm = ~0u;
-                unsigned cand = __vcmpne4(P[w], zm) & __vcmpne4(P[w], YM[w]) & __vcmpne4(P[w], xm) &
-                                __vcmpne4(P[w], 0xffffffffu);
+                unsigned cand = ne4(P[w], zm) & ne4(P[w], YM[w]) & ne4(P[w], xm) & ne4(P[w], 0xffffffffu);
                 while (cand) {
                     const int q = (__ffs(cand) - 1) >> 3;
                     cand &= ~(0xffu << (8 * q));
@@ -1995,10 +2036,10 @@ __global__ void __launch_bounds__(TT<6>::NT, 3) k_rag6(const __grid_constant__ C
                     unsigned xn = __shfl_down_sync(0xffffffffu, P[w], 1);
                     if (lane == 31) xn = xfw[w];
                     const unsigned yn = ynw[w];
-                    const unsigned own = __vcmpne4(P[w], 0xffffffffu);
-                    fz |= bits(__vcmpne4(P[w], zn) & own & __vcmpne4(zn, 0xffffffffu)) << (4 * w);
-                    fy |= bits(__vcmpne4(P[w], yn) & own & __vcmpne4(yn, 0xffffffffu)) << (4 * w);
-                    fx |= bits(__vcmpne4(P[w], xn) & own & __vcmpne4(xn, 0xffffffffu)) << (4 * w);
+                    const unsigned own = ne4(P[w], 0xffffffffu);
+                    fz |= bits(ne4(P[w], zn) & own & ne4(zn, 0xffffffffu)) << (4 * w);
+                    fy |= bits(ne4(P[w], yn) & own & ne4(yn, 0xffffffffu)) << (4 * w);
+                    fx |= bits(ne4(P[w], xn) & own & ne4(xn, 0xffffffffu)) << (4 * w);
                 }
                 // compact them into the warp's list: (directions, k, lane)
                 unsigned fa = fx | fy | fz;
