@@ -1421,7 +1421,9 @@ template <typename T, int CONN> struct LabelBox {
     static constexpr int RWG = C::TX + 2 * AG;          // grad box: x from x0 - AG
     static constexpr int PBYTES = RWP * C::BY * C::BZ * 4;
     static constexpr int GBYTES = RWG * C::BY * C::BZ * (int)sizeof(T);
-    static constexpr int DSLOTS = 4096;                 // distinct path ends per tile (dedupe table)
+    // distinct path ends per tile (dedupe table): a 2D tile's box holds about 2,100 pixels whose paths
+    // end at a few hundred pixels; a 3D box (26-connectivity) about 9,500
+    static constexpr int DSLOTS = C::D3 ? 4096 : 1024;
     static constexpr int RBYTES = DSLOTS * 8 > C::HASH * 12 ? DSLOTS * 8 : C::HASH * 12;
     static constexpr int OFF_P = (RBYTES + 127) & ~127; // region R (dedupe, then edge hash) first
     static constexpr int OFF_G = OFF_P + ((PBYTES + 127) & ~127);
@@ -1433,7 +1435,8 @@ template <typename T, int CONN> struct LabelBox {
 __device__ __forceinline__ int dedupe_slot(int *dk, int key, int nslots)
 {
     volatile int *vk = dk;
-    unsigned s = ((unsigned)key * 0x9E3779B1u) >> 20;   // 12 bits: nslots == 4096
+    // the top log2(nslots) bits of a multiplicative hash (nslots a power of two)
+    unsigned s = ((unsigned)key * 0x9E3779B1u) >> (33 - __ffs(nslots));
     s &= (unsigned)(nslots - 1);
     for (int probe = 0; probe < 64; probe++) {
         const int k = vk[s];
