@@ -82,7 +82,8 @@ typedef struct {
     int32_t jump_round_cap;      /* max global rounds of step III pointer jumping */
     int32_t jumps_per_round;     /* pointer hops per pixel per round (the paper's RR, Sec. 3.1) */
     int32_t barrier_timeout_ms;  /* device-wide barrier wait limit */
-    int64_t edge_capacity;       /* slots of the region-adjacency hash table */
+    int64_t edge_capacity;       /* slots of the region-adjacency table and edge lists (0: pixels x forward
+                                    neighbours, rounded up to a power of two, at most 2^28) */
     int32_t levels_ctas_per_sm;  /* CTAs per SM of the cooperative waterfall-level kernel (1..32) */
     int32_t barrier_withhold;    /* failure-detection tests only: 1 arms a one-shot hold, 0 = off.  In
                                     the next cooperative kernel the context launches, block 0 does not

@@ -367,8 +367,11 @@ ws_status ensure_rec(ws_context *c, size_t bytes)
 // Edge-table slots of a call over npix pixels (the sizing in run_core).
 size_t edge_slots(size_t npix, int conn, const ws_context *c)
 {
+    // every pixel puts at most one pair per forward neighbour (halfn of them),
+    // so npix * halfn slots never overflow below the 2^28 cap (a checkerboard
+    // of strict minima comes close: a pair for almost every forward neighbour)
     const int halfn = conn == 26 ? 13 : conn / 2;
-    size_t want = npix * (size_t)halfn / 2;
+    size_t want = npix * (size_t)halfn;
     if (c && c->tun.edge_capacity > 0) want = (size_t)c->tun.edge_capacity;
     size_t cap = 1 << 16;
     while (cap < want && cap < ((size_t)1 << 28)) cap <<= 1;
@@ -388,7 +391,7 @@ size_t workspace_bound(size_t npix, size_t ntiles, size_t nimg, int conn, int NL
         // batch summing such requests (twice the wanted slots covers the
         // power-of-two rounding of the sum)
         const int halfn = conn == 26 ? 13 : conn / 2;
-        b += (additive ? npix * (size_t)halfn + ((size_t)1 << 16) : edge_slots(npix, conn, nullptr)) * 40;
+        b += (additive ? 2 * npix * (size_t)halfn + ((size_t)1 << 16) : edge_slots(npix, conn, nullptr)) * 40;
     }
     return b;
 }

@@ -196,8 +196,9 @@ template <typename T, int CONN> static ws_status run_core(ws_context *c, const B
         if (e != cudaSuccess) return set_cuda_error(c, e, "jump launch");
     }
     if (do_rag) {
-        // distinct adjacent basin pairs: about 3 K0 <= 1.5 N for a fragmented 2D
-        // image; slots for a load factor <= 1/2 (capped at 2^28 slots)
+        // at most one pair record per pixel and forward neighbour (the 2D list),
+        // and as many table slots (a load factor <= 1/2 for the region table's
+        // distinct pairs in practice); capped at 2^28 slots
         if ((st = ensure_edges(c, edge_slots((size_t)b.npix, CONN, c), s)) != WS_OK) return st;
         if ((e = cudaMemsetAsync(w.ecnt, 0, 4, s)) != cudaSuccess) return set_cuda_error(c, e, "memset");
     }

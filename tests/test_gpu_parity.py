@@ -338,3 +338,36 @@ def test_invalid_arguments(ctx):
     assert e.value.status == binding.WS_ERR_INVALID
     with pytest.raises(binding.WsError):
         ctx.segment(img, 4, 0)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("shape", [(256, 256), (130, 301)])
+def test_segment_crowded_path_ends(ctx, conn, shape):
+    """A checkerboard of 0 and 1 (plus a ramp on the ones): every 0 is a strict
+    minimum (4-connectivity) or part of a diagonal plateau of minima
+    (8-connectivity), so a tile's box holds more distinct path ends than the
+    adjacency kernel's shared table; the ends it cannot list are chased one by
+    one, and the labels stay those of the oracle."""
+    H, W = shape
+    yy, xx = np.mgrid[0:H, 0:W]
+    img = (((yy + xx) % 2) * (1 + (xx * 7 + yy * 3) % 200)).astype(np.uint8)
+    levels, counts = oracle.segment(img, conn, 3)
+    lv_d, c_d = ctx.segment(dev(img), conn, 3)
+    ctx.check()
+    assert host(c_d).tolist() == counts.tolist()
+    assert np.array_equal(host(lv_d), levels)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_segment_plateau_terraces(ctx, conn):
+    """Wide flat terraces (a blob gradient quantised to 4 levels): long plateau
+    descents inside and across tiles, minimal plateaux joined across tile
+    borders, tiles that are almost all plateau next to tiles with few plateau
+    pixels."""
+    g = blob_grad(300, 421, 21)
+    img = (g >> 6).astype(np.uint8)
+    levels, counts = oracle.segment(img, conn, 4)
+    lv_d, c_d = ctx.segment(dev(img), conn, 4)
+    ctx.check()
+    assert host(c_d).tolist() == counts.tolist()
+    assert np.array_equal(host(lv_d), levels)
