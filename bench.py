@@ -135,9 +135,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def _code_text(path):
+    """The source without // comments, trailing blanks and empty lines: what the compiler sees, so that an
+    edit of the comments alone keeps the traffic figures measured on that source."""
+    out = []
+    for line in open(path, encoding="utf-8"):
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            out.append(code)
+    return "\n".join(out).encode()
+
+
 def _source_sha(kernel):
     src = os.path.join(ROOT, "paper_2410_08946_gb300", "csrc", KERNEL_SOURCE.get(kernel, "ws_tiles.cuh"))
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return hashlib.sha256(_code_text(src)).hexdigest()[:16]
 
 
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")

@@ -10,18 +10,21 @@
 //               follows its arrows through shared memory until the path
 //               leaves the tile, reaches a minimum, or reaches a plateau
 //               pixel.  Writes that end point (par), flags tiles that hold
-//               plateau pixels and lists the minima.
+//               plateau pixels, lists the minima and (2D) lists each tile's
+//               plateau pixels.
 //   k_plateau2  step II distances on the listed plateau tiles only (in-tile
 //               relaxation with a frozen halo, device-wide rounds; the fixed
-//               point of Alg. 3)
+//               point of Alg. 3); 2D relaxes the tile's listed plateau pixels
 //   k_resolve2  step II pointer choice, step IV Union of minimal plateaux
+//               inside each tile (2D: and step III along the tile's plateau)
+//   k_union2    step IV across tile borders
 //   k_jump2     step III for plateau tiles (pointer jumping rounds), lists
 //               the minimal-plateau roots
 //   k_label     per tile: final root of every pixel (chasing the few
 //               tile-to-tile hops left), smallest pixel index per basin, and
 //               Alg. 5 step V on pixel pairs (runs of equal neighbour roots
 //               merged in registers, then a shared-memory hash, then the
-//               global region table)
+//               edge list (2D) or the global region table (26-connectivity))
 // These serve 2D (4-, 8-connectivity) and 3D 26-connectivity.
 //
 // 3D volumes with 6-connectivity take a variant of this pipeline with one z
