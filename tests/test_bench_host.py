@@ -86,3 +86,16 @@ def test_reference_arm_line():
     assert rec["impl"] == "reference" and rec["steps"] == 2 and rec["warmup"] == 3
     assert rec["value"] == rec["cpu_baseline"]["value"] == rec["e2e"]["value"] > 0
     assert rec["cpu_baseline"]["cores"] == 1
+
+
+def test_source_hash_ignores_comments(tmp_path):
+    """The traffic records stay valid across comment edits of a kernel source
+    and not across code edits."""
+    a = tmp_path / "a.cuh"
+    a.write_text("int f(int x)  // doubles\n{\n    return 2 * x;\n}\n")
+    b = tmp_path / "b.cuh"
+    b.write_text("// a new header comment\nint f(int x)\n{\n\n    return 2 * x;   // twice\n}\n")
+    c = tmp_path / "c.cuh"
+    c.write_text("int f(int x)\n{\n    return 3 * x;\n}\n")
+    assert bench._code_text(str(a)) == bench._code_text(str(b))
+    assert bench._code_text(str(a)) != bench._code_text(str(c))
